@@ -1,0 +1,202 @@
+/*
+ * stg.h -- C ABI of the GB300 staggered-fermion hot path.
+ *
+ * Operations (arXiv:1801.01473):
+ *   - the off-diagonal blocks D_eo / D_oe of the staggered Dirac matrix (Sec. 2),
+ *     with the staggered and antiperiodic-time phases attached to the links as
+ *     u_mu(x) U_mu(x) (Sec. 4.1) and optional 12-real link compression
+ *     r3 = (r1 x r2)^* (Sec. 4.1);
+ *   - the shifted normal operator  A_sigma = m^2 + sigma - D_eo D_oe  (Eq. shift_eo);
+ *   - the multi-shift CG solve of A_sigma_i x_i = b for all poles sigma_i (Sec. 2);
+ *   - the fermion force of S = sum_i r_i Re(b^dag x_i) with respect to the links.
+ *
+ * Conventions.
+ *   site      i = x + Lx*(y + Ly*(z + Lz*t)), mu = 0..3 = x, y, z, t; all extents even.
+ *   parity    (x+y+z+t) mod 2; a site of either parity has half index i>>1 (Vh = V/2).
+ *   phases    u_mu(x) = (-1)^(x_0+...+x_{mu-1}), times -1 on t-links with x_t = Lt-1
+ *             when the lattice is antiperiodic in time.
+ *   operator  (D psi)(x) = 1/2 sum_mu [ u_mu(x) U_mu(x) psi(x+mu) - u_mu(x-mu) U_mu(x-mu)^dag psi(x-mu) ].
+ *             D_eo maps odd -> even, D_oe maps even -> odd; D_oe^dag = -D_eo.
+ *
+ * Canonical (interchange) layouts, complex128, row-major:
+ *   links     [4][Lt][Lz][Ly][Lx][3][3]           (U[mu][i][a][b], a = row)
+ *   fields    [Vh][3] on one parity, half-index order
+ *   force     [4][Lt][Lz][Ly][Lx][3][3]
+ * Internal layouts (what stg_dslash_* and stg_normal_op read and write):
+ *   F64 field: 3 arrays of Vh double2 (colour-major structure of arrays), 48 B/site.
+ *   F32 field: Vh float4 (colours 0,1) followed by Vh float2 (colour 2), 24 B/site.
+ *   A gauge of precision F64 works on F64 fields; F32, BF16 and F16 gauges work on F32 fields.
+ *
+ * Memory.  Every pointer argument named *_dev is device memory owned by the caller
+ * and must stay valid until the work queued on `stream` has finished.  Host arrays are
+ * read before the call returns.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ * Opaque handles (stg_lattice, stg_gauge) and the solver workspaces are owned by the
+ * library; *_destroy releases them.
+ *
+ * Errors.  Every call returns stg_status; nothing aborts or exits.  Arguments are
+ * checked on the host before any launch.  stg_last_error() returns a message describing
+ * the last failure of the calling thread.  Calls are asynchronous on `stream` except the
+ * solvers, which synchronise the stream to fill their statistics.
+ */
+#ifndef STG_H
+#define STG_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    STG_OK = 0,
+    STG_ERR_ARG = -1,     /* null pointer, bad enum, bad count, misaligned pointer          */
+    STG_ERR_SHAPE = -2,   /* lattice extents not even / too small, mismatched lattices      */
+    STG_ERR_CUDA = -3,    /* a CUDA runtime call failed (message in stg_last_error)          */
+    STG_ERR_NOCONV = -4,  /* solver hit max_iter; statistics filled, best iterate returned   */
+    STG_ERR_TIMEOUT = -5, /* a bounded device-side wait gave up                              */
+    STG_ERR_OOM = -6      /* device allocation failed                                       */
+} stg_status;
+
+typedef enum { STG_F64 = 0, STG_F32 = 1, STG_BF16 = 2, STG_F16 = 3 } stg_prec;
+typedef enum { STG_RECON18 = 18, STG_RECON12 = 12 } stg_recon;
+
+typedef struct stg_lattice stg_lattice;
+typedef struct stg_gauge stg_gauge;
+
+/* Human-readable name of a status code; never NULL. */
+const char *stg_status_string(stg_status s);
+/* Message of the last failing call on this thread ("" if none); never NULL. */
+const char *stg_last_error(void);
+/* Library version string. */
+const char *stg_version(void);
+
+/* ---- lattice geometry ---------------------------------------------------------------- */
+
+/* dims = {Lx, Ly, Lz, Lt}; every extent even and >= 2, V <= 2^31.  t_antiperiodic != 0
+ * puts the antiperiodic boundary sign on the t-links with x_t = Lt-1 (Sec. 4.1 folds it
+ * into u_mu).  *out receives a new handle.  STG_ERR_SHAPE on odd or small extents. */
+stg_status stg_lattice_create(const int32_t dims[4], int32_t t_antiperiodic, stg_lattice **out);
+void stg_lattice_destroy(stg_lattice *lat);
+/* Number of sites of one parity (0 even, 1 odd) or of the whole lattice (-1); -1 on NULL. */
+int64_t stg_lattice_sites(const stg_lattice *lat, int32_t parity);
+
+/* ---- gauge field ----------------------------------------------------------------------- */
+
+/* Copies the canonical complex128 links (device memory, [4][V][3][3]) into a
+ * library-owned copy in the internal structure-of-arrays layout
+ * [mu][parity][chunk][Vh] at precision `prec`.  recon = STG_RECON12 keeps only rows 1 and
+ * 2 and rebuilds row 3 = (r1 x r2)^* in registers (Sec. 4.1); this is exact only for
+ * SU(3) links.  BF16/F16 require STG_RECON12.  The copy is finished when the work on
+ * `stream` is.  The lattice must outlive the gauge. */
+stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, stg_prec prec, stg_recon recon,
+                            void *stream, stg_gauge **out);
+void stg_gauge_destroy(stg_gauge *g);
+/* Bytes of the internal link copy (4 V links). */
+size_t stg_gauge_bytes(const stg_gauge *g);
+
+/* ---- fermion fields ----------------------------------------------------------------------- */
+
+/* Bytes of one parity's field in the internal layout for vector precision F64 or F32
+ * (48 or 24 bytes per site); 0 for any other precision or a NULL lattice. */
+size_t stg_field_bytes(const stg_lattice *lat, stg_prec vec_prec);
+/* canonical complex128 [Vh][3] (device) <-> internal layout (device). vec_prec F64 or F32. */
+stg_status stg_field_pack(const stg_lattice *lat, stg_prec vec_prec, const void *canon_c128_dev, void *internal_dev,
+                          void *stream);
+stg_status stg_field_unpack(const stg_lattice *lat, stg_prec vec_prec, const void *internal_dev, void *canon_c128_dev,
+                            void *stream);
+
+/* ---- the staggered operator (Sec. 2, Sec. 4.2) ----------------------------------------------- */
+
+/* out_even = D_eo in_odd.  Internal layout at the gauge's vector precision. in/out must not
+ * overlap.  Pointers 16-byte aligned. */
+stg_status stg_dslash_eo(const stg_gauge *g, void *out_even_dev, const void *in_odd_dev, void *stream);
+/* out_odd = D_oe in_even. */
+stg_status stg_dslash_oe(const stg_gauge *g, void *out_odd_dev, const void *in_even_dev, void *stream);
+/* nrhs applications of one block sharing each link load: out_parity 0 -> D_eo, 1 -> D_oe;
+ * field j at in_dev + j*stride_bytes (same for out).  1 <= nrhs <= 64; stride a multiple of
+ * 16 bytes and >= stg_field_bytes. */
+stg_status stg_dslash_multi(const stg_gauge *g, int32_t out_parity, int32_t nrhs, void *out_dev, const void *in_dev,
+                            size_t stride_bytes, void *stream);
+
+/* out_even = (m^2 + shift) in_even - D_eo D_oe in_even  (Eq. shift_eo), tmp_odd a caller buffer
+ * of stg_field_bytes.  If pq_dev != NULL, *pq_dev (one device double) receives Re<in, out>,
+ * reduced in FP64 in a fixed order.  The reduction uses a scratch buffer owned by the gauge
+ * handle: concurrent stg_normal_op calls on one gauge in different streams race on it. */
+stg_status stg_normal_op(const stg_gauge *g, double mass, double shift, void *out_even_dev, const void *in_even_dev,
+                         void *tmp_odd_dev, double *pq_dev, void *stream);
+
+/* ---- multi-shift CG (Sec. 2, Eq. shift_eo) ------------------------------------------------- */
+
+typedef struct {
+    int32_t nshift;          /* 1 .. 32 poles                                                     */
+    const double *shifts;    /* host [nshift], sigma_i >= 0                                        */
+    double mass;             /* m                                                                 */
+    double tol;              /* target relative FP64 true residual |b - A_i x_i| / |b| per shift   */
+    int32_t max_iter;        /* iteration cap of each phase (> 0)                                 */
+    double inner_tol;        /* mixed solves: stopping residual of the inner multi-shift phase
+                                (0 -> 1e-6 for F32 gauges, 2e-3 for BF16/F16 gauges)             */
+    double reliable_delta;   /* mixed solves: reliable update once |r| fell by this factor since
+                                the last one (0 -> 0.1)                                           */
+    int32_t log_rows;        /* optional: rows of scalar_log to fill (0 = none)                    */
+    double *scalar_log;      /* host [log_rows][2 + nshift]: alpha_k, beta_k, zeta_i^{k+1} of the
+                                first multi-shift iterations of system 0                         */
+} stg_mscg_params;
+
+typedef struct {
+    int32_t iters;            /* multi-shift iterations                                            */
+    int32_t reliable_updates; /* FP64 true-residual recomputations during refinement               */
+    int32_t refine_iters;     /* largest refinement iteration count over the shifts                */
+    double *true_resid;       /* host [nshift] (may be NULL): final FP64 |b - A_i x_i| / |b|       */
+    int32_t *shift_iters;     /* host [nshift] (may be NULL): multi-shift iteration at which each
+                                 shift stopped                                                    */
+} stg_mscg_stats;
+
+/* Solves A_{sigma_i} x_i = b for every shift.
+ *   g_f64    F64 gauge (RECON18 or RECON12): true residuals, reliable updates, refinement.
+ *   g_inner  NULL -> pure FP64 solve.  Otherwise an F32/BF16/F16 gauge on the same lattice:
+ *            multi-shift phase in that precision (FP32 vectors, FP64 scalars and reductions),
+ *            then each shift above tol is refined by CG with FP64 reliable updates.
+ *   b_c128_dev          canonical complex128 [Vh][3] even-site source (device).
+ *   x_c128_dev[nshift]  canonical complex128 [Vh][3] outputs (device), may not alias b.
+ * Synchronises `stream` before returning.  STG_ERR_NOCONV if a shift is still above tol
+ * after max_iter (stats filled, x holds the last iterate). */
+stg_status stg_mscg_solve(const stg_gauge *g_f64, const stg_gauge *g_inner, const stg_mscg_params *params,
+                          const void *b_c128_dev, void *const *x_c128_dev, stg_mscg_stats *stats, void *stream);
+
+/* One lattice of a batched solve: nrhs sources (pseudofermions) on the same gauge. */
+typedef struct {
+    const stg_gauge *g_f64;
+    const stg_gauge *g_inner;  /* all instances of a batch are mixed, or none is                  */
+    int32_t nrhs;              /* 1 .. 16                                                          */
+    const void *const *b;      /* [nrhs] canonical complex128 sources (device)                     */
+    void *const *x;            /* [nrhs * nshift] outputs, x[r * nshift + i] (device)              */
+    stg_mscg_stats *stats;     /* [nrhs] (may be NULL)                                             */
+} stg_instance;
+
+/* Solves every (instance, rhs, shift) system of a batch of lattices of different sizes
+ * together: each iteration launches one set of kernels for the whole batch, link loads are
+ * shared by the rhs of an instance, converged systems are masked out.  Shifts, mass, tol
+ * from params (shared).  1 <= ninst <= 16. */
+stg_status stg_mscg_solve_batched(int32_t ninst, const stg_instance *inst, const stg_mscg_params *params,
+                                  void *stream);
+
+/* ---- fermion force ------------------------------------------------------------------------------ */
+
+/* For S = sum_i r_i Re(b^dag x_i) with x_i = A_{sigma_i}^{-1} b (the solutions passed in),
+ * computes per link (z, mu), with y_i = D_oe x_i and u = u_mu(z):
+ *   W = + sum_i r_i u y_i(z+mu) x_i(z)^dag   (z even)
+ *   W = - sum_i r_i u x_i(z+mu) y_i(z)^dag   (z odd)
+ * so that dS = Re tr(dU W) under a change dU of that link, and writes
+ *   kind 0: F = TA(U W) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6,  Z = U W   (dS/deps = tr(X F) along
+ *           U -> exp(eps X) U, X in su(3)), or
+ *   kind 1: W^dag = dS/dRe U + i dS/dIm U.
+ * Accumulated in FP64.  x_c128_dev[nshift]: canonical complex128 even fields (device);
+ * out_c128_dev: canonical complex128 [4][V][3][3] (device).  g_f64 must be an F64 gauge. */
+stg_status stg_fermion_force(const stg_gauge *g_f64, int32_t nshift, const double *residues,
+                             const void *const *x_c128_dev, void *out_c128_dev, int32_t kind, void *stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* STG_H */

@@ -1,0 +1,271 @@
+"""Python binding of the C ABI (include/stg.h) on torch tensors.
+
+Argument marshalling only: every arithmetic step runs in libstg's CUDA
+kernels.  Torch supplies device memory and the current CUDA stream.
+
+Tensors:
+  links      complex128 [4, V, 3, 3] (or [4, Lt, Lz, Ly, Lx, 3, 3]) on the GPU
+  fields     complex128 [Vh, 3] canonical, half-index order of one parity
+  internal   float64 [6*Vh] (F64) or float32 [6*Vh] (F32) in the library's layout
+A host (CPU) tensor passed where a canonical field is expected is copied to the
+device first and results are copied back: that is the end-to-end path.
+"""
+from __future__ import annotations
+
+import ctypes
+from typing import Sequence
+
+import torch
+
+from .lib import (PREC, STG_ERR_NOCONV, STG_F32, STG_F64, STG_RECON12, STG_RECON18, Instance, MscgParams,
+                  MscgStats, check, lib)
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
+    return ctypes.c_void_p(t.data_ptr())
+
+
+def _dev(t: torch.Tensor, dtype=torch.complex128) -> torch.Tensor:
+    if not t.is_cuda:
+        t = t.to("cuda", non_blocking=True)
+    if t.dtype != dtype:
+        raise TypeError(f"expected {dtype}, got {t.dtype}")
+    return t.contiguous()
+
+
+class Lattice:
+    """Lattice geometry: dims (Lx, Ly, Lz, Lt), all even; antiperiodic in time by default."""
+
+    def __init__(self, dims: Sequence[int], antiperiodic: bool = True):
+        self.dims = tuple(int(d) for d in dims)
+        arr = (ctypes.c_int32 * 4)(*self.dims)
+        h = ctypes.c_void_p()
+        check(lib().stg_lattice_create(arr, int(bool(antiperiodic)), ctypes.byref(h)), "stg_lattice_create")
+        self._h = h
+        self.antiperiodic = bool(antiperiodic)
+        self.V = int(lib().stg_lattice_sites(h, -1))
+        self.Vh = int(lib().stg_lattice_sites(h, 0))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def field_bytes(self, prec: str) -> int:
+        return int(lib().stg_field_bytes(self._h, PREC[prec]))
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().stg_lattice_destroy(h)
+            self._h = None
+
+
+class Gauge:
+    """Library-owned copy of the links at precision prec ('f64', 'f32', 'bf16', 'f16'),
+    18-real or 12-real (recon=12: rows 1, 2 stored, row 3 rebuilt)."""
+
+    def __init__(self, lattice: Lattice, links: torch.Tensor, prec: str = "f64", recon: int = 18, stream=None):
+        links = _dev(links).reshape(4, lattice.V, 3, 3)
+        h = ctypes.c_void_p()
+        check(lib().stg_gauge_create(lattice.handle, _ptr(links), PREC[prec],
+                                     STG_RECON12 if recon == 12 else STG_RECON18, _stream(stream), ctypes.byref(h)),
+              "stg_gauge_create")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        self._h = h
+        self.lattice = lattice
+        self.prec = prec
+        self.recon = recon
+        self.vec_prec = "f64" if prec == "f64" else "f32"
+        self.nbytes = int(lib().stg_gauge_bytes(h))
+
+    @property
+    def handle(self):
+        return self._h
+
+    def new_field(self, n: int | None = None) -> torch.Tensor:
+        """Uninitialised internal-layout field(s) at this gauge's vector precision."""
+        dt = torch.float64 if self.vec_prec == "f64" else torch.float32
+        shape = (6 * self.lattice.Vh,) if n is None else (n, 6 * self.lattice.Vh)
+        return torch.empty(shape, dtype=dt, device="cuda")
+
+    def __del__(self):
+        h = getattr(self, "_h", None)
+        if h is not None and h.value:
+            lib().stg_gauge_destroy(h)
+            self._h = None
+
+
+# ------------------------------------------------------------------ fields
+
+def pack(lattice: Lattice, canon: torch.Tensor, prec: str = "f64", stream=None) -> torch.Tensor:
+    """Canonical complex128 [Vh, 3] -> internal layout (float64 or float32 [6*Vh])."""
+    canon = _dev(canon).reshape(lattice.Vh, 3)
+    dt = torch.float64 if prec == "f64" else torch.float32
+    out = torch.empty(6 * lattice.Vh, dtype=dt, device="cuda")
+    check(lib().stg_field_pack(lattice.handle, PREC[prec], _ptr(canon), _ptr(out), _stream(stream)), "stg_field_pack")
+    return out
+
+
+def unpack(lattice: Lattice, internal: torch.Tensor, stream=None) -> torch.Tensor:
+    prec = "f64" if internal.dtype == torch.float64 else "f32"
+    out = torch.empty((lattice.Vh, 3), dtype=torch.complex128, device="cuda")
+    check(lib().stg_field_unpack(lattice.handle, PREC[prec], _ptr(internal), _ptr(out), _stream(stream)),
+          "stg_field_unpack")
+    return out
+
+
+# ------------------------------------------------------------------ operator (internal layout)
+
+def dslash_eo_(gauge: Gauge, out: torch.Tensor, inp: torch.Tensor, stream=None) -> torch.Tensor:
+    check(lib().stg_dslash_eo(gauge.handle, _ptr(out), _ptr(inp), _stream(stream)), "stg_dslash_eo")
+    return out
+
+
+def dslash_oe_(gauge: Gauge, out: torch.Tensor, inp: torch.Tensor, stream=None) -> torch.Tensor:
+    check(lib().stg_dslash_oe(gauge.handle, _ptr(out), _ptr(inp), _stream(stream)), "stg_dslash_oe")
+    return out
+
+
+def dslash_multi_(gauge: Gauge, out_parity: int, out: torch.Tensor, inp: torch.Tensor, stream=None) -> torch.Tensor:
+    """out[j] = D inp[j] for each row j (2-D internal tensors), link loads shared across rows."""
+    n = inp.shape[0]
+    stride = inp.stride(0) * inp.element_size()
+    if out.stride(0) != inp.stride(0):
+        raise ValueError("out and inp need the same row stride")
+    check(lib().stg_dslash_multi(gauge.handle, int(out_parity), int(n), _ptr(out), _ptr(inp), stride, _stream(stream)),
+          "stg_dslash_multi")
+    return out
+
+
+def normal_op_(gauge: Gauge, mass: float, shift: float, out: torch.Tensor, inp: torch.Tensor, tmp: torch.Tensor,
+               pq: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    check(lib().stg_normal_op(gauge.handle, float(mass), float(shift), _ptr(out), _ptr(inp), _ptr(tmp),
+                              _ptr(pq) if pq is not None else None, _stream(stream)), "stg_normal_op")
+    return out
+
+
+# ------------------------------------------------------------------ operator (canonical layout)
+
+def _canon_apply(gauge: Gauge, canon: torch.Tensor, fn) -> torch.Tensor:
+    host = not canon.is_cuda
+    lat = gauge.lattice
+    x = pack(lat, canon, gauge.vec_prec)
+    y = fn(x)
+    out = unpack(lat, y)
+    return out.cpu() if host else out
+
+
+def dslash_eo(gauge: Gauge, psi_odd: torch.Tensor) -> torch.Tensor:
+    """D_eo psi_odd on canonical complex128 [Vh, 3] fields (host or device)."""
+    return _canon_apply(gauge, psi_odd, lambda x: dslash_eo_(gauge, torch.empty_like(x), x))
+
+
+def dslash_oe(gauge: Gauge, psi_even: torch.Tensor) -> torch.Tensor:
+    """D_oe psi_even on canonical complex128 [Vh, 3] fields (host or device)."""
+    return _canon_apply(gauge, psi_even, lambda x: dslash_oe_(gauge, torch.empty_like(x), x))
+
+
+def normal_op(gauge: Gauge, mass: float, shift: float, psi_even: torch.Tensor) -> torch.Tensor:
+    """(m^2 + shift) psi - D_eo D_oe psi on canonical complex128 [Vh, 3] fields."""
+    return _canon_apply(gauge, psi_even,
+                        lambda x: normal_op_(gauge, mass, shift, torch.empty_like(x), x, torch.empty_like(x)))
+
+
+# ------------------------------------------------------------------ multi-shift CG
+
+def _params(shifts, mass, tol, max_iter, inner_tol, reliable_delta, log_rows):
+    sh = (ctypes.c_double * len(shifts))(*[float(s) for s in shifts])
+    log = (ctypes.c_double * max(1, log_rows * (2 + len(shifts))))()
+    p = MscgParams(len(shifts), ctypes.cast(sh, ctypes.POINTER(ctypes.c_double)), float(mass), float(tol),
+                   int(max_iter), float(inner_tol), float(reliable_delta), int(log_rows),
+                   ctypes.cast(log, ctypes.POINTER(ctypes.c_double)) if log_rows > 0 else None)
+    return p, sh, log
+
+
+def _stats(nshift):
+    tr = (ctypes.c_double * nshift)()
+    si = (ctypes.c_int32 * nshift)()
+    st = MscgStats(0, 0, 0, ctypes.cast(tr, ctypes.POINTER(ctypes.c_double)),
+                   ctypes.cast(si, ctypes.POINTER(ctypes.c_int32)))
+    return st, tr, si
+
+
+def _stats_dict(st, tr, si):
+    return dict(iters=st.iters, reliable_updates=st.reliable_updates, refine_iters=st.refine_iters,
+                true_resid=list(tr), shift_iters=list(si))
+
+
+def mscg(g_f64: Gauge, b: torch.Tensor, shifts, mass: float, tol: float = 1e-10, g_inner: Gauge | None = None,
+         max_iter: int = 20000, inner_tol: float = 0.0, reliable_delta: float = 0.0, log_rows: int = 0,
+         allow_noconv: bool = False, out: torch.Tensor | None = None, stream=None):
+    """Multi-shift CG: x_i = (m^2 + sigma_i - D_eo D_oe)^-1 b.  b canonical complex128 [Vh, 3].
+    Returns (x [nshift, Vh, 3] complex128, stats dict)."""
+    host = not b.is_cuda
+    bd = _dev(b).reshape(g_f64.lattice.Vh, 3)
+    ns = len(shifts)
+    x = out if out is not None else torch.empty((ns, g_f64.lattice.Vh, 3), dtype=torch.complex128, device="cuda")
+    xp = (ctypes.c_void_p * ns)(*[x[i].data_ptr() for i in range(ns)])
+    p, _sh, log = _params(shifts, mass, tol, max_iter, inner_tol, reliable_delta, log_rows)
+    st, tr, si = _stats(ns)
+    rc = lib().stg_mscg_solve(g_f64.handle, g_inner.handle if g_inner is not None else None, ctypes.byref(p), _ptr(bd),
+                              ctypes.cast(xp, ctypes.POINTER(ctypes.c_void_p)), ctypes.byref(st), _stream(stream))
+    check(rc, "stg_mscg_solve", allow=(STG_ERR_NOCONV,) if allow_noconv else ())
+    stats = _stats_dict(st, tr, si)
+    stats["status"] = rc
+    if log_rows > 0:
+        import numpy as np
+        stats["scalar_log"] = np.array(log[:]).reshape(log_rows, 2 + ns)[:min(log_rows, st.iters)]
+    return (x.cpu() if host else x), stats
+
+
+def mscg_batched(instances, shifts, mass: float, tol: float = 1e-10, max_iter: int = 20000, inner_tol: float = 0.0,
+                 reliable_delta: float = 0.0, stream=None):
+    """instances: list of (g_f64, g_inner or None, [b_r canonical [Vh,3] cuda tensors]).
+    Returns list of (x [nrhs, nshift, Vh, 3], [stats per rhs])."""
+    ns = len(shifts)
+    keep = []
+    arr = (Instance * len(instances))()
+    outs = []
+    for k, (gf, gi, bs) in enumerate(instances):
+        bs = [_dev(b).reshape(gf.lattice.Vh, 3) for b in bs]
+        x = torch.empty((len(bs), ns, gf.lattice.Vh, 3), dtype=torch.complex128, device="cuda")
+        bp = (ctypes.c_void_p * len(bs))(*[t.data_ptr() for t in bs])
+        xp = (ctypes.c_void_p * (len(bs) * ns))(*[x[r, i].data_ptr() for r in range(len(bs)) for i in range(ns)])
+        sts = (MscgStats * len(bs))()
+        bufs = []
+        for r in range(len(bs)):
+            st, tr, si = _stats(ns)
+            sts[r] = st
+            bufs.append((tr, si))
+        arr[k] = Instance(gf.handle, gi.handle if gi is not None else None, len(bs),
+                          ctypes.cast(bp, ctypes.POINTER(ctypes.c_void_p)),
+                          ctypes.cast(xp, ctypes.POINTER(ctypes.c_void_p)),
+                          ctypes.cast(sts, ctypes.POINTER(MscgStats)))
+        keep += [bs, bp, xp, sts, bufs]
+        outs.append((x, sts, bufs))
+    p, _sh, _log = _params(shifts, mass, tol, max_iter, inner_tol, reliable_delta, 0)
+    check(lib().stg_mscg_solve_batched(len(instances), arr, ctypes.byref(p), _stream(stream)), "stg_mscg_solve_batched")
+    res = []
+    for x, sts, bufs in outs:
+        res.append((x, [_stats_dict(sts[r], bufs[r][0], bufs[r][1]) for r in range(len(bufs))]))
+    return res
+
+
+# ------------------------------------------------------------------ fermion force
+
+def fermion_force(g_f64: Gauge, residues, x: torch.Tensor, kind: int = 0, stream=None) -> torch.Tensor:
+    """Per-link force [4, V, 3, 3] complex128 from solutions x [nshift, Vh, 3]:
+    kind 0 -> TA(U W) (Lie-algebra force), kind 1 -> W^dag (gradient wrt link entries)."""
+    ns = len(residues)
+    xd = _dev(x).reshape(ns, g_f64.lattice.Vh, 3)
+    res = (ctypes.c_double * ns)(*[float(r) for r in residues])
+    xp = (ctypes.c_void_p * ns)(*[xd[i].data_ptr() for i in range(ns)])
+    out = torch.empty((4, g_f64.lattice.V, 3, 3), dtype=torch.complex128, device="cuda")
+    check(lib().stg_fermion_force(g_f64.handle, ns, res, ctypes.cast(xp, ctypes.POINTER(ctypes.c_void_p)), _ptr(out),
+                                  int(kind), _stream(stream)), "stg_fermion_force")
+    return out

@@ -1,0 +1,7 @@
+// D_eo / D_oe instantiations for FP32 links (18-real and 12-real) on FP32 fields.
+#include "stg_common.h"
+
+namespace stg {
+cudaError_t launch_dslash_f32r18(const DArgs &a, int mode, cudaStream_t st) { return launch_dslash_t<LinkF32R18>(a, mode, st); }
+cudaError_t launch_dslash_f32r12(const DArgs &a, int mode, cudaStream_t st) { return launch_dslash_t<LinkF32R12>(a, mode, st); }
+}  // namespace stg

@@ -1,0 +1,196 @@
+// force.cu -- fermion force of the pseudofermion action S = sum_i r_i Re(b^dag x_i),
+// x_i = (m^2 + sigma_i - D_eo D_oe)^-1 b: the adjoint of D_eo / D_oe over the multi-shift
+// solutions (the fermionic MD force of Sec. 4).
+//
+// dS = -sum_i r_i x_i^dag dA_i x_i with dA_i = -(dD_eo D_oe + D_eo dD_oe) and D_eo = -D_oe^dag,
+// so with y_i = D_oe x_i the change of one link U_mu(z) enters as dS = Re tr(dU W):
+//     z even:  W = + sum_i r_i u_mu(z) y_i(z+mu) x_i(z)^dag
+//     z odd :  W = - sum_i r_i u_mu(z) x_i(z+mu) y_i(z)^dag
+// Output kind 0: F = TA(U W) (traceless anti-Hermitian; dS/deps = tr(X F) along U -> exp(eps X) U);
+// kind 1: W^dag (dS/dRe U + i dS/dIm U).
+//
+// Work split: y_i = D_oe x_i for all shifts by the multi-rhs D kernel (link loads shared);
+// then one thread per site z and direction mu gathers its rank-nshift sum of outer products in
+// FP64 registers (no atomics: every link is owned by exactly one thread).
+#include <cstring>
+#include <vector>
+
+#include "stg_common.h"
+
+namespace stg {
+
+struct ForceArgs {
+    Geom g;
+    const void *links;
+    const void *x[kMaxShifts];  // even FP64 internal fields
+    const void *y[kMaxShifts];  // odd FP64 internal fields
+    double res[kMaxShifts];
+    int nshift;
+    int kind;
+    double2 *out;  // canonical [4][V][3][3]
+};
+
+constexpr int kForceBlock = 128;
+
+template <typename LinkT>
+__global__ void __launch_bounds__(kForceBlock) k_force(const __grid_constant__ ForceArgs a)
+{
+    const int par = blockIdx.y;
+    const int h = blockIdx.x * kForceBlock + threadIdx.x;
+    const int Vh = a.g.Vh;
+    if (h >= Vh) return;
+    const Site s = site_of(a.g, par, h);
+    const long long V = 2LL * Vh;
+    for (int mu = 0; mu < 4; ++mu) {
+        const Hop hp = hop_of(a.g, s, mu);
+        const double u = (double)hp.sf;  // u_mu(z) of the link (z, mu)
+        cx<double> W[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) W[r][c] = cx<double>{0.0, 0.0};
+        for (int i = 0; i < a.nshift; ++i) {
+            cx<double> f[3], g[3];  // W += w * f g^dag
+            double w;
+            if (par == 0) {
+                Field<double>::load(a.y[i], Vh, hp.hf, f);
+                Field<double>::load(a.x[i], Vh, h, g);
+                w = a.res[i] * u;
+            } else {
+                Field<double>::load(a.x[i], Vh, hp.hf, f);
+                Field<double>::load(a.y[i], Vh, h, g);
+                w = -a.res[i] * u;
+            }
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                const cx<double> fr = cx<double>{w * f[r].re, w * f[r].im};
+#pragma unroll
+                for (int c = 0; c < 3; ++c) cmac_conj(W[r][c], g[c], fr);  // W_rc += fr * conj(g_c)
+            }
+        }
+        double2 *o = a.out + ((long long)mu * V + s.i) * 9;
+        if (a.kind == 1) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) o[r * 3 + c] = make_double2(W[c][r].re, -W[c][r].im);
+            continue;
+        }
+        cx<double> U[3][3];
+        LinkT::load(link_block<LinkT>(a.links, Vh, mu, par), Vh, h, U);
+        cx<double> Z[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cx<double> z = cx<double>{0.0, 0.0};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) cmac(z, U[r][k], W[k][c]);
+                Z[r][c] = z;
+            }
+        // TA(Z) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6: the trace of Z - Z^dag is 2i Im tr Z
+        const double im_tr = (Z[0][0].im + Z[1][1].im + Z[2][2].im) / 3.0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double re = 0.5 * (Z[r][c].re - Z[c][r].re);
+                double im = 0.5 * (Z[r][c].im + Z[c][r].im);
+                if (r == c) im -= im_tr;
+                o[r * 3 + c] = make_double2(re, im);
+            }
+    }
+}
+
+template <typename R>
+__global__ void k_pack_many(int Vh, const double2 *const *__restrict__ canon, void *const *__restrict__ out)
+{
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    const double2 *src = canon[blockIdx.y];
+    cx<R> v[3];
+    for (int c = 0; c < 3; ++c) {
+        double2 d = src[(size_t)h * 3 + c];
+        v[c] = cx<R>{(R)d.x, (R)d.y};
+    }
+    Field<R>::store(out[blockIdx.y], Vh, h, v);
+}
+
+}  // namespace stg
+
+using namespace stg;
+
+extern "C" stg_status stg_fermion_force(const stg_gauge *g, int32_t nshift, const double *residues,
+                                        const void *const *x_c128_dev, void *out_c128_dev, int32_t kind, void *stream)
+{
+    if (!g || !residues || !x_c128_dev || !out_c128_dev) return set_error(STG_ERR_ARG, "stg_fermion_force: null pointer");
+    if (!kind_is_f64(g->kind)) return set_error(STG_ERR_ARG, "stg_fermion_force: needs an F64 gauge");
+    if (nshift < 1 || nshift > kMaxShifts) return set_error(STG_ERR_ARG, "stg_fermion_force: nshift must be in 1..32");
+    if (kind != 0 && kind != 1) return set_error(STG_ERR_ARG, "stg_fermion_force: kind must be 0 or 1");
+    for (int i = 0; i < nshift; ++i)
+        if (!x_c128_dev[i] || (reinterpret_cast<uintptr_t>(x_c128_dev[i]) & 15))
+            return set_error(STG_ERR_ARG, "stg_fermion_force: x must be non-null and 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(out_c128_dev) & 15)
+        return set_error(STG_ERR_ARG, "stg_fermion_force: out must be 16-byte aligned");
+
+    cudaStream_t st = (cudaStream_t)stream;
+    const int Vh = g->g.Vh;
+    const size_t fb = (size_t)Vh * 48;
+    char *ws = nullptr;
+    const size_t ptr_bytes = 2 * kMaxShifts * sizeof(void *);
+    STG_CUDA_TRY(cudaMallocAsync((void **)&ws, 2 * nshift * fb + ptr_bytes, st));
+    struct Free {
+        void *p;
+        cudaStream_t s;
+        ~Free() { cudaFreeAsync(p, s); }
+    } fr{ws, st};
+
+    std::vector<const void *> ptrs(2 * kMaxShifts, nullptr);
+    ForceArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = g->g;
+    a.links = g->links;
+    a.nshift = nshift;
+    a.kind = kind;
+    a.out = static_cast<double2 *>(out_c128_dev);
+    for (int i = 0; i < nshift; ++i) {
+        a.x[i] = ws + (size_t)i * fb;
+        a.y[i] = ws + (size_t)(nshift + i) * fb;
+        a.res[i] = residues[i];
+        ptrs[i] = x_c128_dev[i];
+        ptrs[kMaxShifts + i] = a.x[i];
+    }
+    void **d_ptrs = reinterpret_cast<void **>(ws + 2 * nshift * fb);
+    STG_CUDA_TRY(cudaMemcpyAsync(d_ptrs, ptrs.data(), ptr_bytes, cudaMemcpyHostToDevice, st));
+    k_pack_many<double><<<dim3((Vh + 255) / 256, nshift), 256, 0, st>>>(
+        Vh, reinterpret_cast<const double2 *const *>(d_ptrs), d_ptrs + kMaxShifts);
+    STG_CUDA_TRY(cudaGetLastError());
+
+    // y_i = D_oe x_i, link loads shared across up to kMaxRhs shifts per group
+    for (int base = 0; base < nshift;) {
+        DArgs d;
+        memset(&d, 0, sizeof(d));
+        d.out_par = 1;
+        int ng = 0;
+        while (ng < kMaxGroups && base < nshift) {
+            DGroup &G = d.grp[ng++];
+            G.g = g->g;
+            G.links = g->links;
+            G.nrhs = (nshift - base) < kMaxRhs ? (nshift - base) : kMaxRhs;
+            for (int j = 0; j < G.nrhs; ++j) {
+                G.in[j] = a.x[base + j];
+                G.out[j] = const_cast<void *>(a.y[base + j]);
+            }
+            base += G.nrhs;
+        }
+        d.ngroups = ng;
+        STG_CUDA_TRY(launch_dslash(g->kind, d, 0, st));
+    }
+    dim3 grid((Vh + kForceBlock - 1) / kForceBlock, 2);
+    if (g->kind == kF64R18)
+        k_force<LinkF64R18><<<grid, kForceBlock, 0, st>>>(a);
+    else
+        k_force<LinkF64R12><<<grid, kForceBlock, 0, st>>>(a);
+    STG_CUDA_TRY(cudaGetLastError());
+    return STG_OK;
+}

@@ -1,0 +1,979 @@
+// solver.cu -- multi-shift CG for (m^2 - D_eo D_oe + sigma_i) x_i = b (Sec. 2, Eq. shift_eo),
+// batched over lattices, right-hand sides and shifts, with an optional low-precision inner
+// solve and FP64 reliable updates.
+//
+// A "system" is one right-hand side b with its shifts.  The solve runs in two phases.
+//
+// Phase 1 (multi-shift CG, inner precision R = double or float).  One Krylov space for all
+// shifts of a system: base shift sigma_0 = min sigma_i, relative shifts s_i = sigma_i - sigma_0.
+// Per iteration, for every system of the batch at once:
+//   D_oe p -> t ;  q = (m^2 + sigma_0) p - D_eo t  with the partial sums of Re<p,q>   (k_dslash)
+//   alpha = <r,r>/Re<p,q>;  zeta_i' and alpha_i = alpha zeta_i'/zeta_i  (FP64)          (k_alpha)
+//   r -= alpha q  with the partial sums of |r|^2                                        (k_update_r)
+//   beta = |r|^2_new/|r|^2_old;  beta_i = beta (zeta_i'/zeta_i)^2;  per-shift stop test
+//   zeta_i' |r| <= tol |b|;  history rotation  (FP64)                                    (k_beta)
+//   x_i += alpha_i p_i ;  p_i = zeta_i' r + beta_i p_i   (one pass over all live shifts)  (k_update_shifts)
+// The base direction p is the p_i of the base shift (zeta = 1, alpha_0 = alpha, beta_0 = beta).
+// Reductions are FP64 per block, summed in a fixed order: results do not depend on timing.
+// Iterations are captured into a CUDA graph in chunks; converged systems skip all work, so the
+// host only looks at convergence flags between chunks.
+//
+// Phase 2 (per-shift refinement, FP64 reliable updates).  Every (system, shift) pair gets its
+// FP64 true residual r = b - A_i x_i.  Pairs above tol run CG on A_i in the inner precision
+// (the phase-1 kernels with one shift), accumulating a correction y; whenever the iterated
+// residual has fallen by reliable_delta, or reached tol, the host folds x += y in FP64 and
+// recomputes r = b - A_i x in FP64 (a reliable update), continuing from the new r with the
+// same search direction.  A pair stops when its FP64 true residual is <= tol |b|.
+// For a pure-FP64 solve (no inner gauge) phase 1 runs to tol and phase 2 only checks.
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <vector>
+
+#include "stg_common.h"
+
+namespace stg {
+
+constexpr int kVecBlock = 256;
+
+struct SysScal {
+    double rr, alpha, alpha_old, beta_old, bnorm2, tol2, tol2_true, rr_last, delta2, coef;
+    double zeta[kMaxShifts], zeta_old[kMaxShifts], zeta_new[kMaxShifts], s[kMaxShifts];
+    double cx[kMaxShifts], cr[kMaxShifts], cp[kMaxShifts];
+    int upd_x[kMaxShifts], upd_p[kMaxShifts], active[kMaxShifts], shift_iters[kMaxShifts];
+    int nshift, i0, running, iters, max_iter, nactive, phase2, reliable;
+};
+
+struct SysVecs {
+    void *r, *q, *t;                         // inner precision: r, q even; t odd
+    void *x[kMaxShifts], *p[kMaxShifts];     // inner precision
+    void *xhi, *rhi, *t64, *b64;             // phase 2: FP64 solution, residual, odd temp, source
+    const double2 *bcanon;                   // canonical source (phase 1)
+    double *part_d, *part_v, *part_v2;       // partial sums (dslash blocks / vector blocks)
+    int Vh, nblk_d, nblk_v, pad;
+};
+
+// ------------------------------------------------------------------ vector kernels
+
+template <typename R>
+__device__ __forceinline__ double norm2_site(const cx<R> v[3])
+{
+    double s = 0.0;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) s += (double)v[c].re * (double)v[c].re + (double)v[c].im * (double)v[c].im;
+    return s;
+}
+
+// phase-1 start: r = p_i = b (rounded to R), x_i = 0; partials |r|^2 (R) and |b|^2 (FP64)
+template <typename R>
+__global__ void __launch_bounds__(kVecBlock) k_p1_init(const SysVecs *__restrict__ sv, int nshift)
+{
+    const SysVecs &V = sv[blockIdx.y];
+    if ((int)(blockIdx.x * kVecBlock) >= V.Vh) return;
+    int h = blockIdx.x * kVecBlock + threadIdx.x;
+    double pr = 0.0, pb = 0.0;
+    if (h < V.Vh) {
+        cx<R> v[3], z[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double2 d = V.bcanon[(size_t)h * 3 + c];
+            pb += d.x * d.x + d.y * d.y;
+            v[c] = cx<R>{(R)d.x, (R)d.y};
+            z[c] = cx<R>{R(0), R(0)};
+        }
+        pr = norm2_site(v);
+        Field<R>::store(V.r, V.Vh, h, v);
+        for (int i = 0; i < nshift; ++i) {
+            Field<R>::store(V.p[i], V.Vh, h, v);
+            Field<R>::store(V.x[i], V.Vh, h, z);
+        }
+        if (V.b64) {
+            cx<double> w[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double2 d = V.bcanon[(size_t)h * 3 + c];
+                w[c] = cx<double>{d.x, d.y};
+            }
+            Field<double>::store(V.b64, V.Vh, h, w);
+        }
+    }
+    __shared__ double sh[32];
+    double t = block_sum(pr, sh);
+    if (threadIdx.x == 0) V.part_v[blockIdx.x] = t;
+    t = block_sum(pb, sh);
+    if (threadIdx.x == 0) V.part_v2[blockIdx.x] = t;
+}
+
+// r -= alpha q, partial |r|^2
+template <typename R>
+__global__ void __launch_bounds__(kVecBlock) k_update_r(const SysScal *__restrict__ sc, const SysVecs *__restrict__ sv)
+{
+    const SysScal &S = sc[blockIdx.y];
+    const SysVecs &V = sv[blockIdx.y];
+    if (!S.running || (int)(blockIdx.x * kVecBlock) >= V.Vh) return;
+    int h = blockIdx.x * kVecBlock + threadIdx.x;
+    double pr = 0.0;
+    if (h < V.Vh) {
+        const R a = (R)S.alpha;
+        cx<R> r[3], q[3];
+        Field<R>::load_rw(V.r, V.Vh, h, r);
+        Field<R>::load_rw(V.q, V.Vh, h, q);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = cx<R>{fma(-a, q[c].re, r[c].re), fma(-a, q[c].im, r[c].im)};
+        Field<R>::store(V.r, V.Vh, h, r);
+        pr = norm2_site(r);
+    }
+    __shared__ double sh[32];
+    double t = block_sum(pr, sh);
+    if (threadIdx.x == 0) V.part_v[blockIdx.x] = t;
+}
+
+// x_i += cx_i p_i ; p_i = cr_i r + cp_i p_i  for the shifts flagged by k_beta
+template <typename R>
+__global__ void __launch_bounds__(kVecBlock) k_update_shifts(const SysScal *__restrict__ sc,
+                                                              const SysVecs *__restrict__ sv)
+{
+    const SysScal &S = sc[blockIdx.y];
+    const SysVecs &V = sv[blockIdx.y];
+    if (!S.running || (int)(blockIdx.x * kVecBlock) >= V.Vh) return;
+    __shared__ R s_cx[kMaxShifts], s_cr[kMaxShifts], s_cp[kMaxShifts];
+    __shared__ int s_ux[kMaxShifts], s_up[kMaxShifts];
+    const int ns = S.nshift;
+    if (threadIdx.x < ns) {
+        s_cx[threadIdx.x] = (R)S.cx[threadIdx.x];
+        s_cr[threadIdx.x] = (R)S.cr[threadIdx.x];
+        s_cp[threadIdx.x] = (R)S.cp[threadIdx.x];
+        s_ux[threadIdx.x] = S.upd_x[threadIdx.x];
+        s_up[threadIdx.x] = S.upd_p[threadIdx.x];
+    }
+    __syncthreads();
+    int h = blockIdx.x * kVecBlock + threadIdx.x;
+    if (h >= V.Vh) return;
+    cx<R> r[3];
+    Field<R>::load_rw(V.r, V.Vh, h, r);
+    for (int i = 0; i < ns; ++i) {
+        const int ux = s_ux[i], up = s_up[i];
+        if (!ux && !up) continue;
+        cx<R> p[3];
+        Field<R>::load_rw(V.p[i], V.Vh, h, p);
+        if (ux) {
+            cx<R> x[3];
+            Field<R>::load_rw(V.x[i], V.Vh, h, x);
+            const R a = s_cx[i];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) x[c] = cx<R>{fma(a, p[c].re, x[c].re), fma(a, p[c].im, x[c].im)};
+            Field<R>::store(V.x[i], V.Vh, h, x);
+        }
+        if (up) {
+            const R zr = s_cr[i], b = s_cp[i];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) p[c] = cx<R>{fma(zr, r[c].re, b * p[c].re), fma(zr, r[c].im, b * p[c].im)};
+            Field<R>::store(V.p[i], V.Vh, h, p);
+        }
+    }
+}
+
+// ------------------------------------------------------------------ scalar kernels (one warp per system)
+
+__device__ __forceinline__ double warp_sum_strided(const double *a, int n)
+{
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += 32) s += a[k];
+    return warp_sum(s);
+}
+
+__device__ __forceinline__ int warp_sum_int(int v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// phase-1 scalar start
+__global__ void k_p1_init_scal(SysScal *sc, const SysVecs *sv, int *done, double tol)
+{
+    SysScal &S = sc[blockIdx.x];
+    const SysVecs &V = sv[blockIdx.x];
+    const double rr = warp_sum_strided(V.part_v, V.nblk_v);
+    const double bb = warp_sum_strided(V.part_v2, V.nblk_v);
+    for (int i = threadIdx.x; i < S.nshift; i += 32) {
+        S.zeta[i] = S.zeta_old[i] = S.zeta_new[i] = 1.0;
+        S.active[i] = bb > 0.0;
+        S.upd_x[i] = S.upd_p[i] = 0;
+        S.shift_iters[i] = 0;
+        S.cx[i] = S.cr[i] = S.cp[i] = 0.0;
+    }
+    if (threadIdx.x == 0) {
+        S.rr = rr;
+        S.bnorm2 = bb;
+        S.tol2 = tol * tol * bb;
+        S.alpha = 0.0;
+        S.alpha_old = 1.0;
+        S.beta_old = 0.0;
+        S.iters = 0;
+        S.running = 0;
+        S.nactive = bb > 0.0 ? S.nshift : 0;
+        done[blockIdx.x] = bb > 0.0 ? 0 : 1;
+    }
+}
+
+__global__ void k_alpha(SysScal *sc, const SysVecs *sv, const int *done)
+{
+    SysScal &S = sc[blockIdx.x];
+    if (done[blockIdx.x]) {
+        if (threadIdx.x == 0) S.running = 0;
+        return;
+    }
+    const SysVecs &V = sv[blockIdx.x];
+    const double pq = warp_sum_strided(V.part_d, V.nblk_d);
+    const double alpha = S.rr / pq;
+    for (int i = threadIdx.x; i < S.nshift; i += 32) {
+        if (!S.active[i]) continue;
+        const double z = S.zeta[i], zo = S.zeta_old[i];
+        const double zn = z * zo * S.alpha_old /
+                          (alpha * S.beta_old * (zo - z) + zo * S.alpha_old * (1.0 + S.s[i] * alpha));
+        S.zeta_new[i] = zn;
+        S.cx[i] = alpha * zn / z;
+    }
+    if (threadIdx.x == 0) {
+        S.alpha = alpha;
+        S.running = 1;
+    }
+}
+
+__global__ void k_beta(SysScal *sc, const SysVecs *sv, int *done, int *need_rel, double *log, int log_rows)
+{
+    SysScal &S = sc[blockIdx.x];
+    if (!S.running) return;
+    const SysVecs &V = sv[blockIdx.x];
+    const double rr_new = warp_sum_strided(V.part_v, V.nblk_v);
+    const double beta = rr_new / S.rr;
+    const int ns = S.nshift;
+    int nact = 0;
+    for (int i = threadIdx.x; i < ns; i += 32) {
+        if (S.active[i]) {
+            const double z = S.zeta[i], zn = S.zeta_new[i];
+            const double ratio = zn / z;
+            S.cr[i] = zn;
+            S.cp[i] = beta * ratio * ratio;
+            S.upd_x[i] = 1;
+            const bool conv = zn * zn * rr_new <= S.tol2;
+            if (conv) {
+                S.active[i] = 0;
+                S.shift_iters[i] = S.iters + 1;
+                S.upd_p[i] = 0;
+            } else {
+                S.upd_p[i] = 1;
+                ++nact;
+            }
+            S.zeta_old[i] = z;
+            S.zeta[i] = zn;
+        } else {
+            S.upd_x[i] = 0;
+            S.upd_p[i] = 0;
+        }
+    }
+    nact = warp_sum_int(nact);
+    const bool cont = nact > 0 && S.iters + 1 < S.max_iter;
+    for (int i = threadIdx.x; i < ns; i += 32) {
+        if (!cont) {
+            S.upd_p[i] = 0;
+        } else if (i == S.i0) {  // the base direction continues while any shift does
+            S.upd_p[i] = 1;
+            S.cr[i] = 1.0;
+            S.cp[i] = beta;
+        }
+        if (log != nullptr && blockIdx.x == 0 && S.iters < log_rows)
+            log[(size_t)S.iters * (2 + ns) + 2 + i] = S.upd_x[i] ? S.zeta[i] : 0.0;
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        if (log != nullptr && blockIdx.x == 0 && S.iters < log_rows) {
+            log[(size_t)S.iters * (2 + ns)] = S.alpha;
+            log[(size_t)S.iters * (2 + ns) + 1] = beta;
+        }
+        S.alpha_old = S.alpha;
+        S.beta_old = beta;
+        S.rr = rr_new;
+        S.iters += 1;
+        S.nactive = nact;
+        if (!cont) done[blockIdx.x] = 1;
+        if (S.phase2 && (!cont || rr_new < S.delta2 * S.rr_last)) need_rel[blockIdx.x] = 1;
+    }
+}
+
+// ------------------------------------------------------------------ phase-2 kernels
+
+// x_hi (FP64) += y (inner), y = 0   for pairs in the current reliable update
+template <typename R>
+__global__ void __launch_bounds__(kVecBlock) k_rel_fold(const SysVecs *__restrict__ sv, const int *__restrict__ noupd)
+{
+    if (noupd[blockIdx.y]) return;
+    const SysVecs &V = sv[blockIdx.y];
+    int h = blockIdx.x * kVecBlock + threadIdx.x;
+    if (h >= V.Vh) return;
+    cx<R> y[3], z[3];
+    cx<double> x[3];
+    Field<R>::load_rw(V.x[0], V.Vh, h, y);
+    Field<double>::load_rw(V.xhi, V.Vh, h, x);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        x[c] = cx<double>{x[c].re + (double)y[c].re, x[c].im + (double)y[c].im};
+        z[c] = cx<R>{R(0), R(0)};
+    }
+    Field<double>::store(V.xhi, V.Vh, h, x);
+    Field<R>::store(V.x[0], V.Vh, h, z);
+}
+
+// after the FP64 residual r_hi = b - A x_hi (partials of |r_hi|^2 in part_d): decide per pair
+__global__ void k_rel_finish(SysScal *sc, const SysVecs *sv, const int *noupd, int *done, int *need_rel,
+                             int *finished, double *true_rr, int *rel_count)
+{
+    const int s = blockIdx.x;
+    if (noupd[s]) return;
+    SysScal &S = sc[s];
+    const SysVecs &V = sv[s];
+    const double rr = warp_sum_strided(V.part_d, V.nblk_d);
+    if (threadIdx.x == 0) {
+        true_rr[s] = rr;
+        rel_count[s] += 1;
+        need_rel[s] = 0;
+        if (rr <= S.tol2_true || S.iters >= S.max_iter) {
+            finished[s] = 1;
+            done[s] = 1;
+        } else {
+            done[s] = 0;
+            S.active[0] = 1;
+            S.nactive = 1;
+        }
+    }
+}
+
+// r = inner(r_hi) (and, at the start of phase 2, p = r, y = 0); partial |r|^2
+template <typename R>
+__global__ void __launch_bounds__(kVecBlock) k_rel_copy(const SysVecs *__restrict__ sv, const int *__restrict__ noupd,
+                                                         const int *__restrict__ finished, int start)
+{
+    const int s = blockIdx.y;
+    const SysVecs &V = sv[s];
+    if (noupd[s] || finished[s] || (int)(blockIdx.x * kVecBlock) >= V.Vh) return;
+    int h = blockIdx.x * kVecBlock + threadIdx.x;
+    double pr = 0.0;
+    if (h < V.Vh) {
+        cx<double> rh[3];
+        cx<R> r[3];
+        Field<double>::load_rw(V.rhi, V.Vh, h, rh);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) r[c] = cx<R>{(R)rh[c].re, (R)rh[c].im};
+        Field<R>::store(V.r, V.Vh, h, r);
+        if (start) {
+            cx<R> z[3];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) z[c] = cx<R>{R(0), R(0)};
+            Field<R>::store(V.p[0], V.Vh, h, r);
+            Field<R>::store(V.x[0], V.Vh, h, z);
+        }
+        pr = norm2_site(r);
+    }
+    __shared__ double sh[32];
+    double t = block_sum(pr, sh);
+    if (threadIdx.x == 0) V.part_v[blockIdx.x] = t;
+}
+
+__global__ void k_rel_scal(SysScal *sc, const SysVecs *sv, const int *noupd, const int *finished, int start)
+{
+    const int s = blockIdx.x;
+    if (noupd[s] || finished[s]) return;
+    SysScal &S = sc[s];
+    const double rr = warp_sum_strided(sv[s].part_v, sv[s].nblk_v);
+    if (threadIdx.x == 0) {
+        S.rr = rr;
+        S.rr_last = rr;
+        if (start) {
+            S.zeta[0] = S.zeta_old[0] = S.zeta_new[0] = 1.0;
+            S.s[0] = 0.0;
+            S.active[0] = 1;
+            S.nactive = 1;
+            S.alpha_old = 1.0;
+            S.beta_old = 0.0;
+            S.iters = 0;
+            S.running = 0;
+        }
+    }
+}
+
+// FP64 copy/convert x_inner -> x_hi for (system, shift) pairs (phase-1 results)
+struct ConvPair {
+    const void *src;
+    void *dst;
+    int Vh;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kVecBlock) k_convert_to_f64(const ConvPair *__restrict__ pr)
+{
+    const ConvPair &P = pr[blockIdx.y];
+    int h = blockIdx.x * kVecBlock + threadIdx.x;
+    if (h >= P.Vh) return;
+    cx<R> v[3];
+    cx<double> w[3];
+    Field<R>::load_rw(P.src, P.Vh, h, v);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) w[c] = cx<double>{(double)v[c].re, (double)v[c].im};
+    Field<double>::store(P.dst, P.Vh, h, w);
+}
+
+__global__ void __launch_bounds__(kVecBlock) k_unpack_pairs(const ConvPair *__restrict__ pr)
+{
+    const ConvPair &P = pr[blockIdx.y];
+    int h = blockIdx.x * kVecBlock + threadIdx.x;
+    if (h >= P.Vh) return;
+    cx<double> v[3];
+    Field<double>::load_rw(P.src, P.Vh, h, v);
+    double2 *o = static_cast<double2 *>(P.dst);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) o[(size_t)h * 3 + c] = make_double2(v[c].re, v[c].im);
+}
+
+// ------------------------------------------------------------------ host engine
+
+namespace {
+
+struct DevBuf {
+    std::vector<void *> ptrs;
+    cudaStream_t st = nullptr;
+    cudaError_t err = cudaSuccess;
+    void *alloc(size_t bytes)
+    {
+        if (err != cudaSuccess) return nullptr;
+        void *p = nullptr;
+        err = cudaMallocAsync(&p, bytes ? bytes : 16, st);
+        if (err == cudaSuccess) ptrs.push_back(p);
+        return p;
+    }
+    ~DevBuf()
+    {
+        for (void *p : ptrs) cudaFreeAsync(p, st);
+    }
+};
+
+struct InstInfo {
+    const stg_gauge *gi;   // gauge of the inner iterations
+    const stg_gauge *g64;  // FP64 gauge
+    int nrhs;
+    int sys0;              // first phase-1 system of this instance
+};
+
+// D_oe / D_eo argument lists for a set of systems on their instances' gauges
+struct DPlan {
+    std::vector<DArgs> oe, eo;  // launched with modes 0 and (1 or 2)
+};
+
+static void add_group(std::vector<DArgs> &lst, const DGroup &G)
+{
+    if (lst.empty() || lst.back().ngroups == kMaxGroups) {
+        DArgs a;
+        memset(&a, 0, sizeof(a));
+        lst.push_back(a);
+    }
+    DArgs &a = lst.back();
+    a.grp[a.ngroups++] = G;
+}
+
+}  // namespace
+
+template <typename R>
+static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg_params *prm, cudaStream_t user_st)
+{
+    const bool mixed = !std::is_same<R, double>::value;
+    const int ns = prm->nshift;
+    const double mass2 = prm->mass * prm->mass;
+    double sigma0 = prm->shifts[0];
+    int i0 = 0;
+    for (int i = 1; i < ns; ++i)
+        if (prm->shifts[i] < sigma0) { sigma0 = prm->shifts[i]; i0 = i; }
+
+    std::vector<InstInfo> ii(ninst);
+    int nsys = 0;
+    for (int k = 0; k < ninst; ++k) {
+        ii[k].g64 = inst[k].g_f64;
+        ii[k].gi = mixed ? inst[k].g_inner : inst[k].g_f64;
+        ii[k].nrhs = inst[k].nrhs;
+        ii[k].sys0 = nsys;
+        nsys += inst[k].nrhs;
+    }
+    const int npair = nsys * ns;
+    const int kind_i = ii[0].gi->kind, kind_64 = ii[0].g64->kind;
+    const double inner_tol = mixed ? (prm->inner_tol > 0 ? prm->inner_tol
+                                                          : (kind_i == kBF16R12 || kind_i == kF16R12 ? 2e-3 : 1e-6))
+                                   : prm->tol;
+    const double delta = prm->reliable_delta > 0 ? prm->reliable_delta : 0.1;
+    const int vb = Field<R>::kBytesPerSite;
+
+    // work stream ordered after the caller's stream
+    cudaStream_t ws;
+    STG_CUDA_TRY(cudaStreamCreateWithFlags(&ws, cudaStreamNonBlocking));
+    struct StreamGuard {
+        cudaStream_t s;
+        ~StreamGuard() { cudaStreamSynchronize(s); cudaStreamDestroy(s); }
+    } sguard{ws};
+    cudaEvent_t ev;
+    STG_CUDA_TRY(cudaEventCreateWithFlags(&ev, cudaEventDisableTiming));
+    struct EventGuard {
+        cudaEvent_t e;
+        ~EventGuard() { cudaEventDestroy(e); }
+    } eguard{ev};
+    STG_CUDA_TRY(cudaEventRecord(ev, user_st));
+    STG_CUDA_TRY(cudaStreamWaitEvent(ws, ev, 0));
+
+    DevBuf mem;
+    mem.st = ws;
+
+    // ---------------- buffers
+    std::vector<SysVecs> v1(nsys), v2(npair);
+    std::vector<SysScal> s1(nsys), s2(npair);
+    memset(v1.data(), 0, sizeof(SysVecs) * nsys);
+    memset(v2.data(), 0, sizeof(SysVecs) * npair);
+    memset(s1.data(), 0, sizeof(SysScal) * nsys);
+    memset(s2.data(), 0, sizeof(SysScal) * npair);
+    int nblkv_max = 0;
+    for (int k = 0; k < ninst; ++k) {
+        const int Vh = ii[k].g64->g.Vh;
+        const int nbd = (Vh + kDslashBlock - 1) / kDslashBlock, nbv = (Vh + kVecBlock - 1) / kVecBlock;
+        nblkv_max = std::max(nblkv_max, nbv);
+        const size_t fb = (size_t)Vh * vb, f64b = (size_t)Vh * 48;
+        for (int r = 0; r < ii[k].nrhs; ++r) {
+            const int s = ii[k].sys0 + r;
+            SysVecs &V = v1[s];
+            V.Vh = Vh;
+            V.nblk_d = nbd;
+            V.nblk_v = nbv;
+            V.r = mem.alloc(fb);
+            V.q = mem.alloc(fb);
+            V.t = mem.alloc(fb);
+            for (int i = 0; i < ns; ++i) {
+                V.p[i] = mem.alloc(fb);
+                V.x[i] = mixed ? mem.alloc(fb) : nullptr;  // FP64 solves accumulate straight into x_hi
+            }
+            V.b64 = mem.alloc(f64b);
+            V.bcanon = static_cast<const double2 *>(inst[k].b[r]);
+            V.part_d = static_cast<double *>(mem.alloc(sizeof(double) * nbd));
+            V.part_v = static_cast<double *>(mem.alloc(sizeof(double) * nbv));
+            V.part_v2 = static_cast<double *>(mem.alloc(sizeof(double) * nbv));
+            SysScal &S = s1[s];
+            S.nshift = ns;
+            S.i0 = i0;
+            S.max_iter = prm->max_iter;
+            for (int i = 0; i < ns; ++i) S.s[i] = prm->shifts[i] - sigma0;
+            S.coef = mass2 + sigma0;
+            for (int i = 0; i < ns; ++i) {
+                const int pidx = s * ns + i;
+                SysVecs &W = v2[pidx];
+                W.Vh = Vh;
+                W.nblk_d = nbd;
+                W.nblk_v = nbv;
+                W.xhi = mem.alloc(f64b);
+                if (!mixed) V.x[i] = W.xhi;
+                W.rhi = mem.alloc(f64b);
+                W.t64 = mem.alloc(f64b);
+                W.b64 = V.b64;
+                W.part_d = static_cast<double *>(mem.alloc(sizeof(double) * nbd));
+                W.part_v = static_cast<double *>(mem.alloc(sizeof(double) * nbv));
+                SysScal &P = s2[pidx];
+                P.nshift = 1;
+                P.i0 = 0;
+                P.max_iter = prm->max_iter;
+                P.phase2 = 1;
+                P.delta2 = delta * delta;
+                P.coef = mass2 + prm->shifts[i];
+            }
+        }
+    }
+    if (mem.err != cudaSuccess) return cuda_error(mem.err, "stg_mscg_solve: workspace allocation");
+
+    SysVecs *d_v1 = static_cast<SysVecs *>(mem.alloc(sizeof(SysVecs) * nsys));
+    SysScal *d_s1 = static_cast<SysScal *>(mem.alloc(sizeof(SysScal) * nsys));
+    SysVecs *d_v2 = static_cast<SysVecs *>(mem.alloc(sizeof(SysVecs) * npair));
+    SysScal *d_s2 = static_cast<SysScal *>(mem.alloc(sizeof(SysScal) * npair));
+    // int flags: done1[nsys], need1[nsys], done2[npair], need2[npair], noupd[npair], finished[npair], relcnt[npair]
+    int *d_flags = static_cast<int *>(mem.alloc(sizeof(int) * (2 * nsys + 5 * npair)));
+    double *d_true_rr = static_cast<double *>(mem.alloc(sizeof(double) * npair));
+    double *d_log = prm->log_rows > 0 ? static_cast<double *>(mem.alloc(sizeof(double) * prm->log_rows * (2 + ns)))
+                                      : nullptr;
+    ConvPair *d_pairs = static_cast<ConvPair *>(mem.alloc(sizeof(ConvPair) * npair));
+    if (mem.err != cudaSuccess) return cuda_error(mem.err, "stg_mscg_solve: workspace allocation");
+    int *done1 = d_flags, *need1 = d_flags + nsys, *done2 = d_flags + 2 * nsys, *need2 = done2 + npair,
+        *noupd = need2 + npair, *finished = noupd + npair, *relcnt = finished + npair;
+
+    // phase-2 inner vectors (allocated after the FP64 ones so phase 1 stays compact)
+    for (int s = 0; s < nsys; ++s)
+        for (int i = 0; i < ns; ++i) {
+            SysVecs &W = v2[s * ns + i];
+            const size_t fb = (size_t)W.Vh * vb;
+            W.r = mem.alloc(fb);
+            W.q = mem.alloc(fb);
+            W.t = mem.alloc(fb);
+            W.p[0] = mem.alloc(fb);
+            W.x[0] = mem.alloc(fb);
+        }
+    if (mem.err != cudaSuccess) return cuda_error(mem.err, "stg_mscg_solve: workspace allocation");
+
+    STG_CUDA_TRY(cudaMemcpyAsync(d_v1, v1.data(), sizeof(SysVecs) * nsys, cudaMemcpyHostToDevice, ws));
+    STG_CUDA_TRY(cudaMemcpyAsync(d_s1, s1.data(), sizeof(SysScal) * nsys, cudaMemcpyHostToDevice, ws));
+    STG_CUDA_TRY(cudaMemcpyAsync(d_v2, v2.data(), sizeof(SysVecs) * npair, cudaMemcpyHostToDevice, ws));
+    STG_CUDA_TRY(cudaMemcpyAsync(d_s2, s2.data(), sizeof(SysScal) * npair, cudaMemcpyHostToDevice, ws));
+    STG_CUDA_TRY(cudaMemsetAsync(d_flags, 0, sizeof(int) * (2 * nsys + 5 * npair), ws));
+
+    // ---------------- dslash plans
+    // phase 1: rhs of one instance share link loads (groups of up to kMaxRhs)
+    DPlan p1;
+    for (int k = 0; k < ninst; ++k) {
+        for (int r0 = 0; r0 < ii[k].nrhs; r0 += kMaxRhs) {
+            DGroup Goe, Geo;
+            memset(&Goe, 0, sizeof(Goe));
+            Goe.g = ii[k].gi->g;
+            Goe.links = ii[k].gi->links;
+            Goe.nrhs = std::min(kMaxRhs, ii[k].nrhs - r0);
+            Geo = Goe;
+            for (int j = 0; j < Goe.nrhs; ++j) {
+                const int s = ii[k].sys0 + r0 + j;
+                Goe.in[j] = v1[s].p[i0];
+                Goe.out[j] = v1[s].t;
+                Goe.skip[j] = done1 + s;
+                Geo.in[j] = v1[s].t;
+                Geo.out[j] = v1[s].q;
+                Geo.epi_p[j] = v1[s].p[i0];
+                Geo.coef[j] = mass2 + sigma0;
+                Geo.partial[j] = v1[s].part_d;
+                Geo.skip[j] = done1 + s;
+            }
+            add_group(p1.oe, Goe);
+            add_group(p1.eo, Geo);
+        }
+    }
+    // phase 2: the (rhs, shift) pairs of one instance share link loads
+    DPlan p2, p64;
+    for (int k = 0; k < ninst; ++k) {
+        const int first = ii[k].sys0 * ns, cnt = ii[k].nrhs * ns;
+        for (int q0 = 0; q0 < cnt; q0 += kMaxRhs) {
+            DGroup Goe, Geo, Hoe, Heo;
+            memset(&Goe, 0, sizeof(Goe));
+            Goe.g = ii[k].gi->g;
+            Goe.links = ii[k].gi->links;
+            Goe.nrhs = std::min(kMaxRhs, cnt - q0);
+            Geo = Goe;
+            Hoe = Goe;
+            Hoe.links = ii[k].g64->links;
+            Heo = Hoe;
+            for (int j = 0; j < Goe.nrhs; ++j) {
+                const int pidx = first + q0 + j;
+                const SysVecs &W = v2[pidx];
+                Goe.in[j] = W.p[0];
+                Goe.out[j] = W.t;
+                Goe.skip[j] = done2 + pidx;
+                Geo.in[j] = W.t;
+                Geo.out[j] = W.q;
+                Geo.epi_p[j] = W.p[0];
+                Geo.coef[j] = s2[pidx].coef;
+                Geo.partial[j] = W.part_d;
+                Geo.skip[j] = done2 + pidx;
+                // FP64 true residual r_hi = b - A x_hi
+                Hoe.in[j] = W.xhi;
+                Hoe.out[j] = W.t64;
+                Hoe.skip[j] = noupd + pidx;
+                Heo.in[j] = W.t64;
+                Heo.out[j] = W.rhi;
+                Heo.epi_p[j] = W.xhi;
+                Heo.epi_b[j] = W.b64;
+                Heo.coef[j] = s2[pidx].coef;
+                Heo.partial[j] = W.part_d;
+                Heo.skip[j] = noupd + pidx;
+            }
+            add_group(p2.oe, Goe);
+            add_group(p2.eo, Geo);
+            add_group(p64.oe, Hoe);
+            add_group(p64.eo, Heo);
+        }
+    }
+
+    const dim3 vgrid1(nblkv_max, nsys), vgrid2(nblkv_max, npair);
+
+    auto iterate = [&](const DPlan &pl, SysScal *dS, SysVecs *dV, int *dn, int *nr, int n, dim3 vg, double *log,
+                       int log_rows) -> cudaError_t {
+        cudaError_t e;
+        for (const DArgs &a : pl.oe)
+            if ((e = launch_dslash(kind_i, a, 0, ws)) != cudaSuccess) return e;
+        for (const DArgs &a : pl.eo)
+            if ((e = launch_dslash(kind_i, a, 1, ws)) != cudaSuccess) return e;
+        k_alpha<<<n, 32, 0, ws>>>(dS, dV, dn);
+        k_update_r<R><<<vg, kVecBlock, 0, ws>>>(dS, dV);
+        k_beta<<<n, 32, 0, ws>>>(dS, dV, dn, nr, log, log_rows);
+        k_update_shifts<R><<<vg, kVecBlock, 0, ws>>>(dS, dV);
+        return cudaGetLastError();
+    };
+
+    // Chunks of `kChunk` iterations are captured once per phase into a CUDA graph and replayed;
+    // converged systems make every kernel of the chunk a no-op, so overshooting is cheap.
+    struct GraphCache {
+        cudaGraph_t graph = nullptr;
+        cudaGraphExec_t exec = nullptr;
+        int state = 0;  // 0 not built, 1 graph, 2 direct launches
+        ~GraphCache()
+        {
+            if (exec) cudaGraphExecDestroy(exec);
+            if (graph) cudaGraphDestroy(graph);
+        }
+    };
+    constexpr int kChunk = 8;
+    // Runs chunks until every system's done flag is set (or, with stop_on_need, until some
+    // system asks for a reliable update).
+    auto run_until_done = [&](GraphCache &gc, const DPlan &pl, SysScal *dS, SysVecs *dV, int *dn, int *nr, int n,
+                              dim3 vg, double *log, int log_rows, bool stop_on_need, std::vector<int> &h_done,
+                              std::vector<int> &h_need) -> stg_status {
+        if (gc.state == 0) {
+            gc.state = 2;
+            if (cudaStreamBeginCapture(ws, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+                cudaError_t e = cudaSuccess;
+                for (int k = 0; k < kChunk && e == cudaSuccess; ++k)
+                    e = iterate(pl, dS, dV, dn, nr, n, vg, log, log_rows);
+                cudaError_t e2 = cudaStreamEndCapture(ws, &gc.graph);
+                if (e == cudaSuccess && e2 == cudaSuccess && cudaGraphInstantiate(&gc.exec, gc.graph, 0) == cudaSuccess)
+                    gc.state = 1;
+                else
+                    cudaGetLastError();
+            } else {
+                cudaGetLastError();
+            }
+        }
+        const long long cap = (long long)prm->max_iter / kChunk + 4;
+        for (long long c = 0; c <= cap; ++c) {
+            cudaError_t e = gc.state == 1 ? cudaGraphLaunch(gc.exec, ws) : cudaSuccess;
+            for (int k = 0; gc.state != 1 && k < kChunk && e == cudaSuccess; ++k)
+                e = iterate(pl, dS, dV, dn, nr, n, vg, log, log_rows);
+            if (e == cudaSuccess) e = cudaMemcpyAsync(h_done.data(), dn, sizeof(int) * n, cudaMemcpyDeviceToHost, ws);
+            if (e == cudaSuccess && stop_on_need)
+                e = cudaMemcpyAsync(h_need.data(), nr, sizeof(int) * n, cudaMemcpyDeviceToHost, ws);
+            if (e == cudaSuccess) e = cudaStreamSynchronize(ws);
+            if (e != cudaSuccess) return cuda_error(e, "stg_mscg_solve: iteration");
+            bool all = true, any_need = false;
+            for (int s = 0; s < n; ++s) {
+                all &= h_done[s] != 0;
+                if (stop_on_need) any_need |= h_need[s] != 0;
+            }
+            if (all || any_need) break;
+        }
+        return STG_OK;
+    };
+    GraphCache gc1, gc2;
+
+    // ---------------- phase 1
+    k_p1_init<R><<<vgrid1, kVecBlock, 0, ws>>>(d_v1, ns);
+    k_p1_init_scal<<<nsys, 32, 0, ws>>>(d_s1, d_v1, done1, inner_tol);
+    STG_CUDA_TRY(cudaGetLastError());
+    std::vector<int> h_done1(nsys), h_need1(nsys);
+    stg_status st = run_until_done(gc1, p1, d_s1, d_v1, done1, need1, nsys, vgrid1, d_log, prm->log_rows, false,
+                                   h_done1, h_need1);
+    if (st != STG_OK) return st;
+
+    // ---------------- phase 2: FP64 true residuals, refinement with reliable updates
+    if (mixed) {
+        std::vector<ConvPair> cp(npair);
+        for (int s = 0; s < nsys; ++s)
+            for (int i = 0; i < ns; ++i) cp[s * ns + i] = ConvPair{v1[s].x[i], v2[s * ns + i].xhi, v1[s].Vh};
+        STG_CUDA_TRY(cudaMemcpyAsync(d_pairs, cp.data(), sizeof(ConvPair) * npair, cudaMemcpyHostToDevice, ws));
+        k_convert_to_f64<R><<<vgrid2, kVecBlock, 0, ws>>>(d_pairs);
+        STG_CUDA_TRY(cudaGetLastError());
+    }
+    // per-pair |b|^2 and tolerances from phase 1
+    {
+        std::vector<SysScal> tmp(nsys);
+        STG_CUDA_TRY(cudaMemcpyAsync(tmp.data(), d_s1, sizeof(SysScal) * nsys, cudaMemcpyDeviceToHost, ws));
+        STG_CUDA_TRY(cudaStreamSynchronize(ws));
+        for (int s = 0; s < nsys; ++s) {
+            s1[s] = tmp[s];
+            for (int i = 0; i < ns; ++i) {
+                SysScal &P = s2[s * ns + i];
+                P.bnorm2 = tmp[s].bnorm2;
+                P.tol2_true = prm->tol * prm->tol * tmp[s].bnorm2;
+                P.tol2 = 0.25 * P.tol2_true;
+            }
+        }
+        STG_CUDA_TRY(cudaMemcpyAsync(d_s2, s2.data(), sizeof(SysScal) * npair, cudaMemcpyHostToDevice, ws));
+    }
+    std::vector<int> h_done2(npair, 1), h_need2(npair, 1), h_fin(npair, 0), h_noupd(npair, 0);
+    auto reliable_update = [&](bool start) -> stg_status {
+        STG_CUDA_TRY(cudaMemcpyAsync(noupd, h_noupd.data(), sizeof(int) * npair, cudaMemcpyHostToDevice, ws));
+        if (!start) k_rel_fold<R><<<vgrid2, kVecBlock, 0, ws>>>(d_v2, noupd);
+        for (const DArgs &a : p64.oe) STG_CUDA_TRY(launch_dslash(kind_64, a, 0, ws));
+        for (const DArgs &a : p64.eo) STG_CUDA_TRY(launch_dslash(kind_64, a, 2, ws));
+        k_rel_finish<<<npair, 32, 0, ws>>>(d_s2, d_v2, noupd, done2, need2, finished, d_true_rr, relcnt);
+        k_rel_copy<R><<<vgrid2, kVecBlock, 0, ws>>>(d_v2, noupd, finished, start ? 1 : 0);
+        k_rel_scal<<<npair, 32, 0, ws>>>(d_s2, d_v2, noupd, finished, start ? 1 : 0);
+        STG_CUDA_TRY(cudaGetLastError());
+        STG_CUDA_TRY(cudaMemcpyAsync(h_fin.data(), finished, sizeof(int) * npair, cudaMemcpyDeviceToHost, ws));
+        STG_CUDA_TRY(cudaStreamSynchronize(ws));
+        return STG_OK;
+    };
+    // every pair starts with a true-residual check
+    st = reliable_update(true);
+    if (st != STG_OK) return st;
+    const long long rel_cap = 4LL * prm->max_iter + 64;
+    for (long long round = 0; round < rel_cap; ++round) {
+        bool all = true;
+        for (int q = 0; q < npair; ++q) all &= h_fin[q] != 0;
+        if (all) break;
+        st = run_until_done(gc2, p2, d_s2, d_v2, done2, need2, npair, vgrid2, nullptr, 0, true, h_done2, h_need2);
+        if (st != STG_OK) return st;
+        bool any = false;
+        for (int q = 0; q < npair; ++q) {
+            h_noupd[q] = (h_need2[q] && !h_fin[q]) ? 0 : 1;
+            any |= h_noupd[q] == 0;
+        }
+        if (!any) {
+            // nothing flagged yet: every live pair is still iterating
+            bool live = false;
+            for (int q = 0; q < npair; ++q) live |= !h_fin[q] && !h_done2[q];
+            if (!live) break;
+            continue;
+        }
+        st = reliable_update(false);
+        if (st != STG_OK) return st;
+    }
+
+    // ---------------- outputs and statistics
+    {
+        std::vector<ConvPair> cp(npair);
+        for (int k = 0; k < ninst; ++k)
+            for (int r = 0; r < ii[k].nrhs; ++r)
+                for (int i = 0; i < ns; ++i) {
+                    const int s = ii[k].sys0 + r, pidx = s * ns + i;
+                    cp[pidx] = ConvPair{v2[pidx].xhi, inst[k].x[r * ns + i], v2[pidx].Vh};
+                }
+        STG_CUDA_TRY(cudaMemcpyAsync(d_pairs, cp.data(), sizeof(ConvPair) * npair, cudaMemcpyHostToDevice, ws));
+        k_unpack_pairs<<<vgrid2, kVecBlock, 0, ws>>>(d_pairs);
+        STG_CUDA_TRY(cudaGetLastError());
+    }
+    std::vector<SysScal> f1(nsys), f2(npair);
+    std::vector<double> trr(npair);
+    std::vector<int> rc(npair);
+    std::vector<double> hlog(prm->log_rows > 0 ? (size_t)prm->log_rows * (2 + ns) : 0);
+    STG_CUDA_TRY(cudaMemcpyAsync(f1.data(), d_s1, sizeof(SysScal) * nsys, cudaMemcpyDeviceToHost, ws));
+    STG_CUDA_TRY(cudaMemcpyAsync(f2.data(), d_s2, sizeof(SysScal) * npair, cudaMemcpyDeviceToHost, ws));
+    STG_CUDA_TRY(cudaMemcpyAsync(trr.data(), d_true_rr, sizeof(double) * npair, cudaMemcpyDeviceToHost, ws));
+    STG_CUDA_TRY(cudaMemcpyAsync(rc.data(), relcnt, sizeof(int) * npair, cudaMemcpyDeviceToHost, ws));
+    if (d_log)
+        STG_CUDA_TRY(cudaMemcpyAsync(hlog.data(), d_log, sizeof(double) * hlog.size(), cudaMemcpyDeviceToHost, ws));
+    STG_CUDA_TRY(cudaStreamSynchronize(ws));
+    if (d_log) {
+        const int rows = std::min(prm->log_rows, f1[0].iters);
+        memcpy(prm->scalar_log, hlog.data(), sizeof(double) * rows * (2 + ns));
+    }
+
+    bool conv = true;
+    for (int k = 0; k < ninst; ++k)
+        for (int r = 0; r < ii[k].nrhs; ++r) {
+            const int s = ii[k].sys0 + r;
+            stg_mscg_stats *S = inst[k].stats ? &inst[k].stats[r] : nullptr;
+            int rel = 0, ref = 0;
+            for (int i = 0; i < ns; ++i) {
+                const int pidx = s * ns + i;
+                const double bb = f1[s].bnorm2;
+                const double res = bb > 0 ? std::sqrt(trr[pidx] / bb) : 0.0;
+                conv &= res <= prm->tol;
+                rel += std::max(0, rc[pidx] - 1);
+                ref = std::max(ref, f2[pidx].iters);
+                if (S && S->true_resid) S->true_resid[i] = res;
+                if (S && S->shift_iters) S->shift_iters[i] = f1[s].shift_iters[i] ? f1[s].shift_iters[i] : f1[s].iters;
+            }
+            if (S) {
+                S->iters = f1[s].iters;
+                S->reliable_updates = rel;
+                S->refine_iters = ref;
+            }
+        }
+    STG_CUDA_TRY(cudaEventRecord(ev, ws));
+    STG_CUDA_TRY(cudaStreamWaitEvent(user_st, ev, 0));
+    if (!conv) return set_error(STG_ERR_NOCONV, "stg_mscg_solve: a shift is above tol after max_iter");
+    return STG_OK;
+}
+
+static stg_status validate(int ninst, const stg_instance *inst, const stg_mscg_params *prm, bool &mixed)
+{
+    if (!inst || !prm) return set_error(STG_ERR_ARG, "stg_mscg_solve: null pointer");
+    if (ninst < 1 || ninst > 16) return set_error(STG_ERR_ARG, "stg_mscg_solve: ninst must be in 1..16");
+    if (prm->nshift < 1 || prm->nshift > kMaxShifts || !prm->shifts)
+        return set_error(STG_ERR_ARG, "stg_mscg_solve: nshift must be in 1..32 with a shifts array");
+    for (int i = 0; i < prm->nshift; ++i)
+        if (!(prm->shifts[i] >= 0.0) || !std::isfinite(prm->shifts[i]))
+            return set_error(STG_ERR_ARG, "stg_mscg_solve: shifts must be finite and >= 0");
+    if (!std::isfinite(prm->mass) || !(prm->tol > 0.0) || prm->max_iter < 1)
+        return set_error(STG_ERR_ARG, "stg_mscg_solve: need finite mass, tol > 0, max_iter > 0");
+    if (prm->log_rows < 0 || (prm->log_rows > 0 && !prm->scalar_log))
+        return set_error(STG_ERR_ARG, "stg_mscg_solve: scalar_log required when log_rows > 0");
+    mixed = inst[0].g_inner != nullptr;
+    int kind_i = -1, kind_64 = -1;
+    for (int k = 0; k < ninst; ++k) {
+        const stg_instance &I = inst[k];
+        if (!I.g_f64 || !I.b || !I.x) return set_error(STG_ERR_ARG, "stg_mscg_solve: null gauge/b/x");
+        if (!kind_is_f64(I.g_f64->kind)) return set_error(STG_ERR_ARG, "stg_mscg_solve: g_f64 must be an F64 gauge");
+        if ((I.g_inner != nullptr) != mixed)
+            return set_error(STG_ERR_ARG, "stg_mscg_solve: all instances must be mixed, or none");
+        if (I.nrhs < 1 || I.nrhs > 16) return set_error(STG_ERR_ARG, "stg_mscg_solve: nrhs must be in 1..16");
+        if (kind_64 >= 0 && I.g_f64->kind != kind_64)
+            return set_error(STG_ERR_ARG, "stg_mscg_solve: all FP64 gauges must share one storage kind");
+        kind_64 = I.g_f64->kind;
+        if (mixed) {
+            if (kind_is_f64(I.g_inner->kind))
+                return set_error(STG_ERR_ARG, "stg_mscg_solve: g_inner must be an F32, BF16 or F16 gauge");
+            for (int d = 0; d < 4; ++d)
+                if (I.g_inner->g.L[d] != I.g_f64->g.L[d] || I.g_inner->g.antiperiodic != I.g_f64->g.antiperiodic)
+                    return set_error(STG_ERR_SHAPE, "stg_mscg_solve: g_inner and g_f64 lattices differ");
+            if (kind_i >= 0 && I.g_inner->kind != kind_i)
+                return set_error(STG_ERR_ARG, "stg_mscg_solve: all inner gauges must share one storage kind");
+            kind_i = I.g_inner->kind;
+        }
+        for (int r = 0; r < I.nrhs; ++r) {
+            if (!I.b[r] || (reinterpret_cast<uintptr_t>(I.b[r]) & 15))
+                return set_error(STG_ERR_ARG, "stg_mscg_solve: b must be non-null and 16-byte aligned");
+            for (int i = 0; i < prm->nshift; ++i) {
+                const void *x = I.x[r * prm->nshift + i];
+                if (!x || (reinterpret_cast<uintptr_t>(x) & 15))
+                    return set_error(STG_ERR_ARG, "stg_mscg_solve: x must be non-null and 16-byte aligned");
+                if (x == I.b[r]) return set_error(STG_ERR_ARG, "stg_mscg_solve: x may not alias b");
+            }
+        }
+    }
+    return STG_OK;
+}
+
+}  // namespace stg
+
+using namespace stg;
+
+extern "C" {
+
+stg_status stg_mscg_solve_batched(int32_t ninst, const stg_instance *inst, const stg_mscg_params *params, void *stream)
+{
+    bool mixed = false;
+    stg_status s = validate(ninst, inst, params, mixed);
+    if (s != STG_OK) return s;
+    return mixed ? solve_impl<float>(ninst, inst, params, (cudaStream_t)stream)
+                 : solve_impl<double>(ninst, inst, params, (cudaStream_t)stream);
+}
+
+stg_status stg_mscg_solve(const stg_gauge *g_f64, const stg_gauge *g_inner, const stg_mscg_params *params,
+                          const void *b_c128_dev, void *const *x_c128_dev, stg_mscg_stats *stats, void *stream)
+{
+    if (!g_f64 || !params || !b_c128_dev || !x_c128_dev) return set_error(STG_ERR_ARG, "stg_mscg_solve: null pointer");
+    const void *b[1] = {b_c128_dev};
+    stg_instance in;
+    in.g_f64 = g_f64;
+    in.g_inner = g_inner;
+    in.nrhs = 1;
+    in.b = b;
+    in.x = x_c128_dev;
+    in.stats = stats;
+    return stg_mscg_solve_batched(1, &in, params, stream);
+}
+
+}  // extern "C"

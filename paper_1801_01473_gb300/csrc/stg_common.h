@@ -1,0 +1,60 @@
+// stg_common.h -- host-side definitions shared by the translation units of libstg:
+// the opaque handles, the link-storage kinds, error reporting and the launchers
+// implemented in the per-precision dslash units.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <string>
+
+#include "../../include/stg.h"
+#include "dslash.cuh"
+
+namespace stg {
+
+// Link storage kinds (precision x compression); index of the dslash instantiation.
+enum LinkKind { kF64R18 = 0, kF64R12 = 1, kF32R18 = 2, kF32R12 = 3, kBF16R12 = 4, kF16R12 = 5 };
+
+int link_bytes(int kind);
+inline bool kind_is_f64(int kind) { return kind == kF64R18 || kind == kF64R12; }
+
+// Launchers, one per storage kind, implemented in dslash_f64.cu / dslash_f32.cu / dslash_h16.cu.
+cudaError_t launch_dslash_f64r18(const DArgs &a, int mode, cudaStream_t st);
+cudaError_t launch_dslash_f64r12(const DArgs &a, int mode, cudaStream_t st);
+cudaError_t launch_dslash_f32r18(const DArgs &a, int mode, cudaStream_t st);
+cudaError_t launch_dslash_f32r12(const DArgs &a, int mode, cudaStream_t st);
+cudaError_t launch_dslash_bf16r12(const DArgs &a, int mode, cudaStream_t st);
+cudaError_t launch_dslash_f16r12(const DArgs &a, int mode, cudaStream_t st);
+cudaError_t launch_dslash(int kind, const DArgs &a, int mode, cudaStream_t st);
+
+// Pack canonical complex128 links [4][V][3][3] into the internal layout of `kind`.
+cudaError_t launch_pack_links(int kind, const Geom &g, const void *canon, void *links, cudaStream_t st);
+
+// Error reporting (thread-local message read by stg_last_error).
+stg_status set_error(stg_status s, const std::string &msg);
+stg_status cuda_error(cudaError_t e, const char *where);
+
+}  // namespace stg
+
+struct stg_lattice {
+    stg::Geom g;
+    long long V;
+};
+
+struct stg_gauge {
+    const stg_lattice *lat;
+    stg::Geom g;
+    stg_prec prec;
+    stg_recon recon;
+    int kind;
+    void *links;
+    size_t bytes;
+    double *scratch;       // per-block partial sums of stg_normal_op's reduction
+    size_t scratch_count;  // doubles in scratch
+};
+
+#define STG_CUDA_TRY(call)                                       \
+    do {                                                         \
+        cudaError_t e_ = (call);                                 \
+        if (e_ != cudaSuccess) return stg::cuda_error(e_, #call); \
+    } while (0)

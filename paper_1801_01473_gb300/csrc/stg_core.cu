@@ -1,0 +1,369 @@
+// stg_core.cu -- C ABI: lattice and gauge handles, field packing, D_eo / D_oe and the
+// shifted normal operator (Sec. 2, Eq. shift_eo; link compression and phases, Sec. 4.1).
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+
+#include "stg_common.h"
+
+namespace stg {
+
+static thread_local std::string g_last_error;
+
+stg_status set_error(stg_status s, const std::string &msg)
+{
+    g_last_error = msg;
+    return s;
+}
+
+stg_status cuda_error(cudaError_t e, const char *where)
+{
+    std::string m = std::string(where) + ": " + cudaGetErrorName(e) + " (" + cudaGetErrorString(e) + ")";
+    return set_error(e == cudaErrorMemoryAllocation ? STG_ERR_OOM : STG_ERR_CUDA, m);
+}
+
+int link_bytes(int kind)
+{
+    switch (kind) {
+    case kF64R18: return LinkF64R18::kBytes;
+    case kF64R12: return LinkF64R12::kBytes;
+    case kF32R18: return LinkF32R18::kBytes;
+    case kF32R12: return LinkF32R12::kBytes;
+    case kBF16R12: return Link16R12<__nv_bfloat16>::kBytes;
+    case kF16R12: return Link16R12<__half>::kBytes;
+    }
+    return 0;
+}
+
+cudaError_t launch_dslash(int kind, const DArgs &a, int mode, cudaStream_t st)
+{
+    switch (kind) {
+    case kF64R18: return launch_dslash_f64r18(a, mode, st);
+    case kF64R12: return launch_dslash_f64r12(a, mode, st);
+    case kF32R18: return launch_dslash_f32r18(a, mode, st);
+    case kF32R12: return launch_dslash_f32r12(a, mode, st);
+    case kBF16R12: return launch_dslash_bf16r12(a, mode, st);
+    case kF16R12: return launch_dslash_f16r12(a, mode, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// ------------------------------------------------------------------ packing kernels
+
+// One thread per link (mu, i): canonical [mu][i][3][3] complex128 -> block (mu, parity(i)) at i>>1.
+template <typename LinkT>
+__global__ void k_pack_links(Geom g, const double2 *__restrict__ canon, void *__restrict__ links)
+{
+    long long V = 2LL * g.Vh;
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= 4 * V) return;
+    int mu = (int)(tid / V);
+    int i = (int)(tid - (long long)mu * V);
+    int x = i % g.L[0], r = i / g.L[0];
+    int y = r % g.L[1], r2 = r / g.L[1];
+    int z = r2 % g.L[2], t = r2 / g.L[2];
+    int par = (x + y + z + t) & 1;
+    double2 m[9];
+    for (int k = 0; k < 9; ++k) m[k] = canon[tid * 9 + k];
+    void *blk = static_cast<char *>(links) + (size_t)(mu * 2 + par) * g.Vh * LinkT::kBytes;
+    LinkT::pack(blk, g.Vh, i >> 1, m);
+}
+
+template <typename LinkT>
+static cudaError_t pack_links_t(const Geom &g, const void *canon, void *links, cudaStream_t st)
+{
+    long long n = 4LL * 2 * g.Vh;
+    int bs = 256;
+    k_pack_links<LinkT><<<(unsigned)((n + bs - 1) / bs), bs, 0, st>>>(g, static_cast<const double2 *>(canon), links);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_links(int kind, const Geom &g, const void *canon, void *links, cudaStream_t st)
+{
+    switch (kind) {
+    case kF64R18: return pack_links_t<LinkF64R18>(g, canon, links, st);
+    case kF64R12: return pack_links_t<LinkF64R12>(g, canon, links, st);
+    case kF32R18: return pack_links_t<LinkF32R18>(g, canon, links, st);
+    case kF32R12: return pack_links_t<LinkF32R12>(g, canon, links, st);
+    case kBF16R12: return pack_links_t<Link16R12<__nv_bfloat16>>(g, canon, links, st);
+    case kF16R12: return pack_links_t<Link16R12<__half>>(g, canon, links, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
+// canonical [Vh][3] complex128 <-> internal field
+template <typename R>
+__global__ void k_pack_field(int Vh, const double2 *__restrict__ canon, void *__restrict__ out)
+{
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    cx<R> v[3];
+    for (int c = 0; c < 3; ++c) {
+        double2 d = canon[(size_t)h * 3 + c];
+        v[c] = cx<R>{(R)d.x, (R)d.y};
+    }
+    Field<R>::store(out, Vh, h, v);
+}
+
+template <typename R>
+__global__ void k_unpack_field(int Vh, const void *__restrict__ in, double2 *__restrict__ canon)
+{
+    int h = blockIdx.x * blockDim.x + threadIdx.x;
+    if (h >= Vh) return;
+    cx<R> v[3];
+    Field<R>::load_rw(in, Vh, h, v);
+    for (int c = 0; c < 3; ++c) canon[(size_t)h * 3 + c] = make_double2((double)v[c].re, (double)v[c].im);
+}
+
+// fixed-order sum of n partials into *out (one block)
+__global__ void k_sum_partials(const double *__restrict__ part, int n, double *__restrict__ out)
+{
+    __shared__ double sh[32];
+    double s = 0.0;
+    for (int k = threadIdx.x; k < n; k += blockDim.x) s += part[k];
+    s = block_sum(s, sh);
+    if (threadIdx.x == 0) *out = s;
+}
+
+}  // namespace stg
+
+using namespace stg;
+
+// ------------------------------------------------------------------ C ABI
+
+static bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15u) == 0; }
+
+extern "C" {
+
+const char *stg_status_string(stg_status s)
+{
+    switch (s) {
+    case STG_OK: return "STG_OK";
+    case STG_ERR_ARG: return "STG_ERR_ARG: invalid argument";
+    case STG_ERR_SHAPE: return "STG_ERR_SHAPE: invalid lattice shape";
+    case STG_ERR_CUDA: return "STG_ERR_CUDA: CUDA runtime error";
+    case STG_ERR_NOCONV: return "STG_ERR_NOCONV: solver did not converge";
+    case STG_ERR_TIMEOUT: return "STG_ERR_TIMEOUT: bounded device wait gave up";
+    case STG_ERR_OOM: return "STG_ERR_OOM: device allocation failed";
+    }
+    return "STG_ERR_UNKNOWN";
+}
+
+const char *stg_last_error(void) { return g_last_error.c_str(); }
+
+const char *stg_version(void) { return "stg 0.1 (sm_103a)"; }
+
+stg_status stg_lattice_create(const int32_t dims[4], int32_t t_antiperiodic, stg_lattice **out)
+{
+    if (!dims || !out) return set_error(STG_ERR_ARG, "stg_lattice_create: null pointer");
+    *out = nullptr;
+    long long V = 1;
+    for (int k = 0; k < 4; ++k) {
+        if (dims[k] < 2 || (dims[k] & 1))
+            return set_error(STG_ERR_SHAPE, "stg_lattice_create: every extent must be even and >= 2");
+        V *= dims[k];
+    }
+    if (V > (1LL << 31)) return set_error(STG_ERR_SHAPE, "stg_lattice_create: volume above 2^31 sites");
+    stg_lattice *l = new (std::nothrow) stg_lattice;
+    if (!l) return set_error(STG_ERR_OOM, "stg_lattice_create: host allocation");
+    for (int k = 0; k < 4; ++k) l->g.L[k] = dims[k];
+    l->g.Vh = (int)(V / 2);
+    l->g.antiperiodic = t_antiperiodic ? 1 : 0;
+    l->V = V;
+    *out = l;
+    return STG_OK;
+}
+
+void stg_lattice_destroy(stg_lattice *lat) { delete lat; }
+
+int64_t stg_lattice_sites(const stg_lattice *lat, int32_t parity)
+{
+    if (!lat) return -1;
+    if (parity == 0 || parity == 1) return lat->g.Vh;
+    if (parity == -1) return lat->V;
+    return -1;
+}
+
+stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, stg_prec prec, stg_recon recon,
+                            void *stream, stg_gauge **out)
+{
+    if (!lat || !links_c128_dev || !out) return set_error(STG_ERR_ARG, "stg_gauge_create: null pointer");
+    *out = nullptr;
+    if (!aligned16(links_c128_dev)) return set_error(STG_ERR_ARG, "stg_gauge_create: links not 16-byte aligned");
+    int kind = -1;
+    if (recon != STG_RECON18 && recon != STG_RECON12) return set_error(STG_ERR_ARG, "stg_gauge_create: bad recon");
+    switch (prec) {
+    case STG_F64: kind = recon == STG_RECON18 ? kF64R18 : kF64R12; break;
+    case STG_F32: kind = recon == STG_RECON18 ? kF32R18 : kF32R12; break;
+    case STG_BF16: kind = recon == STG_RECON12 ? kBF16R12 : -1; break;
+    case STG_F16: kind = recon == STG_RECON12 ? kF16R12 : -1; break;
+    default: break;
+    }
+    if (kind < 0) return set_error(STG_ERR_ARG, "stg_gauge_create: unsupported precision/compression pair");
+
+    stg_gauge *g = new (std::nothrow) stg_gauge;
+    if (!g) return set_error(STG_ERR_OOM, "stg_gauge_create: host allocation");
+    g->lat = lat;
+    g->g = lat->g;
+    g->prec = prec;
+    g->recon = recon;
+    g->kind = kind;
+    g->bytes = (size_t)4 * lat->V * link_bytes(kind);
+    g->links = nullptr;
+    g->scratch = nullptr;
+    g->scratch_count = (size_t)kMaxRhs * ((lat->g.Vh + kDslashBlock - 1) / kDslashBlock);
+    cudaError_t e = cudaMalloc(&g->links, g->bytes);
+    if (e == cudaSuccess) e = cudaMalloc(&g->scratch, g->scratch_count * sizeof(double));
+    if (e == cudaSuccess) e = launch_pack_links(kind, lat->g, links_c128_dev, g->links, (cudaStream_t)stream);
+    if (e != cudaSuccess) {
+        stg_status s = cuda_error(e, "stg_gauge_create");
+        cudaFree(g->links);
+        cudaFree(g->scratch);
+        delete g;
+        return s;
+    }
+    *out = g;
+    return STG_OK;
+}
+
+void stg_gauge_destroy(stg_gauge *g)
+{
+    if (!g) return;
+    cudaFree(g->links);
+    cudaFree(g->scratch);
+    delete g;
+}
+
+size_t stg_gauge_bytes(const stg_gauge *g) { return g ? g->bytes : 0; }
+
+size_t stg_field_bytes(const stg_lattice *lat, stg_prec vec_prec)
+{
+    if (!lat) return 0;
+    if (vec_prec == STG_F64) return (size_t)lat->g.Vh * Field<double>::kBytesPerSite;
+    if (vec_prec == STG_F32) return (size_t)lat->g.Vh * Field<float>::kBytesPerSite;
+    return 0;
+}
+
+stg_status stg_field_pack(const stg_lattice *lat, stg_prec vec_prec, const void *canon_c128_dev, void *internal_dev,
+                          void *stream)
+{
+    if (!lat || !canon_c128_dev || !internal_dev) return set_error(STG_ERR_ARG, "stg_field_pack: null pointer");
+    if (!aligned16(canon_c128_dev) || !aligned16(internal_dev))
+        return set_error(STG_ERR_ARG, "stg_field_pack: pointers must be 16-byte aligned");
+    int Vh = lat->g.Vh, bs = 256;
+    if (vec_prec == STG_F64)
+        k_pack_field<double><<<(Vh + bs - 1) / bs, bs, 0, (cudaStream_t)stream>>>(Vh, (const double2 *)canon_c128_dev,
+                                                                                  internal_dev);
+    else if (vec_prec == STG_F32)
+        k_pack_field<float><<<(Vh + bs - 1) / bs, bs, 0, (cudaStream_t)stream>>>(Vh, (const double2 *)canon_c128_dev,
+                                                                                 internal_dev);
+    else
+        return set_error(STG_ERR_ARG, "stg_field_pack: vector precision must be F64 or F32");
+    STG_CUDA_TRY(cudaGetLastError());
+    return STG_OK;
+}
+
+stg_status stg_field_unpack(const stg_lattice *lat, stg_prec vec_prec, const void *internal_dev, void *canon_c128_dev,
+                            void *stream)
+{
+    if (!lat || !canon_c128_dev || !internal_dev) return set_error(STG_ERR_ARG, "stg_field_unpack: null pointer");
+    if (!aligned16(canon_c128_dev) || !aligned16(internal_dev))
+        return set_error(STG_ERR_ARG, "stg_field_unpack: pointers must be 16-byte aligned");
+    int Vh = lat->g.Vh, bs = 256;
+    if (vec_prec == STG_F64)
+        k_unpack_field<double><<<(Vh + bs - 1) / bs, bs, 0, (cudaStream_t)stream>>>(Vh, internal_dev,
+                                                                                    (double2 *)canon_c128_dev);
+    else if (vec_prec == STG_F32)
+        k_unpack_field<float><<<(Vh + bs - 1) / bs, bs, 0, (cudaStream_t)stream>>>(Vh, internal_dev,
+                                                                                   (double2 *)canon_c128_dev);
+    else
+        return set_error(STG_ERR_ARG, "stg_field_unpack: vector precision must be F64 or F32");
+    STG_CUDA_TRY(cudaGetLastError());
+    return STG_OK;
+}
+
+stg_status stg_dslash_multi(const stg_gauge *g, int32_t out_parity, int32_t nrhs, void *out_dev, const void *in_dev,
+                            size_t stride_bytes, void *stream)
+{
+    if (!g || !out_dev || !in_dev) return set_error(STG_ERR_ARG, "stg_dslash: null pointer");
+    if (out_parity != 0 && out_parity != 1) return set_error(STG_ERR_ARG, "stg_dslash: out_parity must be 0 or 1");
+    if (nrhs < 1 || nrhs > 64) return set_error(STG_ERR_ARG, "stg_dslash: nrhs must be in 1..64");
+    size_t fb = (size_t)g->g.Vh * (kind_is_f64(g->kind) ? 48 : 24);
+    if (nrhs > 1 && (stride_bytes < fb || (stride_bytes & 15)))
+        return set_error(STG_ERR_ARG, "stg_dslash: stride must be >= the field size and a multiple of 16 bytes");
+    if (!aligned16(out_dev) || !aligned16(in_dev)) return set_error(STG_ERR_ARG, "stg_dslash: pointers must be 16-byte aligned");
+    const char *ib = static_cast<const char *>(in_dev);
+    char *ob = static_cast<char *>(out_dev);
+    if (ib < ob + (nrhs - 1) * stride_bytes + fb && ob < ib + (nrhs - 1) * stride_bytes + fb)
+        return set_error(STG_ERR_ARG, "stg_dslash: input and output overlap");
+    for (int base = 0; base < nrhs;) {
+        DArgs a;
+        memset(&a, 0, sizeof(a));
+        a.out_par = out_parity;
+        int ng = 0;
+        while (ng < kMaxGroups && base < nrhs) {
+            DGroup &G = a.grp[ng++];
+            G.g = g->g;
+            G.links = g->links;
+            G.nrhs = (nrhs - base) < kMaxRhs ? (nrhs - base) : kMaxRhs;
+            for (int j = 0; j < G.nrhs; ++j) {
+                G.in[j] = ib + (size_t)(base + j) * stride_bytes;
+                G.out[j] = ob + (size_t)(base + j) * stride_bytes;
+            }
+            base += G.nrhs;
+        }
+        a.ngroups = ng;
+        STG_CUDA_TRY(launch_dslash(g->kind, a, 0, (cudaStream_t)stream));
+    }
+    return STG_OK;
+}
+
+stg_status stg_dslash_eo(const stg_gauge *g, void *out_even_dev, const void *in_odd_dev, void *stream)
+{
+    return stg_dslash_multi(g, 0, 1, out_even_dev, in_odd_dev, 0, stream);
+}
+
+stg_status stg_dslash_oe(const stg_gauge *g, void *out_odd_dev, const void *in_even_dev, void *stream)
+{
+    return stg_dslash_multi(g, 1, 1, out_odd_dev, in_even_dev, 0, stream);
+}
+
+stg_status stg_normal_op(const stg_gauge *g, double mass, double shift, void *out_even_dev, const void *in_even_dev,
+                         void *tmp_odd_dev, double *pq_dev, void *stream)
+{
+    if (!g || !out_even_dev || !in_even_dev || !tmp_odd_dev) return set_error(STG_ERR_ARG, "stg_normal_op: null pointer");
+    if (!aligned16(out_even_dev) || !aligned16(in_even_dev) || !aligned16(tmp_odd_dev))
+        return set_error(STG_ERR_ARG, "stg_normal_op: pointers must be 16-byte aligned");
+    if (out_even_dev == in_even_dev || tmp_odd_dev == in_even_dev || tmp_odd_dev == out_even_dev)
+        return set_error(STG_ERR_ARG, "stg_normal_op: in, out and tmp must be distinct");
+    cudaStream_t st = (cudaStream_t)stream;
+    DArgs a;
+    memset(&a, 0, sizeof(a));
+    a.ngroups = 1;
+    DGroup &G = a.grp[0];
+    G.g = g->g;
+    G.links = g->links;
+    G.nrhs = 1;
+    // D_oe: even -> odd
+    a.out_par = 1;
+    G.in[0] = in_even_dev;
+    G.out[0] = tmp_odd_dev;
+    STG_CUDA_TRY(launch_dslash(g->kind, a, 0, st));
+    // D_eo with the fused epilogue out = (m^2 + shift) in - D_eo tmp, partial Re<in, out>
+    a.out_par = 0;
+    G.in[0] = tmp_odd_dev;
+    G.out[0] = out_even_dev;
+    G.epi_p[0] = in_even_dev;
+    G.coef[0] = mass * mass + shift;
+    G.partial[0] = pq_dev ? g->scratch : nullptr;
+    STG_CUDA_TRY(launch_dslash(g->kind, a, 1, st));
+    if (pq_dev) {
+        int nb = (g->g.Vh + kDslashBlock - 1) / kDslashBlock;
+        k_sum_partials<<<1, 256, 0, st>>>(g->scratch, nb, pq_dev);
+        STG_CUDA_TRY(cudaGetLastError());
+    }
+    return STG_OK;
+}
+
+}  // extern "C"

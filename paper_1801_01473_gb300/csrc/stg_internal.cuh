@@ -1,0 +1,374 @@
+// stg_internal.cuh -- device-side building blocks of the staggered hot path:
+// complex arithmetic, internal field and link layouts, lattice geometry.
+//
+// Layouts (all structure-of-arrays over the Vh sites of one parity, so a warp
+// reading 32 consecutive half indices issues fully coalesced 8- or 16-byte loads):
+//   F64 field   3 x Vh double2 (one array per colour)                       48 B/site
+//   F32 field   Vh float4 (colours 0,1) then Vh float2 (colour 2)           24 B/site
+//   links       [mu][parity][chunks over Vh] per (precision, compression):
+//     F64/18    9 x Vh double2      U00 U01 U02 U10 U11 U12 U20 U21 U22      144 B
+//     F64/12    6 x Vh double2      rows 0 and 1                             96 B
+//     F32/18    4 x Vh float4 + Vh float2 (U00U01 U02U10 U11U12 U20U21, U22)  72 B
+//     F32/12    3 x Vh float4       (U00U01 U02U10 U11U12)                   48 B
+//     16/12     Vh x 8 halves + Vh x 4 halves (U00..U10, U11 U12)            24 B
+// Row 3 of a 12-real link is rebuilt as (r1 x r2)^* (link compression, Sec. 4.1).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <stdint.h>
+
+namespace stg {
+
+constexpr int kMaxShifts = 32;
+
+// ------------------------------------------------------------------ complex
+
+template <typename R>
+struct cx {
+    R re, im;
+};
+
+template <typename R>
+__device__ __forceinline__ cx<R> cmk(R a, R b) { return cx<R>{a, b}; }
+
+// acc += a * b
+template <typename R>
+__device__ __forceinline__ void cmac(cx<R> &acc, const cx<R> &a, const cx<R> &b)
+{
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(-a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(a.im, b.re, acc.im);
+}
+
+// acc += conj(a) * b
+template <typename R>
+__device__ __forceinline__ void cmac_conj(cx<R> &acc, const cx<R> &a, const cx<R> &b)
+{
+    acc.re = fma(a.re, b.re, acc.re);
+    acc.re = fma(a.im, b.im, acc.re);
+    acc.im = fma(a.re, b.im, acc.im);
+    acc.im = fma(-a.im, b.re, acc.im);
+}
+
+template <typename R>
+__device__ __forceinline__ cx<R> cmul(const cx<R> &a, const cx<R> &b)
+{
+    return cx<R>{a.re * b.re - a.im * b.im, a.re * b.im + a.im * b.re};
+}
+
+template <typename R>
+__device__ __forceinline__ cx<R> cconj(const cx<R> &a) { return cx<R>{a.re, -a.im}; }
+
+// third row of an SU(3) matrix from the first two: r3 = (r1 x r2)^*
+template <typename R>
+__device__ __forceinline__ void reconstruct_row3(cx<R> U[3][3])
+{
+    cx<R> a = cmul(U[0][1], U[1][2]), b = cmul(U[0][2], U[1][1]);
+    U[2][0] = cx<R>{a.re - b.re, -(a.im - b.im)};
+    a = cmul(U[0][2], U[1][0]); b = cmul(U[0][0], U[1][2]);
+    U[2][1] = cx<R>{a.re - b.re, -(a.im - b.im)};
+    a = cmul(U[0][0], U[1][1]); b = cmul(U[0][1], U[1][0]);
+    U[2][2] = cx<R>{a.re - b.re, -(a.im - b.im)};
+}
+
+// ------------------------------------------------------------------ geometry
+
+struct Geom {
+    int L[4];       // Lx Ly Lz Lt
+    int Vh;         // sites per parity
+    int antiperiodic;
+};
+
+// Coordinates and lexicographic index of the site with half index h on parity par.
+struct Site {
+    int x, y, z, t;
+    int i;  // lexicographic index
+};
+
+__device__ __forceinline__ Site site_of(const Geom &g, int par, int h)
+{
+    Site s;
+    int lxh = g.L[0] >> 1;
+    int r = h / lxh;
+    int xh = h - r * lxh;
+    s.y = r % g.L[1];
+    int r2 = r / g.L[1];
+    s.z = r2 % g.L[2];
+    s.t = r2 / g.L[2];
+    int odd = (par + s.y + s.z + s.t) & 1;
+    s.x = 2 * xh + odd;
+    s.i = 2 * h + odd;
+    return s;
+}
+
+// Half indices of the forward/backward neighbours along mu (periodic wrap), and
+// the link phases u_mu(x) and u_mu(x-mu) of the forward and backward hops.
+struct Hop {
+    int hf, hb;
+    float sf, sb;
+};
+
+__device__ __forceinline__ Hop hop_of(const Geom &g, const Site &s, int mu)
+{
+    Hop o;
+    int c, L, stride;
+    if (mu == 0) { c = s.x; L = g.L[0]; stride = 1; }
+    else if (mu == 1) { c = s.y; L = g.L[1]; stride = g.L[0]; }
+    else if (mu == 2) { c = s.z; L = g.L[2]; stride = g.L[0] * g.L[1]; }
+    else { c = s.t; L = g.L[3]; stride = g.L[0] * g.L[1] * g.L[2]; }
+    int f = (c == L - 1) ? s.i - (L - 1) * stride : s.i + stride;
+    int b = (c == 0) ? s.i + (L - 1) * stride : s.i - stride;
+    o.hf = f >> 1;
+    o.hb = b >> 1;
+    // staggered phase eta_mu(x) = (-1)^(x_0 + ... + x_{mu-1}); it does not depend on x_mu,
+    // so the backward link (x - mu, mu) carries the same eta.
+    int e = (mu == 0) ? 0 : (mu == 1) ? s.x : (mu == 2) ? (s.x + s.y) : (s.x + s.y + s.z);
+    float eta = (e & 1) ? -1.f : 1.f;
+    o.sf = eta;
+    o.sb = eta;
+    if (mu == 3 && g.antiperiodic) {
+        if (s.t == L - 1) o.sf = -o.sf;  // forward link sits on x_t = Lt-1
+        if (s.t == 0) o.sb = -o.sb;      // backward link (x - t) sits on x_t = Lt-1
+    }
+    return o;
+}
+
+// ------------------------------------------------------------------ fields
+
+template <typename R>
+struct Field;
+
+template <>
+struct Field<double> {
+    static constexpr int kBytesPerSite = 48;
+    __device__ __forceinline__ static void load(const void *base, int Vh, int h, cx<double> v[3])
+    {
+        const double2 *p = static_cast<const double2 *>(base);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double2 d = __ldg(p + (size_t)c * Vh + h);
+            v[c] = cx<double>{d.x, d.y};
+        }
+    }
+    __device__ __forceinline__ static void store(void *base, int Vh, int h, const cx<double> v[3])
+    {
+        double2 *p = static_cast<double2 *>(base);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[(size_t)c * Vh + h] = make_double2(v[c].re, v[c].im);
+    }
+    // plain (non-texture-path) load for buffers written earlier in the same kernel sequence
+    __device__ __forceinline__ static void load_rw(const void *base, int Vh, int h, cx<double> v[3])
+    {
+        const double2 *p = static_cast<const double2 *>(base);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            double2 d = p[(size_t)c * Vh + h];
+            v[c] = cx<double>{d.x, d.y};
+        }
+    }
+};
+
+template <>
+struct Field<float> {
+    static constexpr int kBytesPerSite = 24;
+    __device__ __forceinline__ static void load(const void *base, int Vh, int h, cx<float> v[3])
+    {
+        const float4 *a = static_cast<const float4 *>(base);
+        const float2 *b = reinterpret_cast<const float2 *>(a + Vh);
+        float4 u = __ldg(a + h);
+        float2 w = __ldg(b + h);
+        v[0] = cx<float>{u.x, u.y};
+        v[1] = cx<float>{u.z, u.w};
+        v[2] = cx<float>{w.x, w.y};
+    }
+    __device__ __forceinline__ static void store(void *base, int Vh, int h, const cx<float> v[3])
+    {
+        float4 *a = static_cast<float4 *>(base);
+        float2 *b = reinterpret_cast<float2 *>(a + Vh);
+        a[h] = make_float4(v[0].re, v[0].im, v[1].re, v[1].im);
+        b[h] = make_float2(v[2].re, v[2].im);
+    }
+    __device__ __forceinline__ static void load_rw(const void *base, int Vh, int h, cx<float> v[3])
+    {
+        const float4 *a = static_cast<const float4 *>(base);
+        const float2 *b = reinterpret_cast<const float2 *>(a + Vh);
+        float4 u = a[h];
+        float2 w = b[h];
+        v[0] = cx<float>{u.x, u.y};
+        v[1] = cx<float>{u.z, u.w};
+        v[2] = cx<float>{w.x, w.y};
+    }
+};
+
+// ------------------------------------------------------------------ links
+// Each link type: real type R used for arithmetic, bytes per link, loader
+// into a full 3x3 complex matrix, and a packer from a canonical 3x3 complex128.
+
+struct LinkF64R18 {
+    using R = double;
+    static constexpr int kBytes = 144;
+    __device__ __forceinline__ static void load(const void *blk, int Vh, int h, cx<double> U[3][3])
+    {
+        const double2 *p = static_cast<const double2 *>(blk);
+#pragma unroll
+        for (int k = 0; k < 9; ++k) {
+            double2 d = __ldg(p + (size_t)k * Vh + h);
+            U[k / 3][k % 3] = cx<double>{d.x, d.y};
+        }
+    }
+    __device__ __forceinline__ static void pack(void *blk, int Vh, int h, const double2 *m)
+    {
+        double2 *p = static_cast<double2 *>(blk);
+        for (int k = 0; k < 9; ++k) p[(size_t)k * Vh + h] = m[k];
+    }
+};
+
+struct LinkF64R12 {
+    using R = double;
+    static constexpr int kBytes = 96;
+    __device__ __forceinline__ static void load(const void *blk, int Vh, int h, cx<double> U[3][3])
+    {
+        const double2 *p = static_cast<const double2 *>(blk);
+#pragma unroll
+        for (int k = 0; k < 6; ++k) {
+            double2 d = __ldg(p + (size_t)k * Vh + h);
+            U[k / 3][k % 3] = cx<double>{d.x, d.y};
+        }
+        reconstruct_row3(U);
+    }
+    __device__ __forceinline__ static void pack(void *blk, int Vh, int h, const double2 *m)
+    {
+        double2 *p = static_cast<double2 *>(blk);
+        for (int k = 0; k < 6; ++k) p[(size_t)k * Vh + h] = m[k];
+    }
+};
+
+struct LinkF32R18 {
+    using R = float;
+    static constexpr int kBytes = 72;
+    __device__ __forceinline__ static void load(const void *blk, int Vh, int h, cx<float> U[3][3])
+    {
+        const float4 *p = static_cast<const float4 *>(blk);
+        const float2 *q = reinterpret_cast<const float2 *>(p + 4 * (size_t)Vh);
+#pragma unroll
+        for (int k = 0; k < 4; ++k) {
+            float4 d = __ldg(p + (size_t)k * Vh + h);
+            U[(2 * k) / 3][(2 * k) % 3] = cx<float>{d.x, d.y};
+            U[(2 * k + 1) / 3][(2 * k + 1) % 3] = cx<float>{d.z, d.w};
+        }
+        float2 e = __ldg(q + h);
+        U[2][2] = cx<float>{e.x, e.y};
+    }
+    __device__ __forceinline__ static void pack(void *blk, int Vh, int h, const double2 *m)
+    {
+        float4 *p = static_cast<float4 *>(blk);
+        float2 *q = reinterpret_cast<float2 *>(p + 4 * (size_t)Vh);
+        for (int k = 0; k < 4; ++k)
+            p[(size_t)k * Vh + h] = make_float4((float)m[2 * k].x, (float)m[2 * k].y, (float)m[2 * k + 1].x,
+                                                (float)m[2 * k + 1].y);
+        q[h] = make_float2((float)m[8].x, (float)m[8].y);
+    }
+};
+
+struct LinkF32R12 {
+    using R = float;
+    static constexpr int kBytes = 48;
+    __device__ __forceinline__ static void load(const void *blk, int Vh, int h, cx<float> U[3][3])
+    {
+        const float4 *p = static_cast<const float4 *>(blk);
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            float4 d = __ldg(p + (size_t)k * Vh + h);
+            U[(2 * k) / 3][(2 * k) % 3] = cx<float>{d.x, d.y};
+            U[(2 * k + 1) / 3][(2 * k + 1) % 3] = cx<float>{d.z, d.w};
+        }
+        reconstruct_row3(U);
+    }
+    __device__ __forceinline__ static void pack(void *blk, int Vh, int h, const double2 *m)
+    {
+        float4 *p = static_cast<float4 *>(blk);
+        for (int k = 0; k < 3; ++k)
+            p[(size_t)k * Vh + h] = make_float4((float)m[2 * k].x, (float)m[2 * k].y, (float)m[2 * k + 1].x,
+                                                (float)m[2 * k + 1].y);
+    }
+};
+
+// 16-bit storage (bf16 or fp16) of the two first rows; arithmetic in FP32.
+template <typename H>
+struct Half;
+template <>
+struct Half<__nv_bfloat16> {
+    __device__ __forceinline__ static float to_f(uint16_t b) { return __bfloat162float(__ushort_as_bfloat16(b)); }
+    __device__ __forceinline__ static uint16_t from_d(double v) { return __bfloat16_as_ushort(__double2bfloat16(v)); }
+};
+template <>
+struct Half<__half> {
+    __device__ __forceinline__ static float to_f(uint16_t b) { return __half2float(__ushort_as_half(b)); }
+    __device__ __forceinline__ static uint16_t from_d(double v) { return __half_as_ushort(__double2half(v)); }
+};
+
+template <typename H>
+struct Link16R12 {
+    using R = float;
+    static constexpr int kBytes = 24;
+    __device__ __forceinline__ static void load(const void *blk, int Vh, int h, cx<float> U[3][3])
+    {
+        const uint4 *p = static_cast<const uint4 *>(blk);
+        const uint2 *q = reinterpret_cast<const uint2 *>(p + Vh);
+        uint4 a = __ldg(p + h);
+        uint2 b = __ldg(q + h);
+        uint32_t w[6] = {a.x, a.y, a.z, a.w, b.x, b.y};
+#pragma unroll
+        for (int k = 0; k < 6; ++k)
+            U[k / 3][k % 3] = cx<float>{Half<H>::to_f((uint16_t)(w[k] & 0xffffu)), Half<H>::to_f((uint16_t)(w[k] >> 16))};
+        reconstruct_row3(U);
+    }
+    __device__ __forceinline__ static void pack(void *blk, int Vh, int h, const double2 *m)
+    {
+        uint32_t w[6];
+        for (int k = 0; k < 6; ++k)
+            w[k] = (uint32_t)Half<H>::from_d(m[k].x) | ((uint32_t)Half<H>::from_d(m[k].y) << 16);
+        uint4 *p = static_cast<uint4 *>(blk);
+        uint2 *q = reinterpret_cast<uint2 *>(p + Vh);
+        p[h] = make_uint4(w[0], w[1], w[2], w[3]);
+        q[h] = make_uint2(w[4], w[5]);
+    }
+};
+
+// Base of the (mu, parity) block of an internal link array.
+template <typename LinkT>
+__device__ __forceinline__ const void *link_block(const void *links, int Vh, int mu, int par)
+{
+    return static_cast<const char *>(links) + (size_t)(mu * 2 + par) * Vh * LinkT::kBytes;
+}
+
+// ------------------------------------------------------------------ reductions
+
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Deterministic block sum (fixed tree); result valid in thread 0.  `sh` holds >= 32 doubles.
+__device__ __forceinline__ double block_sum(double v, double *sh)
+{
+    v = warp_sum(v);
+    int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+    __syncthreads();
+    if (lane == 0) sh[wid] = v;
+    __syncthreads();
+    double s = 0.0;
+    if (wid == 0) {
+        int nw = (blockDim.x + 31) >> 5;
+        s = lane < nw ? sh[lane] : 0.0;
+        s = warp_sum(s);
+    }
+    return s;
+}
+
+}  // namespace stg

@@ -89,13 +89,12 @@ def gauge_links(dims, kind: str, seed: int) -> np.ndarray:
     if kind == "unit":
         return unit_links(dims)
     g = rng(seed)
-    if kind == "haar":
-        u = haar_su3(g, 4 * v)
-    elif kind == "expih":
-        u = exp_i_h(g, 4 * v, 0.3)
-    else:
+    if kind not in ("haar", "expih"):
         raise ValueError(f"unknown link kind {kind!r}")
-    return u.reshape(4, v, 3, 3)
+    u = np.empty((4, v, 3, 3), np.complex128)
+    for mu in range(4):  # one direction at a time bounds the temporaries
+        u[mu] = haar_su3(g, v) if kind == "haar" else exp_i_h(g, v, 0.3)
+    return u
 
 
 def gaussian_field(dims, seed: int, parity_sites: bool = True) -> np.ndarray:

@@ -1,0 +1,127 @@
+"""Parity of the CUDA D_eo / D_oe / normal operator with the FP64 oracle.
+
+Tolerances (relative max-norm error over the output vector):
+  F64 links, 18 or 12 real    1e-12  (spec bar for FP64 paths)
+  F32 links                   2e-6   (FP32 rounding of links, vectors and 8-term sums)
+  F16 links                   4e-3   (11-bit mantissa of the stored link rows)
+  BF16 links                  3e-2   (8-bit mantissa of the stored link rows)
+"""
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+TOL = {("f64", 18): 1e-12, ("f64", 12): 1e-12, ("f32", 18): 2e-6, ("f32", 12): 2e-6,
+       ("f16", 12): 4e-3, ("bf16", 12): 3e-2}
+VARIANTS = list(TOL)
+# several tiles of 128 sites plus ragged tails; odd-shaped extents
+LATTICES = [(4, 4, 4, 4), (6, 4, 2, 8), (2, 6, 4, 10), (8, 8, 8, 8), (12, 10, 6, 4)]
+
+
+def stg():
+    import paper_1801_01473_gb300 as p
+    return p
+
+
+def rel(a, b):
+    a = np.asarray(a)
+    b = np.asarray(b)
+    return np.abs(a - b).max() / np.abs(b).max()
+
+
+_links_cache = {}
+
+
+def links_for(dims, kind="haar", seed=101):
+    key = (dims, kind, seed)
+    if key not in _links_cache:
+        _links_cache[key] = S.gauge_links(dims, kind, seed)
+    return _links_cache[key]
+
+
+@pytest.mark.parametrize("dims", LATTICES)
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_dslash_matches_oracle(dims, variant):
+    p = stg()
+    prec, recon = variant
+    u = links_for(dims)
+    lat = p.Lattice(dims)
+    g = p.Gauge(lat, torch.from_numpy(u).cuda(), prec, recon)
+    for out_par in (0, 1):
+        psi = S.gaussian_field(dims, 200 + out_par)
+        ref = oracle.dslash(dims, u, out_par, psi)
+        fn = p.dslash_eo if out_par == 0 else p.dslash_oe
+        got = fn(g, torch.from_numpy(psi).cuda()).cpu().numpy()
+        assert rel(got, ref) <= TOL[variant], (dims, variant, out_par, rel(got, ref))
+
+
+@pytest.mark.parametrize("variant", VARIANTS)
+def test_normal_op_and_fused_dot(variant):
+    p = stg()
+    prec, recon = variant
+    dims, mass, shift = (6, 4, 2, 8), 0.1, 0.03
+    u = links_for(dims)
+    lat = p.Lattice(dims)
+    g = p.Gauge(lat, torch.from_numpy(u).cuda(), prec, recon)
+    psi = S.gaussian_field(dims, 301)
+    ref = oracle.normal_op(dims, u, mass, shift, psi)
+    x = p.pack(lat, torch.from_numpy(psi).cuda(), g.vec_prec)
+    out, tmp = torch.empty_like(x), torch.empty_like(x)
+    pq = torch.zeros(1, dtype=torch.float64, device="cuda")
+    p.normal_op_(g, mass, shift, out, x, tmp, pq)
+    got = p.unpack(lat, out).cpu().numpy()
+    assert rel(got, ref) <= 4 * TOL[variant]
+    pq_ref = np.vdot(psi, ref).real
+    assert abs(pq.item() - pq_ref) <= 4 * TOL[variant] * abs(pq_ref)
+
+
+@pytest.mark.parametrize("variant", [("f64", 18), ("f32", 12), ("bf16", 12)])
+@pytest.mark.parametrize("nrhs", [1, 3, 8, 11])
+def test_multi_rhs_matches_single(variant, nrhs):
+    """Shared link loads over nrhs right-hand sides give bitwise the single-rhs results."""
+    p = stg()
+    prec, recon = variant
+    dims = (8, 4, 6, 4)
+    lat = p.Lattice(dims)
+    g = p.Gauge(lat, torch.from_numpy(links_for(dims)).cuda(), prec, recon)
+    srcs = [S.gaussian_field(dims, 400 + j) for j in range(nrhs)]
+    inp = torch.stack([p.pack(lat, torch.from_numpy(s).cuda(), g.vec_prec) for s in srcs])
+    for out_par in (0, 1):
+        out = torch.empty_like(inp)
+        p.dslash_multi_(g, out_par, out, inp)
+        for j in range(nrhs):
+            one = torch.empty_like(inp[j])
+            (p.dslash_eo_ if out_par == 0 else p.dslash_oe_)(g, one, inp[j].contiguous())
+            assert torch.equal(one, out[j])
+
+
+def test_pack_unpack_roundtrip():
+    p = stg()
+    dims = (6, 4, 2, 8)
+    lat = p.Lattice(dims)
+    psi = torch.from_numpy(S.gaussian_field(dims, 5)).cuda()
+    assert torch.equal(p.unpack(lat, p.pack(lat, psi, "f64")), psi)
+    back = p.unpack(lat, p.pack(lat, psi, "f32"))
+    assert torch.equal(back, psi.to(torch.complex64).to(torch.complex128))
+
+
+def test_full_size_32x32x32x32_sampled():
+    """The benchmarked workload (32^4, exp(i 0.3 H) links, FP32 12-real and FP64 18-real):
+    D_eo over the full lattice against the oracle evaluated on every output site."""
+    p = stg()
+    cfg = S.CONFIGS["bandwidth_32x32x32x32"]
+    dims = cfg["dims"]
+    u = S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])
+    psi = S.gaussian_field(dims, 2000 + cfg["k"], parity_sites=True)
+    ref = oracle.dslash(dims, u, 0, psi)
+    lat = p.Lattice(dims)
+    ut = torch.from_numpy(u).cuda()
+    for prec, recon in [("f32", 12), ("f64", 18), ("bf16", 12)]:
+        g = p.Gauge(lat, ut, prec, recon)
+        got = p.dslash_eo(g, torch.from_numpy(psi).cuda()).cpu().numpy()
+        assert rel(got, ref) <= TOL[(prec, recon)], (prec, recon, rel(got, ref))
+        del g

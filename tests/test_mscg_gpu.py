@@ -1,0 +1,190 @@
+"""Parity of the CUDA multi-shift CG with the FP64 oracle.
+
+Every returned solution is re-checked with the oracle's own FP64 normal
+operator: the bar is the true residual |b - A_i x_i| / |b| <= tol for every
+shift (spec bar for the mixed paths), and for the pure FP64 path also
+agreement of the first multi-shift recurrences with the oracle's (1e-12
+relative) and of the solutions with the oracle's within the condition-number
+bound kappa_i * tol.
+"""
+import os
+
+import numpy as np
+import pytest
+
+import oracle
+import synthetic as S
+
+torch = pytest.importorskip("torch")
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+INNER = [None, ("f32", 12), ("f32", 18), ("f16", 12), ("bf16", 12)]
+
+
+def stg():
+    import paper_1801_01473_gb300 as p
+    return p
+
+
+def gauges(p, dims, u, inner):
+    lat = p.Lattice(dims)
+    ut = torch.from_numpy(u).cuda()
+    g64 = p.Gauge(lat, ut, "f64", 18)
+    gi = p.Gauge(lat, ut, inner[0], inner[1]) if inner else None
+    return lat, g64, gi
+
+
+def oracle_true_resid(dims, u, mass, shifts, b, x):
+    return np.array([oracle.true_residual(dims, u, mass, s, b, x[i]) for i, s in enumerate(shifts)])
+
+
+@pytest.fixture(scope="module")
+def small():
+    cfg = S.CONFIGS["small_4x4x4x4"]
+    dims = cfg["dims"]
+    u = S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])
+    b = S.gaussian_field(dims, 2000 + cfg["k"])
+    return cfg, dims, u, b
+
+
+@pytest.mark.parametrize("inner", INNER)
+def test_small_true_residuals(small, inner):
+    cfg, dims, u, b = small
+    p = stg()
+    shifts = cfg["shifts"]()
+    _, g64, gi = gauges(p, dims, u, inner)
+    x, st = p.mscg(g64, torch.from_numpy(b).cuda(), shifts, cfg["mass"], tol=cfg["tol"], g_inner=gi)
+    x = x.cpu().numpy()
+    tr = oracle_true_resid(dims, u, cfg["mass"], shifts, b, x)
+    assert np.all(tr <= cfg["tol"]), (inner, tr, st)
+    np.testing.assert_allclose(st["true_resid"], tr, rtol=1e-3, atol=1e-14)
+
+
+def test_fp64_recurrences_match_oracle(small):
+    cfg, dims, u, b = small
+    p = stg()
+    ref = np.loadtxt(os.path.join(GOLDEN, "mscg_4x4x4x4_scalars.txt"))
+    _, g64, _ = gauges(p, dims, u, None)
+    x, st = p.mscg(g64, torch.from_numpy(b).cuda(), cfg["shifts"](), cfg["mass"], tol=cfg["tol"], log_rows=25)
+    log = st["scalar_log"]
+    assert log.shape == ref.shape
+    np.testing.assert_allclose(log[:20], ref[:20], rtol=1e-12)
+    o = oracle.mscg(dims, u, cfg["mass"], cfg["shifts"](), b, tol=cfg["tol"])
+    assert abs(st["iters"] - o["iters"]) <= 1
+    # solutions agree within kappa_i * tol
+    a_min, a_max = cfg["mass"] ** 2, cfg["mass"] ** 2 + 16.0
+    for i, s in enumerate(cfg["shifts"]()):
+        err = np.linalg.norm(x[i].cpu().numpy() - o["x"][i]) / np.linalg.norm(o["x"][i])
+        assert err <= 2 * (a_max + s) / (a_min + s) * cfg["tol"]
+
+
+@pytest.mark.parametrize("dims", [(6, 4, 2, 8), (2, 6, 4, 10), (12, 10, 6, 4)])
+@pytest.mark.parametrize("inner", [None, ("f32", 12)])
+def test_ragged_lattices(dims, inner):
+    p = stg()
+    u = S.gauge_links(dims, "expih", 77)
+    b = S.gaussian_field(dims, 78)
+    shifts = [0.0, 1e-3, 0.1, 2.0, 0.05]  # unsorted, base shift first
+    _, g64, gi = gauges(p, dims, u, inner)
+    x, st = p.mscg(g64, torch.from_numpy(b).cuda(), shifts, 0.05, tol=1e-10, g_inner=gi)
+    tr = oracle_true_resid(dims, u, 0.05, shifts, b, x.cpu().numpy())
+    assert np.all(tr <= 1e-10), tr
+
+
+def test_free_field_plane_wave():
+    from tests import latutil as lu
+    p = stg()
+    dims, mass = (8, 4, 4, 6), 0.1
+    n = (1, 2, 3, 1)
+    psi = lu.plane_wave_even(dims, n, [0.3, 1.0j, -0.5])
+    lam = mass ** 2 + np.sum(np.sin(lu.momentum(dims, n)) ** 2)
+    shifts = [1e-4, 0.01, 0.3]
+    _, g64, _ = gauges(p, dims, S.unit_links(dims), None)
+    x, st = p.mscg(g64, torch.from_numpy(psi).cuda(), shifts, mass, tol=1e-12)
+    for i, s in enumerate(shifts):
+        np.testing.assert_allclose(x[i].cpu().numpy(), psi / (lam + s), rtol=0, atol=1e-12 / (lam + s))
+    assert st["iters"] == 1
+
+
+def test_zero_source():
+    p = stg()
+    dims = (4, 4, 4, 4)
+    _, g64, gi = gauges(p, dims, S.gauge_links(dims, "haar", 3), ("f32", 12))
+    b = torch.zeros((128, 3), dtype=torch.complex128, device="cuda")
+    x, st = p.mscg(g64, b, [0.0, 0.1], 0.1, g_inner=gi)
+    assert torch.count_nonzero(x) == 0 and st["true_resid"] == [0.0, 0.0]
+
+
+def test_max_iter_reports_noconv(small):
+    cfg, dims, u, b = small
+    p = stg()
+    _, g64, _ = gauges(p, dims, u, None)
+    from paper_1801_01473_gb300.lib import STG_ERR_NOCONV
+    x, st = p.mscg(g64, torch.from_numpy(b).cuda(), cfg["shifts"](), cfg["mass"], tol=1e-10, max_iter=5,
+                   allow_noconv=True)
+    assert st["status"] == STG_ERR_NOCONV
+    assert st["iters"] == 5 and max(st["true_resid"]) > 1e-10
+    with pytest.raises(p.StgError):
+        p.mscg(g64, torch.from_numpy(b).cuda(), cfg["shifts"](), cfg["mass"], tol=1e-10, max_iter=5)
+
+
+def test_invalid_arguments_rejected():
+    p = stg()
+    dims = (4, 4, 4, 4)
+    lat, g64, gi = gauges(p, dims, S.gauge_links(dims, "haar", 3), ("f32", 12))
+    b = torch.from_numpy(S.gaussian_field(dims, 1)).cuda()
+    with pytest.raises(p.StgError):
+        p.mscg(g64, b, [-1.0], 0.1)              # negative shift
+    with pytest.raises(p.StgError):
+        p.mscg(g64, b, [0.0] * 33, 0.1)          # too many shifts
+    with pytest.raises(p.StgError):
+        p.mscg(gi, b, [0.0], 0.1)                # inner gauge passed as the FP64 gauge
+    other = p.Gauge(p.Lattice((4, 4, 4, 6)), torch.from_numpy(S.gauge_links((4, 4, 4, 6), "haar", 4)).cuda(), "f32", 12)
+    with pytest.raises(p.StgError):
+        p.mscg(g64, b, [0.0], 0.1, g_inner=other)  # lattices differ
+
+
+@pytest.mark.parametrize("inner", [("f32", 12), ("bf16", 12)])
+def test_full_size_32x32x32x32_mixed(inner):
+    """The benchmarked msCG workload: 32^4, 16 poles 1e-5..10, m = 0.01, true residual 1e-10.
+    True residuals of four shifts (the hardest, two middle, the easiest) re-checked by the oracle."""
+    p = stg()
+    cfg = S.CONFIGS["mscg_32x32x32x32"]
+    dims = cfg["dims"]
+    u = S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])
+    b = S.gaussian_field(dims, 2000 + cfg["k"])
+    shifts = cfg["shifts"]()
+    _, g64, gi = gauges(p, dims, u, inner)
+    x, st = p.mscg(g64, torch.from_numpy(b).cuda(), shifts, cfg["mass"], tol=cfg["tol"], g_inner=gi)
+    assert max(st["true_resid"]) <= cfg["tol"]
+    x = x.cpu().numpy()
+    for i in (0, 5, 10, 15):
+        assert oracle.true_residual(dims, u, cfg["mass"], shifts[i], b, x[i]) <= cfg["tol"]
+
+
+def test_batched_uneven_matches_separate_solves():
+    """Four lattices of different sizes, 4 sources each, 16 shifts, solved in one batch;
+    every system's true residual <= tol; each instance agrees with its separate solve."""
+    p = stg()
+    cfg = S.CONFIGS["batched_uneven"]
+    shifts = cfg["shifts"]()
+    insts, keep = [], []
+    for li, dims in enumerate(cfg["dims_list"]):
+        u = S.gauge_links(dims, cfg["links"], 1000 + 10 * cfg["k"] + li)
+        lat, g64, gi = gauges(p, dims, u, ("f32", 12))
+        bs = [torch.from_numpy(S.gaussian_field(dims, 2000 + 10 * cfg["k"] + 4 * li + r)).cuda()
+              for r in range(cfg["nrhs"])]
+        insts.append((g64, gi, bs))
+        keep.append((dims, u, lat))
+    res = p.mscg_batched(insts, shifts, cfg["mass"], tol=cfg["tol"])
+    for (x, stats), (g64, gi, bs), (dims, u, _) in zip(res, insts, keep):
+        for r in range(len(bs)):
+            assert max(stats[r]["true_resid"]) <= cfg["tol"]
+        # one sampled system per lattice re-checked by the oracle, and vs a separate solve
+        xs, _ = p.mscg(g64, bs[1], shifts, cfg["mass"], tol=cfg["tol"], g_inner=gi)
+        b1 = bs[1].cpu().numpy()
+        for i in (0, 15):
+            assert oracle.true_residual(dims, u, cfg["mass"], shifts[i], b1, x[1, i].cpu().numpy()) <= cfg["tol"]
+            rel = (torch.linalg.vector_norm(x[1, i] - xs[i]) / torch.linalg.vector_norm(xs[i])).item()
+            assert rel <= 1e-7

@@ -1,0 +1,416 @@
+"""Benchmark of the staggered hot path on GB300 (one JSON line on stdout).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference] [--batch B] [--no-extras]
+
+Headline metric (metric string as the project defines it):
+  "D_eo GB/s (% HBM peak); msCG s/solve to 1e-10, mixed vs FP64 on 1 GB300"
+value = effective D_eo bandwidth on the 32^4 workload (exp(i 0.3 H) links stored FP32
+12-real, complex64 vectors): algorithmic bytes (all 4V links once + one input and one
+output vector = 432 B per even site) / device time.  One step applies D_eo to a batch of
+B distinct even-site vectors (B launches of the kernel), alternating between two copies of
+the links, so that no step finds its links or vectors in L2 (inputs larger than L2).
+
+The same JSON line carries (measured in the same run, outside the timed steps):
+  e2e        the metric through the public API with host tensors: pinned host -> device
+             copy of each canonical complex128 input, pack, D_eo, unpack, device -> host;
+  roofline   D_eo FP32-12 against the measured HBM copy bandwidth;
+  sweep      16^4 and 32^4 D_eo for every link storage, L2 flushed, median of 50;
+  mscg       32^4 msCG (16 poles 1e-5..10, m = 0.01, true residual 1e-10): mixed
+             (FP32, FP16, BF16 inner, FP64 reliable updates) vs pure FP64, s/solve;
+  batched    the uneven batch (16^4, 24^3x8, 32^3x8, 24^4, 4 sources x 16 shifts) in one
+             solve vs the sum of separate solves;
+  force      48^4 fermion-force time (12 shifts, FP64);
+  cpu_baseline  the FP64 oracle's D_eo on the host cores, bounded sample.
+--impl reference times that oracle as the reference arm (the paper ships no code).
+Multi-GPU: replicas only (independent copies of the workload on every rank).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import re
+import subprocess
+import sys
+import time
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import numpy as np  # noqa: E402
+
+import synthetic as S  # noqa: E402
+
+METRIC = "D_eo GB/s (% HBM peak); msCG s/solve to 1e-10, mixed vs FP64 on 1 GB300"
+UNIT = "GB/s"
+WORKLOAD = "32^4 D_eo, exp(i0.3H) links FP32 12-real, complex64 vectors, batch of distinct sources"
+LINK_BYTES = {("f64", 18): 144, ("f64", 12): 96, ("f32", 18): 72, ("f32", 12): 48, ("bf16", 12): 24,
+              ("f16", 12): 24}
+
+
+def workload_config(batch, ws=1):
+    """The `config` object of the JSON line (shared by both arms)."""
+    return {"workload": WORKLOAD, "lattice": "32x32x32x32", "links": "f32-12", "vectors": "c64",
+            "batch_per_step": batch, "bytes_per_site": bytes_per_site("f32", 12),
+            "l2": "inputs larger than L2: distinct source per launch, two alternating 201 MB link copies",
+            "parallelism": f"replicas x{ws}"}
+
+
+def bytes_per_site(prec, recon):
+    """Algorithmic bytes of one D_eo output site: 8 links (all 4V links once over the
+    lattice) + one input and one output colour vector."""
+    vec = 48 if prec == "f64" else 24
+    return 8 * LINK_BYTES[(prec, recon)] + 2 * vec
+
+
+def dist_env():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return ws, rank, local
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def profile_traffic(name):
+    """dram bytes per launch from a committed ncu summary (profiles/<name>.md), or None."""
+    path = os.path.join(ROOT, "profiles", name)
+    if not os.path.exists(path):
+        return None
+    m = re.search(r"dram_bytes_per_launch:\s*([0-9.eE+]+)", open(path).read())
+    return float(m.group(1)) if m else None
+
+
+class ClockSampler:
+    """nvidia-smi clock/throttle sampling during the timed region."""
+
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, gpu_index=0):
+        self.idx = gpu_index
+        self.proc = None
+        self.path = os.path.join("/tmp", f"stg_clocks_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            self.fh = open(self.path, "w")
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.idx}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "100"],
+                                         stdout=self.fh, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return None
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.fh.close()
+        rows = [r.split(",") for r in open(self.path).read().strip().splitlines() if r.strip()]
+        os.unlink(self.path)
+        if not rows:
+            return None
+        sm = [float(r[1]) for r in rows if r[1].strip().replace(".", "").isdigit()]
+        smax = [float(r[2]) for r in rows if r[2].strip().replace(".", "").isdigit()]
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        reasons = sorted({names[k] for r in rows for k in range(4) if len(r) > 5 + k and "Active" in r[5 + k]
+                          and "Not" not in r[5 + k]})
+        return {"sm_mhz": float(np.median(sm)) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": reasons, "samples": len(rows)}
+
+
+# ---------------------------------------------------------------------------- reference arm
+
+
+def run_reference(args):
+    ws, rank, _ = dist_env()
+    if rank != 0:
+        return 0
+    import oracle
+    oracle.build()
+    dims = S.CONFIGS["bandwidth_32x32x32x32"]["dims"]
+    u = S.gauge_links(dims, "expih", 1000 + 2)
+    psi = S.gaussian_field(dims, 2000 + 2)
+    vh = S.volume(dims) // 2
+    alg = bytes_per_site("f32", 12) * vh
+    for _ in range(args.warmup):
+        oracle.dslash_eo(dims, u, psi)
+    ts = []
+    for _ in range(args.steps):
+        t0 = time.perf_counter()
+        oracle.dslash_eo(dims, u, psi)
+        ts.append(time.perf_counter() - t0)
+    t = float(np.sum(ts))
+    v = alg * args.steps / t / 1e9
+    line = {"metric": METRIC, "value": v, "unit": UNIT, "n_gpus": args.gpus, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": 1e3 * t / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "impl": "reference",
+            "config": workload_config(args.batch, ws),
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                             "sample": f"one FP64 oracle D_eo application at 32^4 per step ({args.steps} steps), "
+                                       "bytes counted as the FP32-12 workload"},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def cpu_baseline(budget_s=12.0):
+    import oracle
+    oracle.build()
+    dims = S.CONFIGS["bandwidth_32x32x32x32"]["dims"]
+    u = S.gauge_links(dims, "expih", 1000 + 2)
+    psi = S.gaussian_field(dims, 2000 + 2)
+    vh = S.volume(dims) // 2
+    oracle.dslash_eo(dims, u, psi)
+    n, t = 0, 0.0
+    while t < budget_s and n < 50:
+        t0 = time.perf_counter()
+        oracle.dslash_eo(dims, u, psi)
+        t += time.perf_counter() - t0
+        n += 1
+    return {"value": bytes_per_site("f32", 12) * vh * n / t / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{n} FP64 oracle D_eo applications at 32^4 ({t:.1f} s), bytes counted as the FP32-12 workload"}
+
+
+# ---------------------------------------------------------------------------- GPU arm
+
+
+def events(torch):
+    return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+
+
+def time_deo_sweep(torch, p, dims, reps=50):
+    """D_eo per storage kind, L2 flushed before every call, median of reps."""
+    cfg_links = S.gauge_links(dims, "expih", 1000 + 2)
+    ut = torch.from_numpy(cfg_links).cuda()
+    lat = p.Lattice(dims)
+    psi = torch.from_numpy(S.gaussian_field(dims, 2000 + 2)).cuda()
+    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    out = []
+    for prec, recon in [("f64", 18), ("f64", 12), ("f32", 18), ("f32", 12), ("f16", 12), ("bf16", 12)]:
+        g = p.Gauge(lat, ut, prec, recon)
+        x = p.pack(lat, psi, g.vec_prec)
+        y = torch.empty_like(x)
+        for _ in range(5):
+            p.dslash_eo_(g, y, x)
+        ts = []
+        for _ in range(reps):
+            flush.zero_()
+            e0, e1 = events(torch)
+            e0.record()
+            p.dslash_eo_(g, y, x)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        t = float(np.median(ts))
+        byt = bytes_per_site(prec, recon) * lat.Vh
+        out.append({"lattice": "x".join(map(str, dims)), "links": f"{prec}-{recon}", "us": round(t * 1e6, 2),
+                    "GBs": round(byt / t / 1e9, 1)})
+        del g
+    return out
+
+
+def time_mscg(torch, p, reps=3):
+    cfg = S.CONFIGS["mscg_32x32x32x32"]
+    dims = cfg["dims"]
+    ut = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
+    b = torch.from_numpy(S.gaussian_field(dims, 2000 + cfg["k"])).cuda()
+    lat = p.Lattice(dims)
+    g64 = p.Gauge(lat, ut, "f64", 18)
+    shifts = cfg["shifts"]()
+    res = {}
+    for name, inner in [("fp32", ("f32", 12)), ("fp16", ("f16", 12)), ("bf16", ("bf16", 12)), ("fp64", None)]:
+        gi = p.Gauge(lat, ut, inner[0], inner[1]) if inner else None
+        ts = []
+        st = None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            _, st = p.mscg(g64, b, shifts, cfg["mass"], tol=cfg["tol"], g_inner=gi, allow_noconv=True)
+            torch.cuda.synchronize()
+            ts.append(time.perf_counter() - t0)
+        res[name] = {"s_per_solve": round(float(np.median(ts)), 5), "iters": st["iters"],
+                     "refine_iters": st["refine_iters"], "reliable_updates": st["reliable_updates"],
+                     "max_true_resid": float(max(st["true_resid"])), "converged": st["status"] == 0}
+        del gi
+    res["mixed_speedup_vs_fp64"] = round(res["fp64"]["s_per_solve"] / min(
+        res[k]["s_per_solve"] for k in ("fp32", "fp16", "bf16") if res[k]["converged"]), 3)
+    return res
+
+
+def time_batched(torch, p, reps=2):
+    cfg = S.CONFIGS["batched_uneven"]
+    shifts = cfg["shifts"]()
+    insts = []
+    for li, dims in enumerate(cfg["dims_list"]):
+        ut = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + 10 * cfg["k"] + li)).cuda()
+        lat = p.Lattice(dims)
+        bs = [torch.from_numpy(S.gaussian_field(dims, 2000 + 10 * cfg["k"] + 4 * li + r)).cuda()
+              for r in range(cfg["nrhs"])]
+        insts.append((p.Gauge(lat, ut, "f64", 18), p.Gauge(lat, ut, "f32", 12), bs))
+    tb = []
+    for _ in range(reps):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        out = p.mscg_batched(insts, shifts, cfg["mass"], tol=cfg["tol"])
+        torch.cuda.synchronize()
+        tb.append(time.perf_counter() - t0)
+    worst = max(max(s["true_resid"]) for _, sts in out for s in sts)
+    ts = 0.0
+    for g64, gi, bs in insts:
+        for b in bs:
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            p.mscg(g64, b, shifts, cfg["mass"], tol=cfg["tol"], g_inner=gi)
+            torch.cuda.synchronize()
+            ts += time.perf_counter() - t0
+    return {"s_per_batch": round(float(np.median(tb)), 5), "sum_of_separate_s": round(ts, 5),
+            "speedup": round(ts / float(np.median(tb)), 3), "systems": 16, "shifts": 16,
+            "max_true_resid": worst}
+
+
+def time_force(torch, p):
+    cfg = S.CONFIGS["force_48x48x48x48"]
+    dims = cfg["dims"]
+    lat = p.Lattice(dims)
+    ut = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
+    g64 = p.Gauge(lat, ut, "f64", 18)
+    del ut
+    res = S.positive_residues(3000 + cfg["k"], 12)
+    g = torch.Generator(device="cuda").manual_seed(2000 + cfg["k"])
+    x = torch.randn((12, lat.Vh, 3), dtype=torch.complex128, device="cuda", generator=g)
+    p.fermion_force(g64, res, x)
+    torch.cuda.synchronize()
+    e0, e1 = events(torch)
+    e0.record()
+    for _ in range(3):
+        f = p.fermion_force(g64, res, x)
+    e1.record()
+    torch.cuda.synchronize()
+    del f
+    return {"lattice": "48^4", "shifts": 12, "ms": round(e0.elapsed_time(e1) / 3, 3),
+            "note": "D_oe on the 12 solutions + per-link gather, FP64"}
+
+
+def run_gpu(args):
+    import torch
+    ws, rank, local = dist_env()
+    if ws > 1:
+        import torch.distributed as dist
+        torch.cuda.set_device(local)
+        dist.init_process_group("nccl")
+    import paper_1801_01473_gb300 as p
+
+    cfg = S.CONFIGS["bandwidth_32x32x32x32"]
+    dims = cfg["dims"]
+    lat = p.Lattice(dims)
+    u = S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])
+    ut = torch.from_numpy(u).cuda()
+    gauges = [p.Gauge(lat, ut, "f32", 12), p.Gauge(lat, ut, "f32", 12)]
+    del ut
+    B = args.batch
+    gen = torch.Generator(device="cuda").manual_seed(2000 + cfg["k"] + rank)
+    src = torch.randn((B, 6 * lat.Vh), dtype=torch.float32, device="cuda", generator=gen)
+    dst = torch.empty_like(src)
+    alg = bytes_per_site("f32", 12) * lat.Vh
+
+    def step():
+        for j in range(B):
+            p.dslash_eo_(gauges[j & 1], dst[j], src[j])
+
+    for _ in range(args.warmup):
+        step()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clk = ClockSampler(local)
+    clk.start()
+    time.sleep(0.3)
+    e0, e1 = events(torch)
+    torch.cuda.synchronize()
+    e0.record()
+    for _ in range(args.steps):
+        step()
+    e1.record()
+    torch.cuda.synchronize()
+    if ws > 1:
+        torch.distributed.barrier()
+    clocks = clk.stop()
+    t = e0.elapsed_time(e1) * 1e-3
+    if ws > 1:
+        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t = float(tt.item())
+    launches = args.steps * B
+    value = ws * alg * launches / t / 1e9
+    per_launch = t / launches
+    peak, peak_kind = measured_peaks()
+    achieved = alg / per_launch / 1e9
+
+    # end to end through the public API with host tensors
+    psi_host = torch.from_numpy(S.gaussian_field(dims, 2000 + cfg["k"])).pin_memory()
+    e2e_reps = max(4, min(64, B))
+    p.dslash_eo(gauges[0], psi_host)
+    torch.cuda.synchronize()
+    t0 = time.perf_counter()
+    for j in range(e2e_reps):
+        out = p.dslash_eo(gauges[j & 1], psi_host)
+    e2e_t = (time.perf_counter() - t0) / e2e_reps
+    e2e = {"value": round(ws * alg / e2e_t / 1e9, 2), "unit": UNIT,
+           "h2d_bytes_per_step": int(psi_host.numel() * 16 * B), "d2h_bytes_per_step": int(out.numel() * 16 * B),
+           "note": f"{e2e_reps} calls of dslash_eo on a pinned host complex128 field (copy, pack, D_eo, unpack, copy back)"}
+    del gauges, src, dst
+
+    line = {"metric": METRIC, "value": round(value, 2), "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": round(1e3 * t / args.steps, 4), "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": workload_config(B, ws),
+            "pct_of_hbm_peak": round(100 * achieved / peak, 2),
+            "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
+                         "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
+                         "traffic": profile_traffic("deo_32x32x32x32_f32r12.md"),
+                         "kernel": "k_dslash<LinkF32R12,1,0>"},
+            "gpu_launches": launches, "clocks": clocks, "e2e": e2e}
+    if rank == 0 and not args.no_extras:
+        line["sweep"] = time_deo_sweep(torch, p, (16, 16, 16, 16)) + time_deo_sweep(torch, p, (32, 32, 32, 32))
+        line["mscg"] = time_mscg(torch, p)
+        line["batched"] = time_batched(torch, p)
+        line["force"] = time_force(torch, p)
+        line["cpu_baseline"] = cpu_baseline()
+    if ws > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=20)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--batch", type=int, default=256)
+    ap.add_argument("--impl", default="stg", choices=["stg", "reference"])
+    ap.add_argument("--no-extras", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    return run_gpu(args)
+
+
+if __name__ == "__main__":
+    sys.exit(main())

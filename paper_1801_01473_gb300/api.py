@@ -30,7 +30,9 @@ def _ptr(t: torch.Tensor) -> ctypes.c_void_p:
     return ctypes.c_void_p(t.data_ptr())
 
 
-def _dev(t: torch.Tensor, dtype=torch.complex128) -> torch.Tensor:
+def _dev(t, dtype=torch.complex128) -> torch.Tensor:
+    if not isinstance(t, torch.Tensor):
+        t = torch.as_tensor(t)
     if not t.is_cuda:
         t = t.to("cuda", non_blocking=True)
     if t.dtype != dtype:

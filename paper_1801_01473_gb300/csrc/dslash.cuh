@@ -11,7 +11,8 @@
 //     MODE 0   out_j = acc_j / 2
 //     MODE 1   out_j = c_j p_j - acc_j / 2             partial_j[block] = Re<p_j, out_j>
 //     MODE 2   out_j = b_j - (c_j p_j - acc_j / 2)     partial_j[block] = |out_j|^2
-// Partials are FP64, one per block and right-hand side (deterministic fixed-order tree).
+// Partials are FP64, one per 64 output sites and right-hand side (fixed-order trees), so the
+// reduced values do not depend on the block size the autotuner picks.
 #pragma once
 
 #include "stg_internal.cuh"
@@ -20,7 +21,11 @@ namespace stg {
 
 constexpr int kMaxRhs = 8;
 constexpr int kMaxGroups = 4;
-constexpr int kDslashBlock = 128;
+constexpr int kDslashBlock = 128;   // default block; the autotuner may pick 64, 128 or 256
+constexpr int kPartialSites = 64;   // one FP64 partial per 64 output sites, whatever the block size
+
+// Number of FP64 partial sums an epilogue launch writes for a lattice of Vh sites per parity.
+__host__ __device__ inline int dslash_partials(int Vh) { return (Vh + kPartialSites - 1) / kPartialSites; }
 
 // A set of right-hand sides on one lattice and gauge.  blockIdx.y selects the group.
 struct DGroup {
@@ -42,13 +47,13 @@ struct DArgs {
     int out_par;  // parity of the output sites: 0 -> D_eo, 1 -> D_oe
 };
 
-template <typename LinkT, int NRHS, int MODE>
-__global__ void __launch_bounds__(kDslashBlock) k_dslash(const __grid_constant__ DArgs a)
+template <typename LinkT, int NRHS, int MODE, int BS>
+__global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
 {
     using R = typename LinkT::R;
     const DGroup &G = a.grp[blockIdx.y];
     const int Vh = G.g.Vh;
-    if ((int)(blockIdx.x * kDslashBlock) >= Vh) return;  // block-uniform
+    if ((int)(blockIdx.x * BS) >= Vh) return;  // block-uniform
 
     bool act[NRHS];
     bool any = false;
@@ -59,7 +64,7 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const __grid_constant__
     }
     if (!any) return;  // block-uniform
 
-    const int h = blockIdx.x * kDslashBlock + threadIdx.x;
+    const int h = blockIdx.x * BS + threadIdx.x;
     const bool live = h < Vh;
     const int op = a.out_par;
 
@@ -144,37 +149,64 @@ __global__ void __launch_bounds__(kDslashBlock) k_dslash(const __grid_constant__
             Field<R>::store(G.out[j], Vh, h, o);
         }
         if (MODE != 0 && G.partial[j] != nullptr) {
-            double t = block_sum(part, sh);
-            if (threadIdx.x == 0) G.partial[j][blockIdx.x] = t;
+            // two warps per 64-site chunk: warp sums, then pairs of warps
+            part = warp_sum(part);
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = part;
+            __syncthreads();
+            constexpr int kChunks = BS / kPartialSites;
+            const int c = blockIdx.x * kChunks + threadIdx.x;
+            if (threadIdx.x < kChunks && c < dslash_partials(Vh))
+                G.partial[j][c] = sh[2 * threadIdx.x] + sh[2 * threadIdx.x + 1];
         }
     }
 }
 
-// Host-side launcher: picks the NRHS instantiation (>= the largest group's nrhs).
-template <typename LinkT>
-cudaError_t launch_dslash_t(const DArgs &a, int mode, cudaStream_t st)
+// Host-side launcher: picks the NRHS instantiation (>= the largest group's nrhs) and the
+// block size `bs` (64, 128 or 256; anything else falls back to 128).
+template <typename LinkT, int NRHS, int BS>
+cudaError_t launch_dslash_nb(const DArgs &a, int mode, int maxv, cudaStream_t st)
 {
-    int maxv = 0, maxr = 0;
+    dim3 grid((maxv + BS - 1) / BS, a.ngroups);
+    if (mode == 0) k_dslash<LinkT, NRHS, 0, BS><<<grid, BS, 0, st>>>(a);
+    else if (mode == 1) k_dslash<LinkT, NRHS, 1, BS><<<grid, BS, 0, st>>>(a);
+    else k_dslash<LinkT, NRHS, 2, BS><<<grid, BS, 0, st>>>(a);
+    return cudaGetLastError();
+}
+
+template <typename LinkT, int NRHS>
+cudaError_t launch_dslash_n(const DArgs &a, int mode, int maxv, int bs, cudaStream_t st)
+{
+    if (bs == 64) return launch_dslash_nb<LinkT, NRHS, 64>(a, mode, maxv, st);
+    if (bs == 256) return launch_dslash_nb<LinkT, NRHS, 256>(a, mode, maxv, st);
+    return launch_dslash_nb<LinkT, NRHS, 128>(a, mode, maxv, st);
+}
+
+inline void dslash_extent(const DArgs &a, int &maxv, int &maxr)
+{
+    maxv = 0;
+    maxr = 0;
     for (int k = 0; k < a.ngroups; ++k) {
         if (a.grp[k].g.Vh > maxv) maxv = a.grp[k].g.Vh;
         if (a.grp[k].nrhs > maxr) maxr = a.grp[k].nrhs;
     }
+}
+
+// NRHS template the launcher uses for a largest group of `maxr` right-hand sides.
+inline int dslash_nrhs_template(int maxr) { return maxr <= 1 ? 1 : maxr <= 2 ? 2 : maxr <= 4 ? 4 : 8; }
+
+template <typename LinkT>
+cudaError_t launch_dslash_t(const DArgs &a, int mode, int bs, cudaStream_t st)
+{
+    int maxv, maxr;
+    dslash_extent(a, maxv, maxr);
     if (a.ngroups <= 0 || maxv <= 0 || maxr <= 0) return cudaSuccess;
-    dim3 grid((maxv + kDslashBlock - 1) / kDslashBlock, a.ngroups);
-    dim3 block(kDslashBlock);
-#define STG_DSL_CASE(N)                                                                         \
-    if (maxr <= N) {                                                                            \
-        if (mode == 0) k_dslash<LinkT, N, 0><<<grid, block, 0, st>>>(a);                         \
-        else if (mode == 1) k_dslash<LinkT, N, 1><<<grid, block, 0, st>>>(a);                    \
-        else k_dslash<LinkT, N, 2><<<grid, block, 0, st>>>(a);                                   \
-        return cudaGetLastError();                                                              \
+    switch (dslash_nrhs_template(maxr)) {
+    case 1: return launch_dslash_n<LinkT, 1>(a, mode, maxv, bs, st);
+    case 2: return launch_dslash_n<LinkT, 2>(a, mode, maxv, bs, st);
+    case 4: return launch_dslash_n<LinkT, 4>(a, mode, maxv, bs, st);
+    default: return maxr <= kMaxRhs ? launch_dslash_n<LinkT, 8>(a, mode, maxv, bs, st) : cudaErrorInvalidValue;
     }
-    STG_DSL_CASE(1)
-    STG_DSL_CASE(2)
-    STG_DSL_CASE(4)
-    STG_DSL_CASE(8)
-#undef STG_DSL_CASE
-    return cudaErrorInvalidValue;
 }
 
 }  // namespace stg

@@ -2,6 +2,6 @@
 #include "stg_common.h"
 
 namespace stg {
-cudaError_t launch_dslash_f64r18(const DArgs &a, int mode, cudaStream_t st) { return launch_dslash_t<LinkF64R18>(a, mode, st); }
-cudaError_t launch_dslash_f64r12(const DArgs &a, int mode, cudaStream_t st) { return launch_dslash_t<LinkF64R12>(a, mode, st); }
+cudaError_t launch_dslash_f64r18(const DArgs &a, int mode, int bs, cudaStream_t st) { return launch_dslash_t<LinkF64R18>(a, mode, bs, st); }
+cudaError_t launch_dslash_f64r12(const DArgs &a, int mode, int bs, cudaStream_t st) { return launch_dslash_t<LinkF64R12>(a, mode, bs, st); }
 }  // namespace stg

@@ -2,6 +2,6 @@
 #include "stg_common.h"
 
 namespace stg {
-cudaError_t launch_dslash_bf16r12(const DArgs &a, int mode, cudaStream_t st) { return launch_dslash_t<Link16R12<__nv_bfloat16>>(a, mode, st); }
-cudaError_t launch_dslash_f16r12(const DArgs &a, int mode, cudaStream_t st) { return launch_dslash_t<Link16R12<__half>>(a, mode, st); }
+cudaError_t launch_dslash_bf16r12(const DArgs &a, int mode, int bs, cudaStream_t st) { return launch_dslash_t<Link16R12<__nv_bfloat16>>(a, mode, bs, st); }
+cudaError_t launch_dslash_f16r12(const DArgs &a, int mode, int bs, cudaStream_t st) { return launch_dslash_t<Link16R12<__half>>(a, mode, bs, st); }
 }  // namespace stg

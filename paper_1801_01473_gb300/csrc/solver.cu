@@ -37,11 +37,11 @@ namespace stg {
 constexpr int kVecBlock = 256;
 
 struct SysScal {
-    double rr, alpha, alpha_old, beta_old, bnorm2, tol2, tol2_true, rr_last, delta2, coef;
+    double rr, alpha, alpha_old, beta_old, bnorm2, tol2, tol2_true, rr_last, delta2, coef, rr_best;
     double zeta[kMaxShifts], zeta_old[kMaxShifts], zeta_new[kMaxShifts], s[kMaxShifts];
     double cx[kMaxShifts], cr[kMaxShifts], cp[kMaxShifts];
     int upd_x[kMaxShifts], upd_p[kMaxShifts], active[kMaxShifts], shift_iters[kMaxShifts];
-    int nshift, i0, running, iters, max_iter, nactive, phase2, reliable;
+    int nshift, i0, running, iters, max_iter, nactive, phase2, stalls;
 };
 
 struct SysVecs {
@@ -338,7 +338,14 @@ __global__ void k_rel_finish(SysScal *sc, const SysVecs *sv, const int *noupd, i
         true_rr[s] = rr;
         rel_count[s] += 1;
         need_rel[s] = 0;
-        if (rr <= S.tol2_true || S.iters >= S.max_iter) {
+        // stagnation guard: give up after 8 consecutive updates without halving the best residual
+        if (rel_count[s] == 1 || rr < 0.25 * S.rr_best) {
+            S.rr_best = rr;
+            S.stalls = 0;
+        } else {
+            S.stalls += 1;
+        }
+        if (rr <= S.tol2_true || S.iters >= S.max_iter || S.stalls >= 8) {
             finished[s] = 1;
             done[s] = 1;
         } else {
@@ -458,7 +465,8 @@ struct DevBuf {
 };
 
 struct InstInfo {
-    const stg_gauge *gi;   // gauge of the inner iterations
+    const stg_gauge *gi;   // gauge of the multi-shift iterations
+    const stg_gauge *gr;   // gauge of the refinement iterations
     const stg_gauge *g64;  // FP64 gauge
     int nrhs;
     int sys0;              // first phase-1 system of this instance
@@ -469,11 +477,13 @@ struct DPlan {
     std::vector<DArgs> oe, eo;  // launched with modes 0 and (1 or 2)
 };
 
-static void add_group(std::vector<DArgs> &lst, const DGroup &G)
+// Appends a group to the launch list; out_par = 1 for D_oe lists, 0 for D_eo lists.
+static void add_group(std::vector<DArgs> &lst, const DGroup &G, int out_par)
 {
     if (lst.empty() || lst.back().ngroups == kMaxGroups) {
         DArgs a;
         memset(&a, 0, sizeof(a));
+        a.out_par = out_par;
         lst.push_back(a);
     }
     DArgs &a = lst.back();
@@ -498,12 +508,22 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     for (int k = 0; k < ninst; ++k) {
         ii[k].g64 = inst[k].g_f64;
         ii[k].gi = mixed ? inst[k].g_inner : inst[k].g_f64;
+        ii[k].gr = ii[k].gi;
         ii[k].nrhs = inst[k].nrhs;
         ii[k].sys0 = nsys;
         nsys += inst[k].nrhs;
     }
     const int npair = nsys * ns;
     const int kind_i = ii[0].gi->kind, kind_64 = ii[0].g64->kind;
+    // 16-bit links are too coarse for the refinement to converge on ill-conditioned shifts
+    // (their rounding error times the condition number exceeds one): refine on FP32 links.
+    const bool refine_f32 = kind_i == kBF16R12 || kind_i == kF16R12;
+    if (refine_f32)
+        for (int k = 0; k < ninst; ++k) {
+            stg_status s = f32_companion(ii[k].g64, user_st, &ii[k].gr);
+            if (s != STG_OK) return s;
+        }
+    const int kind_r = ii[0].gr->kind;
     const double inner_tol = mixed ? (prm->inner_tol > 0 ? prm->inner_tol
                                                           : (kind_i == kBF16R12 || kind_i == kF16R12 ? 2e-3 : 1e-6))
                                    : prm->tol;
@@ -539,7 +559,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     int nblkv_max = 0;
     for (int k = 0; k < ninst; ++k) {
         const int Vh = ii[k].g64->g.Vh;
-        const int nbd = (Vh + kDslashBlock - 1) / kDslashBlock, nbv = (Vh + kVecBlock - 1) / kVecBlock;
+        const int nbd = dslash_partials(Vh), nbv = (Vh + kVecBlock - 1) / kVecBlock;
         nblkv_max = std::max(nblkv_max, nbv);
         const size_t fb = (size_t)Vh * vb, f64b = (size_t)Vh * 48;
         for (int r = 0; r < ii[k].nrhs; ++r) {
@@ -647,8 +667,8 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
                 Geo.partial[j] = v1[s].part_d;
                 Geo.skip[j] = done1 + s;
             }
-            add_group(p1.oe, Goe);
-            add_group(p1.eo, Geo);
+            add_group(p1.oe, Goe, 1);
+            add_group(p1.eo, Geo, 0);
         }
     }
     // phase 2: the (rhs, shift) pairs of one instance share link loads
@@ -658,8 +678,8 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         for (int q0 = 0; q0 < cnt; q0 += kMaxRhs) {
             DGroup Goe, Geo, Hoe, Heo;
             memset(&Goe, 0, sizeof(Goe));
-            Goe.g = ii[k].gi->g;
-            Goe.links = ii[k].gi->links;
+            Goe.g = ii[k].gr->g;
+            Goe.links = ii[k].gr->links;
             Goe.nrhs = std::min(kMaxRhs, cnt - q0);
             Geo = Goe;
             Hoe = Goe;
@@ -689,22 +709,22 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
                 Heo.partial[j] = W.part_d;
                 Heo.skip[j] = noupd + pidx;
             }
-            add_group(p2.oe, Goe);
-            add_group(p2.eo, Geo);
-            add_group(p64.oe, Hoe);
-            add_group(p64.eo, Heo);
+            add_group(p2.oe, Goe, 1);
+            add_group(p2.eo, Geo, 0);
+            add_group(p64.oe, Hoe, 1);
+            add_group(p64.eo, Heo, 0);
         }
     }
 
     const dim3 vgrid1(nblkv_max, nsys), vgrid2(nblkv_max, npair);
 
-    auto iterate = [&](const DPlan &pl, SysScal *dS, SysVecs *dV, int *dn, int *nr, int n, dim3 vg, double *log,
-                       int log_rows) -> cudaError_t {
+    auto iterate = [&](int kind, const DPlan &pl, SysScal *dS, SysVecs *dV, int *dn, int *nr, int n, dim3 vg,
+                       double *log, int log_rows) -> cudaError_t {
         cudaError_t e;
         for (const DArgs &a : pl.oe)
-            if ((e = launch_dslash(kind_i, a, 0, ws)) != cudaSuccess) return e;
+            if ((e = launch_dslash(kind, a, 0, ws)) != cudaSuccess) return e;
         for (const DArgs &a : pl.eo)
-            if ((e = launch_dslash(kind_i, a, 1, ws)) != cudaSuccess) return e;
+            if ((e = launch_dslash(kind, a, 1, ws)) != cudaSuccess) return e;
         k_alpha<<<n, 32, 0, ws>>>(dS, dV, dn);
         k_update_r<R><<<vg, kVecBlock, 0, ws>>>(dS, dV);
         k_beta<<<n, 32, 0, ws>>>(dS, dV, dn, nr, log, log_rows);
@@ -727,15 +747,19 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     constexpr int kChunk = 8;
     // Runs chunks until every system's done flag is set (or, with stop_on_need, until some
     // system asks for a reliable update).
-    auto run_until_done = [&](GraphCache &gc, const DPlan &pl, SysScal *dS, SysVecs *dV, int *dn, int *nr, int n,
+    auto run_until_done = [&](GraphCache &gc, int kind, const DPlan &pl, SysScal *dS, SysVecs *dV, int *dn, int *nr, int n,
                               dim3 vg, double *log, int log_rows, bool stop_on_need, std::vector<int> &h_done,
                               std::vector<int> &h_need) -> stg_status {
         if (gc.state == 0) {
+            // the D launches of one iteration, outside capture, settle the autotuned block sizes;
+            // their outputs (t, q, partials) are recomputed by the first captured iteration
+            for (const DArgs &a : pl.oe) STG_CUDA_TRY(launch_dslash(kind, a, 0, ws));
+            for (const DArgs &a : pl.eo) STG_CUDA_TRY(launch_dslash(kind, a, 1, ws));
             gc.state = 2;
             if (cudaStreamBeginCapture(ws, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
                 cudaError_t e = cudaSuccess;
                 for (int k = 0; k < kChunk && e == cudaSuccess; ++k)
-                    e = iterate(pl, dS, dV, dn, nr, n, vg, log, log_rows);
+                    e = iterate(kind, pl, dS, dV, dn, nr, n, vg, log, log_rows);
                 cudaError_t e2 = cudaStreamEndCapture(ws, &gc.graph);
                 if (e == cudaSuccess && e2 == cudaSuccess && cudaGraphInstantiate(&gc.exec, gc.graph, 0) == cudaSuccess)
                     gc.state = 1;
@@ -749,7 +773,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         for (long long c = 0; c <= cap; ++c) {
             cudaError_t e = gc.state == 1 ? cudaGraphLaunch(gc.exec, ws) : cudaSuccess;
             for (int k = 0; gc.state != 1 && k < kChunk && e == cudaSuccess; ++k)
-                e = iterate(pl, dS, dV, dn, nr, n, vg, log, log_rows);
+                e = iterate(kind, pl, dS, dV, dn, nr, n, vg, log, log_rows);
             if (e == cudaSuccess) e = cudaMemcpyAsync(h_done.data(), dn, sizeof(int) * n, cudaMemcpyDeviceToHost, ws);
             if (e == cudaSuccess && stop_on_need)
                 e = cudaMemcpyAsync(h_need.data(), nr, sizeof(int) * n, cudaMemcpyDeviceToHost, ws);
@@ -771,7 +795,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     k_p1_init_scal<<<nsys, 32, 0, ws>>>(d_s1, d_v1, done1, inner_tol);
     STG_CUDA_TRY(cudaGetLastError());
     std::vector<int> h_done1(nsys), h_need1(nsys);
-    stg_status st = run_until_done(gc1, p1, d_s1, d_v1, done1, need1, nsys, vgrid1, d_log, prm->log_rows, false,
+    stg_status st = run_until_done(gc1, kind_i, p1, d_s1, d_v1, done1, need1, nsys, vgrid1, d_log, prm->log_rows, false,
                                    h_done1, h_need1);
     if (st != STG_OK) return st;
 
@@ -822,7 +846,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         bool all = true;
         for (int q = 0; q < npair; ++q) all &= h_fin[q] != 0;
         if (all) break;
-        st = run_until_done(gc2, p2, d_s2, d_v2, done2, need2, npair, vgrid2, nullptr, 0, true, h_done2, h_need2);
+        st = run_until_done(gc2, kind_r, p2, d_s2, d_v2, done2, need2, npair, vgrid2, nullptr, 0, true, h_done2, h_need2);
         if (st != STG_OK) return st;
         bool any = false;
         for (int q = 0; q < npair; ++q) {

@@ -18,17 +18,24 @@ enum LinkKind { kF64R18 = 0, kF64R12 = 1, kF32R18 = 2, kF32R12 = 3, kBF16R12 = 4
 int link_bytes(int kind);
 inline bool kind_is_f64(int kind) { return kind == kF64R18 || kind == kF64R12; }
 
-// Launchers, one per storage kind, implemented in dslash_f64.cu / dslash_f32.cu / dslash_h16.cu.
-cudaError_t launch_dslash_f64r18(const DArgs &a, int mode, cudaStream_t st);
-cudaError_t launch_dslash_f64r12(const DArgs &a, int mode, cudaStream_t st);
-cudaError_t launch_dslash_f32r18(const DArgs &a, int mode, cudaStream_t st);
-cudaError_t launch_dslash_f32r12(const DArgs &a, int mode, cudaStream_t st);
-cudaError_t launch_dslash_bf16r12(const DArgs &a, int mode, cudaStream_t st);
-cudaError_t launch_dslash_f16r12(const DArgs &a, int mode, cudaStream_t st);
+// Launchers, one per storage kind, implemented in dslash_f64.cu / dslash_f32.cu / dslash_h16.cu;
+// `bs` is the thread-block size (64, 128 or 256).
+cudaError_t launch_dslash_f64r18(const DArgs &a, int mode, int bs, cudaStream_t st);
+cudaError_t launch_dslash_f64r12(const DArgs &a, int mode, int bs, cudaStream_t st);
+cudaError_t launch_dslash_f32r18(const DArgs &a, int mode, int bs, cudaStream_t st);
+cudaError_t launch_dslash_f32r12(const DArgs &a, int mode, int bs, cudaStream_t st);
+cudaError_t launch_dslash_bf16r12(const DArgs &a, int mode, int bs, cudaStream_t st);
+cudaError_t launch_dslash_f16r12(const DArgs &a, int mode, int bs, cudaStream_t st);
+// Launches the D kernel for storage `kind` with the autotuned block size (stg_core.cu).
 cudaError_t launch_dslash(int kind, const DArgs &a, int mode, cudaStream_t st);
+cudaError_t launch_dslash_bs(int kind, const DArgs &a, int mode, int bs, cudaStream_t st);
 
 // Pack canonical complex128 links [4][V][3][3] into the internal layout of `kind`.
 cudaError_t launch_pack_links(int kind, const Geom &g, const void *canon, void *links, cudaStream_t st);
+
+// F32 12-real copy of an F64 gauge (created on first use, owned by the F64 gauge): the operator
+// of the refinement iterations when the multi-shift phase runs on 16-bit links.
+stg_status f32_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge **out);
 
 // Error reporting (thread-local message read by stg_last_error).
 stg_status set_error(stg_status s, const std::string &msg);
@@ -51,6 +58,7 @@ struct stg_gauge {
     size_t bytes;
     double *scratch;       // per-block partial sums of stg_normal_op's reduction
     size_t scratch_count;  // doubles in scratch
+    mutable stg_gauge *f32_copy;  // lazily created F32 12-real companion (F64 gauges only)
 };
 
 #define STG_CUDA_TRY(call)                                       \

@@ -1,9 +1,13 @@
 // stg_core.cu -- C ABI: lattice and gauge handles, field packing, D_eo / D_oe and the
 // shifted normal operator (Sec. 2, Eq. shift_eo; link compression and phases, Sec. 4.1).
 #include <cstdio>
+#include <cstdlib>
 #include <cstring>
+#include <map>
+#include <mutex>
 #include <new>
 #include <string>
+#include <tuple>
 
 #include "stg_common.h"
 
@@ -36,17 +40,84 @@ int link_bytes(int kind)
     return 0;
 }
 
-cudaError_t launch_dslash(int kind, const DArgs &a, int mode, cudaStream_t st)
+cudaError_t launch_dslash_bs(int kind, const DArgs &a, int mode, int bs, cudaStream_t st)
 {
     switch (kind) {
-    case kF64R18: return launch_dslash_f64r18(a, mode, st);
-    case kF64R12: return launch_dslash_f64r12(a, mode, st);
-    case kF32R18: return launch_dslash_f32r18(a, mode, st);
-    case kF32R12: return launch_dslash_f32r12(a, mode, st);
-    case kBF16R12: return launch_dslash_bf16r12(a, mode, st);
-    case kF16R12: return launch_dslash_f16r12(a, mode, st);
+    case kF64R18: return launch_dslash_f64r18(a, mode, bs, st);
+    case kF64R12: return launch_dslash_f64r12(a, mode, bs, st);
+    case kF32R18: return launch_dslash_f32r18(a, mode, bs, st);
+    case kF32R12: return launch_dslash_f32r12(a, mode, bs, st);
+    case kBF16R12: return launch_dslash_bf16r12(a, mode, bs, st);
+    case kF16R12: return launch_dslash_f16r12(a, mode, bs, st);
     }
     return cudaErrorInvalidValue;
+}
+
+// Block-size autotuner of the D kernel.  Keyed by (device, storage kind, epilogue, rhs
+// template, largest Vh of the launch): the first launch of a key outside stream capture runs
+// the kernel with 64-, 128- and 256-thread blocks (each launch recomputes the same outputs, so
+// the repetition is harmless), times them with CUDA events on the launch stream and keeps the
+// fastest.  Launches during capture use the tuned size when known, else 128.  STG_AUTOTUNE=0
+// disables tuning.
+namespace {
+std::mutex g_tune_mu;
+std::map<std::tuple<int, int, int, int, int>, int> g_tuned;
+}  // namespace
+
+cudaError_t launch_dslash(int kind, const DArgs &a, int mode, cudaStream_t st)
+{
+    int maxv, maxr;
+    dslash_extent(a, maxv, maxr);
+    if (a.ngroups <= 0 || maxv <= 0 || maxr <= 0) return cudaSuccess;
+    const int nt = dslash_nrhs_template(maxr);
+    int dev = 0;
+    cudaGetDevice(&dev);
+    const auto key = std::make_tuple(dev, kind, mode, nt, maxv);
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        auto it = g_tuned.find(key);
+        if (it != g_tuned.end()) return launch_dslash_bs(kind, a, mode, it->second, st);
+    }
+    cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
+    if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
+        return launch_dslash_bs(kind, a, mode, kDslashBlock, st);
+    const char *env = getenv("STG_AUTOTUNE");
+    int best = kDslashBlock;
+    if (!(env && env[0] == '0')) {
+        cudaEvent_t e0, e1;
+        if (cudaEventCreate(&e0) != cudaSuccess) return cudaGetLastError();
+        if (cudaEventCreate(&e1) != cudaSuccess) {
+            cudaEventDestroy(e0);
+            return cudaGetLastError();
+        }
+        float best_t = 1e30f;
+        const int cands[3] = {64, 128, 256};
+        for (int bs : cands) {
+            cudaError_t e = launch_dslash_bs(kind, a, mode, bs, st);  // warm-up
+            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_dslash_bs(kind, a, mode, bs, st);
+            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+            float ms = 0.f;
+            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+            if (e != cudaSuccess) {
+                cudaEventDestroy(e0);
+                cudaEventDestroy(e1);
+                return e;
+            }
+            if (ms < best_t) {
+                best_t = ms;
+                best = bs;
+            }
+        }
+        cudaEventDestroy(e0);
+        cudaEventDestroy(e1);
+    }
+    {
+        std::lock_guard<std::mutex> lk(g_tune_mu);
+        g_tuned[key] = best;
+    }
+    return launch_dslash_bs(kind, a, mode, best, st);
 }
 
 // ------------------------------------------------------------------ packing kernels
@@ -90,6 +161,59 @@ cudaError_t launch_pack_links(int kind, const Geom &g, const void *canon, void *
     case kF16R12: return pack_links_t<Link16R12<__half>>(g, canon, links, st);
     }
     return cudaErrorInvalidValue;
+}
+
+// internal F64 links -> internal F32 12-real links (one thread per link)
+template <typename SrcT>
+__global__ void k_links_to_f32r12(Geom g, const void *__restrict__ src, void *__restrict__ dst)
+{
+    const int Vh = g.Vh;
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= 8LL * Vh) return;
+    const int blk = (int)(tid / Vh), h = (int)(tid - (long long)blk * Vh);
+    cx<double> U[3][3];
+    SrcT::load(static_cast<const char *>(src) + (size_t)blk * Vh * SrcT::kBytes, Vh, h, U);
+    double2 m[9];
+    for (int k = 0; k < 9; ++k) m[k] = make_double2(U[k / 3][k % 3].re, U[k / 3][k % 3].im);
+    LinkF32R12::pack(static_cast<char *>(dst) + (size_t)blk * Vh * LinkF32R12::kBytes, Vh, h, m);
+}
+
+static std::mutex g_companion_mu;
+
+stg_status f32_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge **out)
+{
+    std::lock_guard<std::mutex> lk(g_companion_mu);
+    if (!g64->f32_copy) {
+        stg_gauge *g = new (std::nothrow) stg_gauge;
+        if (!g) return set_error(STG_ERR_OOM, "f32_companion: host allocation");
+        *g = *g64;
+        g->prec = STG_F32;
+        g->recon = STG_RECON12;
+        g->kind = kF32R12;
+        g->bytes = (size_t)4 * g64->lat->V * LinkF32R12::kBytes;
+        g->scratch = nullptr;
+        g->links = nullptr;
+        g->f32_copy = nullptr;
+        cudaError_t e = cudaMalloc(&g->links, g->bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&g->scratch, g->scratch_count * sizeof(double));
+        if (e == cudaSuccess) {
+            long long n = 8LL * g->g.Vh;
+            if (g64->kind == kF64R18)
+                k_links_to_f32r12<LinkF64R18><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->g, g64->links, g->links);
+            else
+                k_links_to_f32r12<LinkF64R12><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->g, g64->links, g->links);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            cudaFree(g->links);
+            cudaFree(g->scratch);
+            delete g;
+            return cuda_error(e, "f32_companion");
+        }
+        g64->f32_copy = g;
+    }
+    *out = g64->f32_copy;
+    return STG_OK;
 }
 
 // canonical [Vh][3] complex128 <-> internal field
@@ -212,7 +336,8 @@ stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, 
     g->bytes = (size_t)4 * lat->V * link_bytes(kind);
     g->links = nullptr;
     g->scratch = nullptr;
-    g->scratch_count = (size_t)kMaxRhs * ((lat->g.Vh + kDslashBlock - 1) / kDslashBlock);
+    g->f32_copy = nullptr;
+    g->scratch_count = (size_t)dslash_partials(lat->g.Vh);
     cudaError_t e = cudaMalloc(&g->links, g->bytes);
     if (e == cudaSuccess) e = cudaMalloc(&g->scratch, g->scratch_count * sizeof(double));
     if (e == cudaSuccess) e = launch_pack_links(kind, lat->g, links_c128_dev, g->links, (cudaStream_t)stream);
@@ -230,6 +355,7 @@ stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, 
 void stg_gauge_destroy(stg_gauge *g)
 {
     if (!g) return;
+    if (g->f32_copy) stg_gauge_destroy(g->f32_copy);
     cudaFree(g->links);
     cudaFree(g->scratch);
     delete g;
@@ -359,8 +485,7 @@ stg_status stg_normal_op(const stg_gauge *g, double mass, double shift, void *ou
     G.partial[0] = pq_dev ? g->scratch : nullptr;
     STG_CUDA_TRY(launch_dslash(g->kind, a, 1, st));
     if (pq_dev) {
-        int nb = (g->g.Vh + kDslashBlock - 1) / kDslashBlock;
-        k_sum_partials<<<1, 256, 0, st>>>(g->scratch, nb, pq_dev);
+        k_sum_partials<<<1, 256, 0, st>>>(g->scratch, dslash_partials(g->g.Vh), pq_dev);
         STG_CUDA_TRY(cudaGetLastError());
     }
     return STG_OK;

@@ -126,6 +126,24 @@ stg_status stg_dslash_multi(const stg_gauge *g, int32_t out_parity, int32_t nrhs
 stg_status stg_normal_op(const stg_gauge *g, double mass, double shift, void *out_even_dev, const void *in_even_dev,
                          void *tmp_odd_dev, double *pq_dev, void *stream);
 
+/* Same operation and results as stg_normal_op with pq_dev, for callers that cannot allocate
+ * device memory when they call it: a host framework that owns all device memory through its own
+ * pool, or a time-stepping loop that must not call cudaMalloc/cudaFree (they can synchronize the
+ * device, or fail once memory is partitioned).  It needs no tmp_odd: the odd temporary and the
+ * partial sums live in one 32 MiB file-scope __device__ array that every GPU loading the library
+ * holds until exit.  The paper has no counterpart of this entry point.
+ *   Limit: Vh <= 697232 sites per parity for F64 gauges, <= 1390848 for F32/BF16/F16 gauges
+ *          (a 32^4 lattice fits at FP64); larger lattices return STG_ERR_ARG before any launch.
+ *   Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress
+ *          with that device current) and caches it; make that first call before any stream
+ *          capture.  Nothing is allocated, here or later.
+ *   Sharing: every call on a device uses the same array, which keeps the last call's contents
+ *          (each call overwrites all it reads, so nothing must start at zero); calls that overlap
+ *          on the GPU (different streams, no ordering) race on it.
+ * pq_dev may be NULL (no reduction). */
+stg_status stg_normal_op_noalloc(const stg_gauge *g, double mass, double shift, void *out_even_dev,
+                                 const void *in_even_dev, double *pq_dev, void *stream);
+
 /* ---- multi-shift CG (Sec. 2, Eq. shift_eo) ------------------------------------------------- */
 
 typedef struct {

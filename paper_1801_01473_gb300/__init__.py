@@ -8,10 +8,10 @@ device memory and streams.  Build the library with
 ``python -m paper_1801_01473_gb300.build``.
 """
 from .api import (Gauge, Lattice, dslash_eo, dslash_eo_, dslash_multi_, dslash_oe, dslash_oe_, fermion_force,
-                  mscg, mscg_batched, normal_op, normal_op_, pack, unpack)
+                  mscg, mscg_batched, normal_op, normal_op_, normal_op_noalloc_, pack, unpack)
 from .autograd import PseudofermionAction, pseudofermion_action
 from .lib import StgError, lib
 
 __all__ = ["Lattice", "Gauge", "pack", "unpack", "dslash_eo", "dslash_oe", "dslash_eo_", "dslash_oe_",
-           "dslash_multi_", "normal_op", "normal_op_", "mscg", "mscg_batched", "fermion_force",
+           "dslash_multi_", "normal_op", "normal_op_", "normal_op_noalloc_", "mscg", "mscg_batched", "fermion_force",
            "PseudofermionAction", "pseudofermion_action", "StgError", "lib"]

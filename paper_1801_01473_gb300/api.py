@@ -151,6 +151,15 @@ def normal_op_(gauge: Gauge, mass: float, shift: float, out: torch.Tensor, inp: 
     return out
 
 
+def normal_op_noalloc_(gauge: Gauge, mass: float, shift: float, out: torch.Tensor, inp: torch.Tensor,
+                       pq: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+    """stg_normal_op_noalloc: like normal_op_ but without a caller temporary; the library keeps
+    its scratch in a fixed 32 MiB device array and allocates nothing (see include/stg.h)."""
+    check(lib().stg_normal_op_noalloc(gauge.handle, float(mass), float(shift), _ptr(out), _ptr(inp),
+                                      _ptr(pq) if pq is not None else None, _stream(stream)), "stg_normal_op_noalloc")
+    return out
+
+
 # ------------------------------------------------------------------ operator (canonical layout)
 
 def _canon_apply(gauge: Gauge, canon: torch.Tensor, fn) -> torch.Tensor:

@@ -24,7 +24,7 @@ EXPORTS = [
     "stg_lattice_create", "stg_lattice_destroy", "stg_lattice_sites",
     "stg_gauge_create", "stg_gauge_destroy", "stg_gauge_bytes",
     "stg_field_bytes", "stg_field_pack", "stg_field_unpack",
-    "stg_dslash_eo", "stg_dslash_oe", "stg_dslash_multi", "stg_normal_op",
+    "stg_dslash_eo", "stg_dslash_oe", "stg_dslash_multi", "stg_normal_op", "stg_normal_op_noalloc",
     "stg_mscg_solve", "stg_mscg_solve_batched", "stg_fermion_force",
 ]
 
@@ -86,6 +86,7 @@ def lib() -> ctypes.CDLL:
     L.stg_dslash_oe.argtypes = [P, P, P, P]
     L.stg_dslash_multi.argtypes = [P, I32, I32, P, P, SZ, P]
     L.stg_normal_op.argtypes = [P, D, D, P, P, P, P, P]
+    L.stg_normal_op_noalloc.argtypes = [P, D, D, P, P, P, P]
     L.stg_mscg_solve.argtypes = [P, P, ctypes.POINTER(MscgParams), P, PP, ctypes.POINTER(MscgStats), P]
     L.stg_mscg_solve_batched.argtypes = [I32, ctypes.POINTER(Instance), ctypes.POINTER(MscgParams), P]
     L.stg_fermion_force.argtypes = [P, I32, ctypes.POINTER(D), PP, P, I32, P]
@@ -93,7 +94,7 @@ def lib() -> ctypes.CDLL:
         f = getattr(L, name)
         if f.restype is ctypes.c_int or name in ("stg_lattice_create", "stg_gauge_create", "stg_field_pack",
                                                  "stg_field_unpack", "stg_dslash_eo", "stg_dslash_oe",
-                                                 "stg_dslash_multi", "stg_normal_op", "stg_mscg_solve",
+                                                 "stg_dslash_multi", "stg_normal_op", "stg_normal_op_noalloc", "stg_mscg_solve",
                                                  "stg_mscg_solve_batched", "stg_fermion_force"):
             f.restype = ctypes.c_int
     _lib = L

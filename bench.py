@@ -16,7 +16,8 @@ The same JSON line carries (measured in the same run, outside the timed steps):
   roofline   D_eo FP32-12 against the measured HBM copy bandwidth;
   sweep      16^4 and 32^4 D_eo for every link storage, L2 flushed, median of 50;
   mscg       32^4 msCG (16 poles 1e-5..10, m = 0.01, true residual 1e-10): mixed
-             (FP32, FP16, BF16 inner, FP64 reliable updates) vs pure FP64, s/solve;
+             (FP32, FP16, BF16 inner; double-single reliable updates, FP64-verified) vs pure
+             FP64, s/solve;
   batched    the uneven batch (16^4, 24^3x8, 32^3x8, 24^4, 4 sources x 16 shifts) in one
              solve vs the sum of separate solves;
   force      48^4 fermion-force time (12 shifts, FP64);
@@ -44,8 +45,8 @@ import synthetic as S  # noqa: E402
 METRIC = "D_eo GB/s (% HBM peak); msCG s/solve to 1e-10, mixed vs FP64 on 1 GB300"
 UNIT = "GB/s"
 WORKLOAD = "32^4 D_eo, exp(i0.3H) links FP32 12-real, complex64 vectors, batch of distinct sources"
-LINK_BYTES = {("f64", 18): 144, ("f64", 12): 96, ("f32", 18): 72, ("f32", 12): 48, ("bf16", 12): 24,
-              ("f16", 12): 24}
+LINK_BYTES = {("f64", 18): 144, ("f64", 12): 96, ("ds", 18): 144, ("ds", 12): 96, ("f32", 18): 72,
+              ("f32", 12): 48, ("bf16", 12): 24, ("f16", 12): 24}
 
 
 def workload_config(batch, ws=1):
@@ -59,7 +60,7 @@ def workload_config(batch, ws=1):
 def bytes_per_site(prec, recon):
     """Algorithmic bytes of one D_eo output site: 8 links (all 4V links once over the
     lattice) + one input and one output colour vector."""
-    vec = 48 if prec == "f64" else 24
+    vec = 48 if prec in ("f64", "ds") else 24
     return 8 * LINK_BYTES[(prec, recon)] + 2 * vec
 
 
@@ -200,7 +201,8 @@ def time_deo_sweep(torch, p, dims, reps=50):
     psi = torch.from_numpy(S.gaussian_field(dims, 2000 + 2)).cuda()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     out = []
-    for prec, recon in [("f64", 18), ("f64", 12), ("f32", 18), ("f32", 12), ("f16", 12), ("bf16", 12)]:
+    for prec, recon in [("f64", 18), ("f64", 12), ("ds", 18), ("ds", 12), ("f32", 18), ("f32", 12), ("f16", 12),
+                        ("bf16", 12)]:
         g = p.Gauge(lat, ut, prec, recon)
         x = p.pack(lat, psi, g.vec_prec)
         y = torch.empty_like(x)

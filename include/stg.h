@@ -25,7 +25,9 @@
  * Internal layouts (what stg_dslash_* and stg_normal_op read and write):
  *   F64 field: 3 arrays of Vh double2 (colour-major structure of arrays), 48 B/site.
  *   F32 field: Vh float4 (colours 0,1) followed by Vh float2 (colour 2), 24 B/site.
- *   A gauge of precision F64 works on F64 fields; F32, BF16 and F16 gauges work on F32 fields.
+ *   DS field:  3 arrays of Vh float4 (re.hi, re.lo, im.hi, im.lo), 48 B/site.
+ *   A gauge of precision F64 works on F64 fields, DS on DS fields; F32, BF16 and F16 gauges
+ *   work on F32 fields.
  *
  * Memory.  Every pointer argument named *_dev is device memory owned by the caller
  * and must stay valid until the work queued on `stream` has finished.  Host arrays are
@@ -58,7 +60,10 @@ typedef enum {
     STG_ERR_OOM = -6      /* device allocation failed                                       */
 } stg_status;
 
-typedef enum { STG_F64 = 0, STG_F32 = 1, STG_BF16 = 2, STG_F16 = 3 } stg_prec;
+/* STG_DS: "double-single" storage, every real number as a pair of floats hi + lo (48-bit
+ * significand, relative rounding ~2^-47), computed with error-free FP32 transformations:
+ * FP64-class accuracy on the FP32 pipes.  Same bytes as F64. */
+typedef enum { STG_F64 = 0, STG_F32 = 1, STG_BF16 = 2, STG_F16 = 3, STG_DS = 4 } stg_prec;
 typedef enum { STG_RECON18 = 18, STG_RECON12 = 12 } stg_recon;
 
 typedef struct stg_lattice stg_lattice;
@@ -97,10 +102,10 @@ size_t stg_gauge_bytes(const stg_gauge *g);
 
 /* ---- fermion fields ----------------------------------------------------------------------- */
 
-/* Bytes of one parity's field in the internal layout for vector precision F64 or F32
- * (48 or 24 bytes per site); 0 for any other precision or a NULL lattice. */
+/* Bytes of one parity's field in the internal layout for vector precision F64, DS or F32
+ * (48, 48 or 24 bytes per site); 0 for any other precision or a NULL lattice. */
 size_t stg_field_bytes(const stg_lattice *lat, stg_prec vec_prec);
-/* canonical complex128 [Vh][3] (device) <-> internal layout (device). vec_prec F64 or F32. */
+/* canonical complex128 [Vh][3] (device) <-> internal layout (device). vec_prec F64, DS or F32. */
 stg_status stg_field_pack(const stg_lattice *lat, stg_prec vec_prec, const void *canon_c128_dev, void *internal_dev,
                           void *stream);
 stg_status stg_field_unpack(const stg_lattice *lat, stg_prec vec_prec, const void *internal_dev, void *canon_c128_dev,
@@ -153,9 +158,9 @@ typedef struct {
     double tol;              /* target relative FP64 true residual |b - A_i x_i| / |b| per shift   */
     int32_t max_iter;        /* iteration cap of each phase (> 0)                                 */
     double inner_tol;        /* mixed solves: stopping residual of the inner multi-shift phase
-                                (0 -> 1e-6 for F32 gauges, 2e-3 for BF16/F16 gauges)             */
+                                (0 -> 1e-9 for F32 gauges, 1e-4 for BF16/F16 gauges)             */
     double reliable_delta;   /* mixed solves: reliable update once |r| fell by this factor since
-                                the last one (0 -> 0.1)                                           */
+                                the last one (0 -> 0.01)                                          */
     int32_t log_rows;        /* optional: rows of scalar_log to fill (0 = none)                    */
     double *scalar_log;      /* host [log_rows][2 + nshift]: alpha_k, beta_k, zeta_i^{k+1} of the
                                 first multi-shift iterations of system 0                         */
@@ -168,13 +173,19 @@ typedef struct {
     double *true_resid;       /* host [nshift] (may be NULL): final FP64 |b - A_i x_i| / |b|       */
     int32_t *shift_iters;     /* host [nshift] (may be NULL): multi-shift iteration at which each
                                  shift stopped                                                    */
+    double *inner_resid;      /* host [nshift] (may be NULL): true residual of each shift right
+                                 after the multi-shift phase, before refinement                   */
+    int32_t fp64_fallback;    /* 1 if a mixed solve was repeated with FP64 reliable updates       */
 } stg_mscg_stats;
 
 /* Solves A_{sigma_i} x_i = b for every shift.
  *   g_f64    F64 gauge (RECON18 or RECON12): true residuals, reliable updates, refinement.
  *   g_inner  NULL -> pure FP64 solve.  Otherwise an F32/BF16/F16 gauge on the same lattice:
- *            multi-shift phase in that precision (FP32 vectors, FP64 scalars and reductions),
- *            then each shift above tol is refined by CG with FP64 reliable updates.
+ *            multi-shift phase in that precision (FP32 vectors, FP64 scalars and reductions,
+ *            solutions accumulated in double-single), then each shift above tol is refined by CG
+ *            (FP32 links) with reliable updates in double-single arithmetic; every final residual
+ *            is checked in FP64, and the solve is repeated with FP64 reliable updates if a shift
+ *            fails that check.
  *   b_c128_dev          canonical complex128 [Vh][3] even-site source (device).
  *   x_c128_dev[nshift]  canonical complex128 [Vh][3] outputs (device), may not alias b.
  * Synchronises `stream` before returning.  STG_ERR_NOCONV if a shift is still above tol

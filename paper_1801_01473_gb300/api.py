@@ -21,6 +21,10 @@ from .lib import (PREC, STG_ERR_NOCONV, STG_F32, STG_F64, STG_RECON12, STG_RECON
                   MscgStats, check, lib)
 
 
+# internal field tensors: dtype and elements per site for each vector precision
+_FIELD = {"f64": (torch.float64, 6), "f32": (torch.float32, 6), "ds": (torch.float32, 12)}
+
+
 def _stream(stream=None) -> ctypes.c_void_p:
     s = torch.cuda.current_stream() if stream is None else stream
     return ctypes.c_void_p(s.cuda_stream)
@@ -82,7 +86,7 @@ class Gauge:
         self.lattice = lattice
         self.prec = prec
         self.recon = recon
-        self.vec_prec = "f64" if prec == "f64" else "f32"
+        self.vec_prec = prec if prec in ("f64", "ds") else "f32"
         self.nbytes = int(lib().stg_gauge_bytes(h))
 
     @property
@@ -91,8 +95,8 @@ class Gauge:
 
     def new_field(self, n: int | None = None) -> torch.Tensor:
         """Uninitialised internal-layout field(s) at this gauge's vector precision."""
-        dt = torch.float64 if self.vec_prec == "f64" else torch.float32
-        shape = (6 * self.lattice.Vh,) if n is None else (n, 6 * self.lattice.Vh)
+        dt, per = _FIELD[self.vec_prec]
+        shape = (per * self.lattice.Vh,) if n is None else (n, per * self.lattice.Vh)
         return torch.empty(shape, dtype=dt, device="cuda")
 
     def __del__(self):
@@ -105,16 +109,20 @@ class Gauge:
 # ------------------------------------------------------------------ fields
 
 def pack(lattice: Lattice, canon: torch.Tensor, prec: str = "f64", stream=None) -> torch.Tensor:
-    """Canonical complex128 [Vh, 3] -> internal layout (float64 or float32 [6*Vh])."""
+    """Canonical complex128 [Vh, 3] -> internal layout (float64 [6*Vh] for f64, float32 [6*Vh]
+    for f32, float32 [12*Vh] for ds)."""
     canon = _dev(canon).reshape(lattice.Vh, 3)
-    dt = torch.float64 if prec == "f64" else torch.float32
-    out = torch.empty(6 * lattice.Vh, dtype=dt, device="cuda")
+    dt, per = _FIELD[prec]
+    out = torch.empty(per * lattice.Vh, dtype=dt, device="cuda")
     check(lib().stg_field_pack(lattice.handle, PREC[prec], _ptr(canon), _ptr(out), _stream(stream)), "stg_field_pack")
     return out
 
 
 def unpack(lattice: Lattice, internal: torch.Tensor, stream=None) -> torch.Tensor:
-    prec = "f64" if internal.dtype == torch.float64 else "f32"
+    if internal.dtype == torch.float64:
+        prec = "f64"
+    else:
+        prec = "ds" if internal.numel() == 12 * lattice.Vh else "f32"
     out = torch.empty((lattice.Vh, 3), dtype=torch.complex128, device="cuda")
     check(lib().stg_field_unpack(lattice.handle, PREC[prec], _ptr(internal), _ptr(out), _stream(stream)),
           "stg_field_unpack")
@@ -201,14 +209,16 @@ def _params(shifts, mass, tol, max_iter, inner_tol, reliable_delta, log_rows):
 def _stats(nshift):
     tr = (ctypes.c_double * nshift)()
     si = (ctypes.c_int32 * nshift)()
+    ir = (ctypes.c_double * nshift)()
     st = MscgStats(0, 0, 0, ctypes.cast(tr, ctypes.POINTER(ctypes.c_double)),
-                   ctypes.cast(si, ctypes.POINTER(ctypes.c_int32)))
-    return st, tr, si
+                   ctypes.cast(si, ctypes.POINTER(ctypes.c_int32)), ctypes.cast(ir, ctypes.POINTER(ctypes.c_double)), 0)
+    return st, tr, (si, ir)
 
 
-def _stats_dict(st, tr, si):
+def _stats_dict(st, tr, extra):
+    si, ir = extra
     return dict(iters=st.iters, reliable_updates=st.reliable_updates, refine_iters=st.refine_iters,
-                true_resid=list(tr), shift_iters=list(si))
+                true_resid=list(tr), shift_iters=list(si), inner_resid=list(ir), fp64_fallback=st.fp64_fallback)
 
 
 def mscg(g_f64: Gauge, b: torch.Tensor, shifts, mass: float, tol: float = 1e-10, g_inner: Gauge | None = None,

@@ -51,6 +51,7 @@ template <typename LinkT, int NRHS, int MODE, int BS>
 __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
 {
     using R = typename LinkT::R;
+    pdl_enter();
     const DGroup &G = a.grp[blockIdx.y];
     const int Vh = G.g.Vh;
     if ((int)(blockIdx.x * BS) >= Vh) return;  // block-uniform
@@ -119,7 +120,7 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
 #pragma unroll
     for (int j = 0; j < NRHS; ++j) {
         if (!act[j]) continue;  // uniform over the block
-        double part = 0.0;
+        ProdSum<R> part;
         if (live) {
             cx<R> o[3];
             if (MODE == 0) {
@@ -134,15 +135,18 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
                     o[c] = cx<R>{fma(cj, p[c].re, R(-0.5) * acc[j][c].re), fma(cj, p[c].im, R(-0.5) * acc[j][c].im)};
                 if (MODE == 1) {
 #pragma unroll
-                    for (int c = 0; c < 3; ++c)
-                        part += (double)p[c].re * (double)o[c].re + (double)p[c].im * (double)o[c].im;
+                    for (int c = 0; c < 3; ++c) {
+                        part.add(p[c].re, o[c].re);
+                        part.add(p[c].im, o[c].im);
+                    }
                 } else {
                     cx<R> b[3];
                     Field<R>::load(G.epi_b[j], Vh, h, b);
 #pragma unroll
                     for (int c = 0; c < 3; ++c) {
                         o[c] = cx<R>{b[c].re - o[c].re, b[c].im - o[c].im};
-                        part += (double)o[c].re * (double)o[c].re + (double)o[c].im * (double)o[c].im;
+                        part.add(o[c].re, o[c].re);
+                        part.add(o[c].im, o[c].im);
                     }
                 }
             }
@@ -150,9 +154,9 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
         }
         if (MODE != 0 && G.partial[j] != nullptr) {
             // two warps per 64-site chunk: warp sums, then pairs of warps
-            part = warp_sum(part);
+            double pv = warp_sum(part.value());
             __syncthreads();
-            if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = part;
+            if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = pv;
             __syncthreads();
             constexpr int kChunks = BS / kPartialSites;
             const int c = blockIdx.x * kChunks + threadIdx.x;
@@ -162,16 +166,35 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
     }
 }
 
+// Launches `kernel` with the programmatic-stream-serialization attribute (the kernel must start
+// with pdl_enter()); STG_PDL=0 in the environment launches without it.
+bool pdl_enabled();
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStream_t st, Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
 // Host-side launcher: picks the NRHS instantiation (>= the largest group's nrhs) and the
 // block size `bs` (64, 128 or 256; anything else falls back to 128).
 template <typename LinkT, int NRHS, int BS>
 cudaError_t launch_dslash_nb(const DArgs &a, int mode, int maxv, cudaStream_t st)
 {
     dim3 grid((maxv + BS - 1) / BS, a.ngroups);
-    if (mode == 0) k_dslash<LinkT, NRHS, 0, BS><<<grid, BS, 0, st>>>(a);
-    else if (mode == 1) k_dslash<LinkT, NRHS, 1, BS><<<grid, BS, 0, st>>>(a);
-    else k_dslash<LinkT, NRHS, 2, BS><<<grid, BS, 0, st>>>(a);
-    return cudaGetLastError();
+    if (mode == 0) return launch_pdl(k_dslash<LinkT, NRHS, 0, BS>, grid, dim3(BS), st, a);
+    if (mode == 1) return launch_pdl(k_dslash<LinkT, NRHS, 1, BS>, grid, dim3(BS), st, a);
+    return launch_pdl(k_dslash<LinkT, NRHS, 2, BS>, grid, dim3(BS), st, a);
 }
 
 template <typename LinkT, int NRHS>

@@ -69,11 +69,11 @@ extern "C" stg_status stg_normal_op_noalloc(const stg_gauge *g, double mass, dou
         return set_error(STG_ERR_ARG, "stg_normal_op_noalloc: pointers must be 16-byte aligned");
     if (out_even_dev == in_even_dev) return set_error(STG_ERR_ARG, "stg_normal_op_noalloc: in and out must differ");
     const int Vh = g->g.Vh;
-    const size_t tmp_bytes = ((size_t)Vh * (kind_is_f64(g->kind) ? 48 : 24) + 255) & ~(size_t)255;
+    const size_t tmp_bytes = ((size_t)Vh * kind_vec_bytes(g->kind) + 255) & ~(size_t)255;
     const size_t part_bytes = sizeof(double) * (size_t)dslash_partials(Vh);
     if (tmp_bytes + part_bytes > kStaticScratchBytes)
         return set_error(STG_ERR_ARG, "stg_normal_op_noalloc: lattice too large for the 32 MiB static scratch "
-                                      "(at most 697232 sites per parity for F64 gauges, 1390848 for the others)");
+                                      "(at most 697232 sites per parity for F64/DS gauges, 1390848 for the others)");
     void *base = nullptr;
     stg_status s = static_scratch(&base);
     if (s != STG_OK) return s;

@@ -26,7 +26,10 @@
 // same search direction.  A pair stops when its FP64 true residual is <= tol |b|.
 // For a pure-FP64 solve (no inner gauge) phase 1 runs to tol and phase 2 only checks.
 #include <algorithm>
+#include <chrono>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -64,8 +67,8 @@ __device__ __forceinline__ double norm2_site(const cx<R> v[3])
     return s;
 }
 
-// phase-1 start: r = p_i = b (rounded to R), x_i = 0; partials |r|^2 (R) and |b|^2 (FP64)
-template <typename R>
+// phase-1 start: r = p_i = b (rounded to R), x_i = 0, b64 = b (in H); partials |r|^2 (R) and |b|^2 (FP64)
+template <typename R, typename H>
 __global__ void __launch_bounds__(kVecBlock) k_p1_init(const SysVecs *__restrict__ sv, int nshift)
 {
     const SysVecs &V = sv[blockIdx.y];
@@ -73,28 +76,29 @@ __global__ void __launch_bounds__(kVecBlock) k_p1_init(const SysVecs *__restrict
     int h = blockIdx.x * kVecBlock + threadIdx.x;
     double pr = 0.0, pb = 0.0;
     if (h < V.Vh) {
-        cx<R> v[3], z[3];
+        cx<R> v[3];
+        cx<H> z[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
             double2 d = V.bcanon[(size_t)h * 3 + c];
             pb += d.x * d.x + d.y * d.y;
             v[c] = cx<R>{(R)d.x, (R)d.y};
-            z[c] = cx<R>{R(0), R(0)};
+            z[c] = cx<H>{H(0), H(0)};
         }
         pr = norm2_site(v);
         Field<R>::store(V.r, V.Vh, h, v);
         for (int i = 0; i < nshift; ++i) {
             Field<R>::store(V.p[i], V.Vh, h, v);
-            Field<R>::store(V.x[i], V.Vh, h, z);
+            Field<H>::store(V.x[i], V.Vh, h, z);
         }
         if (V.b64) {
-            cx<double> w[3];
+            cx<H> w[3];
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
                 double2 d = V.bcanon[(size_t)h * 3 + c];
-                w[c] = cx<double>{d.x, d.y};
+                w[c] = cx<H>{H(d.x), H(d.y)};
             }
-            Field<double>::store(V.b64, V.Vh, h, w);
+            Field<H>::store(V.b64, V.Vh, h, w);
         }
     }
     __shared__ double sh[32];
@@ -104,71 +108,109 @@ __global__ void __launch_bounds__(kVecBlock) k_p1_init(const SysVecs *__restrict
     if (threadIdx.x == 0) V.part_v2[blockIdx.x] = t;
 }
 
-// r -= alpha q, partial |r|^2
-template <typename R>
-__global__ void __launch_bounds__(kVecBlock) k_update_r(const SysScal *__restrict__ sc, const SysVecs *__restrict__ sv)
+// Work list of the per-iteration vector kernels: the kVecBlock-site blocks of every system laid
+// end to end (system s owns items [start[s], start[s+1])).  The kernels run persistently, each
+// thread block striding over the items; items of systems that are not running are skipped at the
+// cost of one flag read, so a batch of many systems does not launch hundreds of thousands of
+// mostly idle blocks per iteration.
+struct WorkList {
+    const int *start;  // [nsys + 1]
+    int nsys, total;
+};
+
+// first system whose items include `b`, scanning forward from `s` (items are visited in order)
+__device__ __forceinline__ int advance_sys(const WorkList &w, int s, int b)
 {
-    const SysScal &S = sc[blockIdx.y];
-    const SysVecs &V = sv[blockIdx.y];
-    if (!S.running || (int)(blockIdx.x * kVecBlock) >= V.Vh) return;
-    int h = blockIdx.x * kVecBlock + threadIdx.x;
-    double pr = 0.0;
-    if (h < V.Vh) {
-        const R a = (R)S.alpha;
-        cx<R> r[3], q[3];
-        Field<R>::load_rw(V.r, V.Vh, h, r);
-        Field<R>::load_rw(V.q, V.Vh, h, q);
-#pragma unroll
-        for (int c = 0; c < 3; ++c) r[c] = cx<R>{fma(-a, q[c].re, r[c].re), fma(-a, q[c].im, r[c].im)};
-        Field<R>::store(V.r, V.Vh, h, r);
-        pr = norm2_site(r);
-    }
-    __shared__ double sh[32];
-    double t = block_sum(pr, sh);
-    if (threadIdx.x == 0) V.part_v[blockIdx.x] = t;
+    while (s + 1 < w.nsys && w.start[s + 1] <= b) ++s;
+    return s;
 }
 
-// x_i += cx_i p_i ; p_i = cr_i r + cp_i p_i  for the shifts flagged by k_beta
+// r -= alpha q, partial |r|^2
 template <typename R>
-__global__ void __launch_bounds__(kVecBlock) k_update_shifts(const SysScal *__restrict__ sc,
-                                                              const SysVecs *__restrict__ sv)
+__global__ void __launch_bounds__(kVecBlock) k_update_r(const SysScal *__restrict__ sc, const SysVecs *__restrict__ sv,
+                                                         const WorkList w)
 {
-    const SysScal &S = sc[blockIdx.y];
-    const SysVecs &V = sv[blockIdx.y];
-    if (!S.running || (int)(blockIdx.x * kVecBlock) >= V.Vh) return;
-    __shared__ R s_cx[kMaxShifts], s_cr[kMaxShifts], s_cp[kMaxShifts];
-    __shared__ int s_ux[kMaxShifts], s_up[kMaxShifts];
-    const int ns = S.nshift;
-    if (threadIdx.x < ns) {
-        s_cx[threadIdx.x] = (R)S.cx[threadIdx.x];
-        s_cr[threadIdx.x] = (R)S.cr[threadIdx.x];
-        s_cp[threadIdx.x] = (R)S.cp[threadIdx.x];
-        s_ux[threadIdx.x] = S.upd_x[threadIdx.x];
-        s_up[threadIdx.x] = S.upd_p[threadIdx.x];
-    }
-    __syncthreads();
-    int h = blockIdx.x * kVecBlock + threadIdx.x;
-    if (h >= V.Vh) return;
-    cx<R> r[3];
-    Field<R>::load_rw(V.r, V.Vh, h, r);
-    for (int i = 0; i < ns; ++i) {
-        const int ux = s_ux[i], up = s_up[i];
-        if (!ux && !up) continue;
-        cx<R> p[3];
-        Field<R>::load_rw(V.p[i], V.Vh, h, p);
-        if (ux) {
-            cx<R> x[3];
-            Field<R>::load_rw(V.x[i], V.Vh, h, x);
-            const R a = s_cx[i];
+    pdl_enter();
+    __shared__ double sh[32];
+    int s = 0;
+    for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+        s = advance_sys(w, s, b);
+        const SysScal &S = sc[s];
+        if (!S.running) continue;  // uniform over the block
+        const SysVecs &V = sv[s];
+        const int lb = b - w.start[s];
+        const int h = lb * kVecBlock + threadIdx.x;
+        double pr = 0.0;
+        if (h < V.Vh) {
+            const R a = (R)S.alpha;
+            cx<R> r[3], q[3];
+            Field<R>::load_rw(V.r, V.Vh, h, r);
+            Field<R>::load_rw(V.q, V.Vh, h, q);
 #pragma unroll
-            for (int c = 0; c < 3; ++c) x[c] = cx<R>{fma(a, p[c].re, x[c].re), fma(a, p[c].im, x[c].im)};
-            Field<R>::store(V.x[i], V.Vh, h, x);
+            for (int c = 0; c < 3; ++c) r[c] = cx<R>{fma(-a, q[c].re, r[c].re), fma(-a, q[c].im, r[c].im)};
+            Field<R>::store(V.r, V.Vh, h, r);
+            pr = norm2_site(r);
         }
-        if (up) {
-            const R zr = s_cr[i], b = s_cp[i];
+        double t = block_sum(pr, sh);
+        if (threadIdx.x == 0) V.part_v[lb] = t;
+    }
+}
+
+// x_i += cx_i p_i ; p_i = cr_i r + cp_i p_i  for the shifts flagged by k_beta.
+// p_i and r are in the iteration precision R, the solutions x_i in X (FP64 or double-single, so
+// that x_i keeps digits the FP32 search directions cannot).
+template <typename R, typename X>
+__global__ void __launch_bounds__(kVecBlock) k_update_shifts(const SysScal *__restrict__ sc,
+                                                              const SysVecs *__restrict__ sv, const WorkList w)
+{
+    pdl_enter();
+    __shared__ X s_cx[kMaxShifts];
+    __shared__ R s_cr[kMaxShifts], s_cp[kMaxShifts];
+    __shared__ int s_ux[kMaxShifts], s_up[kMaxShifts];
+    int s = 0, loaded = -1;
+    for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+        s = advance_sys(w, s, b);
+        const SysScal &S = sc[s];
+        if (!S.running) continue;  // uniform over the block
+        const SysVecs &V = sv[s];
+        const int ns = S.nshift;
+        if (loaded != s) {
+            __syncthreads();  // previous item's readers are done with the coefficients
+            if (threadIdx.x < ns) {
+                s_cx[threadIdx.x] = X(S.cx[threadIdx.x]);
+                s_cr[threadIdx.x] = (R)S.cr[threadIdx.x];
+                s_cp[threadIdx.x] = (R)S.cp[threadIdx.x];
+                s_ux[threadIdx.x] = S.upd_x[threadIdx.x];
+                s_up[threadIdx.x] = S.upd_p[threadIdx.x];
+            }
+            __syncthreads();
+            loaded = s;
+        }
+        const int h = (b - w.start[s]) * kVecBlock + threadIdx.x;
+        if (h >= V.Vh) continue;
+        cx<R> r[3];
+        Field<R>::load_rw(V.r, V.Vh, h, r);
+        for (int i = 0; i < ns; ++i) {
+            const int ux = s_ux[i], up = s_up[i];
+            if (!ux && !up) continue;
+            cx<R> p[3];
+            Field<R>::load_rw(V.p[i], V.Vh, h, p);
+            if (ux) {
+                cx<X> x[3];
+                Field<X>::load_rw(V.x[i], V.Vh, h, x);
+                const X a = s_cx[i];
 #pragma unroll
-            for (int c = 0; c < 3; ++c) p[c] = cx<R>{fma(zr, r[c].re, b * p[c].re), fma(zr, r[c].im, b * p[c].im)};
-            Field<R>::store(V.p[i], V.Vh, h, p);
+                for (int c = 0; c < 3; ++c)
+                    x[c] = cx<X>{fma(a, X(p[c].re), x[c].re), fma(a, X(p[c].im), x[c].im)};
+                Field<X>::store(V.x[i], V.Vh, h, x);
+            }
+            if (up) {
+                const R zr = s_cr[i], bb = s_cp[i];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    p[c] = cx<R>{fma(zr, r[c].re, bb * p[c].re), fma(zr, r[c].im, bb * p[c].im)};
+                Field<R>::store(V.p[i], V.Vh, h, p);
+            }
         }
     }
 }
@@ -180,6 +222,30 @@ __device__ __forceinline__ double warp_sum_strided(const double *a, int n)
     double s = 0.0;
     for (int k = threadIdx.x; k < n; k += 32) s += a[k];
     return warp_sum(s);
+}
+
+constexpr int kScalBlock = 256;
+
+// Fixed-order sum of n partials by a whole block of kScalBlock threads (each thread a strided
+// slice, then a fixed tree), returned to every thread.  Many loads in flight: a one-warp sum of
+// the 8192 partials of a 32^4 lattice is latency-bound at tens of microseconds.
+__device__ __forceinline__ double block_sum_strided(const double *a, int n, double *sh)
+{
+    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    int k = threadIdx.x;
+    for (; k + 3 * kScalBlock < n; k += 4 * kScalBlock) {
+        s0 += a[k];
+        s1 += a[k + kScalBlock];
+        s2 += a[k + 2 * kScalBlock];
+        s3 += a[k + 3 * kScalBlock];
+    }
+    for (; k < n; k += kScalBlock) s0 += a[k];
+    double t = block_sum((s0 + s1) + (s2 + s3), sh);
+    if (threadIdx.x == 0) sh[32] = t;
+    __syncthreads();
+    t = sh[32];
+    __syncthreads();
+    return t;
 }
 
 __device__ __forceinline__ int warp_sum_int(int v)
@@ -217,15 +283,18 @@ __global__ void k_p1_init_scal(SysScal *sc, const SysVecs *sv, int *done, double
     }
 }
 
-__global__ void k_alpha(SysScal *sc, const SysVecs *sv, const int *done)
+__global__ void __launch_bounds__(kScalBlock) k_alpha(SysScal *sc, const SysVecs *sv, const int *done)
 {
+    pdl_enter();
     SysScal &S = sc[blockIdx.x];
     if (done[blockIdx.x]) {
         if (threadIdx.x == 0) S.running = 0;
         return;
     }
     const SysVecs &V = sv[blockIdx.x];
-    const double pq = warp_sum_strided(V.part_d, V.nblk_d);
+    __shared__ double sh[33];
+    const double pq = block_sum_strided(V.part_d, V.nblk_d, sh);
+    if (threadIdx.x >= 32) return;  // the per-shift recurrences run in warp 0
     const double alpha = S.rr / pq;
     for (int i = threadIdx.x; i < S.nshift; i += 32) {
         if (!S.active[i]) continue;
@@ -241,12 +310,16 @@ __global__ void k_alpha(SysScal *sc, const SysVecs *sv, const int *done)
     }
 }
 
-__global__ void k_beta(SysScal *sc, const SysVecs *sv, int *done, int *need_rel, double *log, int log_rows)
+__global__ void __launch_bounds__(kScalBlock) k_beta(SysScal *sc, const SysVecs *sv, int *done, int *need_rel,
+                                                      double *log, int log_rows)
 {
+    pdl_enter();
     SysScal &S = sc[blockIdx.x];
     if (!S.running) return;
     const SysVecs &V = sv[blockIdx.x];
-    const double rr_new = warp_sum_strided(V.part_v, V.nblk_v);
+    __shared__ double sh[33];
+    const double rr_new = block_sum_strided(V.part_v, V.nblk_v, sh);
+    if (threadIdx.x >= 32) return;  // the per-shift recurrences run in warp 0
     const double beta = rr_new / S.rr;
     const int ns = S.nshift;
     int nact = 0;
@@ -304,8 +377,8 @@ __global__ void k_beta(SysScal *sc, const SysVecs *sv, int *done, int *need_rel,
 
 // ------------------------------------------------------------------ phase-2 kernels
 
-// x_hi (FP64) += y (inner), y = 0   for pairs in the current reliable update
-template <typename R>
+// x_hi (H) += y (inner), y = 0   for pairs in the current reliable update
+template <typename R, typename H>
 __global__ void __launch_bounds__(kVecBlock) k_rel_fold(const SysVecs *__restrict__ sv, const int *__restrict__ noupd)
 {
     if (noupd[blockIdx.y]) return;
@@ -313,15 +386,15 @@ __global__ void __launch_bounds__(kVecBlock) k_rel_fold(const SysVecs *__restric
     int h = blockIdx.x * kVecBlock + threadIdx.x;
     if (h >= V.Vh) return;
     cx<R> y[3], z[3];
-    cx<double> x[3];
+    cx<H> x[3];
     Field<R>::load_rw(V.x[0], V.Vh, h, y);
-    Field<double>::load_rw(V.xhi, V.Vh, h, x);
+    Field<H>::load_rw(V.xhi, V.Vh, h, x);
 #pragma unroll
     for (int c = 0; c < 3; ++c) {
-        x[c] = cx<double>{x[c].re + (double)y[c].re, x[c].im + (double)y[c].im};
+        x[c] = cx<H>{x[c].re + H(y[c].re), x[c].im + H(y[c].im)};
         z[c] = cx<R>{R(0), R(0)};
     }
-    Field<double>::store(V.xhi, V.Vh, h, x);
+    Field<H>::store(V.xhi, V.Vh, h, x);
     Field<R>::store(V.x[0], V.Vh, h, z);
 }
 
@@ -357,7 +430,7 @@ __global__ void k_rel_finish(SysScal *sc, const SysVecs *sv, const int *noupd, i
 }
 
 // r = inner(r_hi) (and, at the start of phase 2, p = r, y = 0); partial |r|^2
-template <typename R>
+template <typename R, typename H>
 __global__ void __launch_bounds__(kVecBlock) k_rel_copy(const SysVecs *__restrict__ sv, const int *__restrict__ noupd,
                                                          const int *__restrict__ finished, int start)
 {
@@ -367,9 +440,9 @@ __global__ void __launch_bounds__(kVecBlock) k_rel_copy(const SysVecs *__restric
     int h = blockIdx.x * kVecBlock + threadIdx.x;
     double pr = 0.0;
     if (h < V.Vh) {
-        cx<double> rh[3];
+        cx<H> rh[3];
         cx<R> r[3];
-        Field<double>::load_rw(V.rhi, V.Vh, h, rh);
+        Field<H>::load_rw(V.rhi, V.Vh, h, rh);
 #pragma unroll
         for (int c = 0; c < 3; ++c) r[c] = cx<R>{(R)rh[c].re, (R)rh[c].im};
         Field<R>::store(V.r, V.Vh, h, r);
@@ -409,37 +482,47 @@ __global__ void k_rel_scal(SysScal *sc, const SysVecs *sv, const int *noupd, con
     }
 }
 
-// FP64 copy/convert x_inner -> x_hi for (system, shift) pairs (phase-1 results)
+// FP64 verification: true_rr = |r|^2 from the partials of the FP64 residual epilogue
+__global__ void k_verify(const SysVecs *sv, double *true_rr)
+{
+    const double rr = warp_sum_strided(sv[blockIdx.x].part_d, sv[blockIdx.x].nblk_d);
+    if (threadIdx.x == 0) true_rr[blockIdx.x] = rr;
+}
+
+// one (source, destination) field pair of a batched conversion
 struct ConvPair {
     const void *src;
     void *dst;
     int Vh;
 };
 
-template <typename R>
-__global__ void __launch_bounds__(kVecBlock) k_convert_to_f64(const ConvPair *__restrict__ pr)
+// field conversion src (type S) -> dst (type D), one (src, dst) pair per blockIdx.y; src may
+// equal dst when both layouts have the same size (each thread rewrites its own 16-byte slots)
+template <typename S, typename D>
+__global__ void __launch_bounds__(kVecBlock) k_convert_pairs(const ConvPair *__restrict__ pr)
 {
     const ConvPair &P = pr[blockIdx.y];
     int h = blockIdx.x * kVecBlock + threadIdx.x;
     if (h >= P.Vh) return;
-    cx<R> v[3];
-    cx<double> w[3];
-    Field<R>::load_rw(P.src, P.Vh, h, v);
+    cx<S> v[3];
+    cx<D> w[3];
+    Field<S>::load_rw(P.src, P.Vh, h, v);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) w[c] = cx<double>{(double)v[c].re, (double)v[c].im};
-    Field<double>::store(P.dst, P.Vh, h, w);
+    for (int c = 0; c < 3; ++c) w[c] = cx<D>{D(v[c].re), D(v[c].im)};
+    Field<D>::store(P.dst, P.Vh, h, w);
 }
 
+template <typename H>
 __global__ void __launch_bounds__(kVecBlock) k_unpack_pairs(const ConvPair *__restrict__ pr)
 {
     const ConvPair &P = pr[blockIdx.y];
     int h = blockIdx.x * kVecBlock + threadIdx.x;
     if (h >= P.Vh) return;
-    cx<double> v[3];
-    Field<double>::load_rw(P.src, P.Vh, h, v);
+    cx<H> v[3];
+    Field<H>::load_rw(P.src, P.Vh, h, v);
     double2 *o = static_cast<double2 *>(P.dst);
 #pragma unroll
-    for (int c = 0; c < 3; ++c) o[(size_t)h * 3 + c] = make_double2(v[c].re, v[c].im);
+    for (int c = 0; c < 3; ++c) o[(size_t)h * 3 + c] = make_double2((double)v[c].re, (double)v[c].im);
 }
 
 // ------------------------------------------------------------------ host engine
@@ -468,6 +551,7 @@ struct InstInfo {
     const stg_gauge *gi;   // gauge of the multi-shift iterations
     const stg_gauge *gr;   // gauge of the refinement iterations
     const stg_gauge *g64;  // FP64 gauge
+    const stg_gauge *gh;   // gauge of the true residuals (g64 or its double-single companion)
     int nrhs;
     int sys0;              // first phase-1 system of this instance
 };
@@ -492,10 +576,17 @@ static void add_group(std::vector<DArgs> &lst, const DGroup &G, int out_par)
 
 }  // namespace
 
-template <typename R>
-static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg_params *prm, cudaStream_t user_st)
+// R: precision of the iterations (float: mixed solve, double: pure FP64 solve).
+// H: precision of the solutions, sources and true residuals (double, or dsf for the mixed solve's
+//    reliable updates, whose results are then verified in FP64; *retry_f64 is set when that
+//    verification fails so the caller can repeat the solve with H = double).
+template <typename R, typename H>
+static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg_params *prm, cudaStream_t user_st,
+                             bool *retry_f64)
 {
     const bool mixed = !std::is_same<R, double>::value;
+    constexpr bool kDS = std::is_same<H, dsf>::value;
+    *retry_f64 = false;
     const int ns = prm->nshift;
     const double mass2 = prm->mass * prm->mass;
     double sigma0 = prm->shifts[0];
@@ -524,11 +615,43 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
             if (s != STG_OK) return s;
         }
     const int kind_r = ii[0].gr->kind;
+    // operator of the true residuals: the F64 gauge, or its double-single companion
+    for (int k = 0; k < ninst; ++k) {
+        ii[k].gh = ii[k].g64;
+        if (kDS) {
+            stg_status s = ds_companion(ii[k].g64, user_st, &ii[k].gh);
+            if (s != STG_OK) return s;
+        }
+    }
+    const int kind_h = ii[0].gh->kind;
+    // defaults measured on the 32^4, 16-pole workload: running the FP32 multi-shift phase on to an
+    // iterated 1e-9 costs fewer iterations than it saves in refinement; reliable updates every
+    // two decades keep the FP32 recurrences well inside their accuracy
     const double inner_tol = mixed ? (prm->inner_tol > 0 ? prm->inner_tol
-                                                          : (kind_i == kBF16R12 || kind_i == kF16R12 ? 2e-3 : 1e-6))
+                                                          : (kind_i == kBF16R12 || kind_i == kF16R12 ? 1e-4 : 1e-9))
                                    : prm->tol;
-    const double delta = prm->reliable_delta > 0 ? prm->reliable_delta : 0.1;
+    const double delta = prm->reliable_delta > 0 ? prm->reliable_delta : 0.01;
     const int vb = Field<R>::kBytesPerSite;
+
+    // The workspace comes from the device's default stream-ordered memory pool.  Keep up to
+    // 64 GiB of freed pool memory mapped between solves (the default threshold of 0 returns it at
+    // every synchronisation and the next solve pays for mapping it again).
+    {
+        int dev = 0;
+        cudaMemPool_t pool;
+        if (cudaGetDevice(&dev) == cudaSuccess && cudaDeviceGetDefaultMemPool(&pool, dev) == cudaSuccess) {
+            uint64_t thr = 64ull << 30;
+            cudaMemPoolSetAttribute(pool, cudaMemPoolAttrReleaseThreshold, &thr);
+        }
+        cudaGetLastError();
+    }
+    const bool verbose = getenv("STG_VERBOSE") && getenv("STG_VERBOSE")[0] == '1';
+    auto t_start = std::chrono::steady_clock::now();
+    auto stamp = [&](const char *what) {
+        if (!verbose) return;
+        double ms = std::chrono::duration<double, std::milli>(std::chrono::steady_clock::now() - t_start).count();
+        fprintf(stderr, "[stg mscg] %8.3f ms  %s\n", ms, what);
+    };
 
     // work stream ordered after the caller's stream
     cudaStream_t ws;
@@ -573,7 +696,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
             V.t = mem.alloc(fb);
             for (int i = 0; i < ns; ++i) {
                 V.p[i] = mem.alloc(fb);
-                V.x[i] = mixed ? mem.alloc(fb) : nullptr;  // FP64 solves accumulate straight into x_hi
+                V.x[i] = nullptr;  // accumulated straight into the pair's x_hi (precision H)
             }
             V.b64 = mem.alloc(f64b);
             V.bcanon = static_cast<const double2 *>(inst[k].b[r]);
@@ -593,7 +716,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
                 W.nblk_d = nbd;
                 W.nblk_v = nbv;
                 W.xhi = mem.alloc(f64b);
-                if (!mixed) V.x[i] = W.xhi;
+                V.x[i] = W.xhi;
                 W.rhi = mem.alloc(f64b);
                 W.t64 = mem.alloc(f64b);
                 W.b64 = V.b64;
@@ -620,7 +743,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     double *d_true_rr = static_cast<double *>(mem.alloc(sizeof(double) * npair));
     double *d_log = prm->log_rows > 0 ? static_cast<double *>(mem.alloc(sizeof(double) * prm->log_rows * (2 + ns)))
                                       : nullptr;
-    ConvPair *d_pairs = static_cast<ConvPair *>(mem.alloc(sizeof(ConvPair) * npair));
+    ConvPair *d_pairs = static_cast<ConvPair *>(mem.alloc(sizeof(ConvPair) * (npair + nsys)));
     if (mem.err != cudaSuccess) return cuda_error(mem.err, "stg_mscg_solve: workspace allocation");
     int *done1 = d_flags, *need1 = d_flags + nsys, *done2 = d_flags + 2 * nsys, *need2 = done2 + npair,
         *noupd = need2 + npair, *finished = noupd + npair, *relcnt = finished + npair;
@@ -671,19 +794,22 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
             add_group(p1.eo, Geo, 0);
         }
     }
-    // phase 2: the (rhs, shift) pairs of one instance share link loads
-    DPlan p2, p64;
+    // phase 2: the (rhs, shift) pairs of one instance share link loads, in groups of `rg`
+    // right-hand sides per thread (STG_REFINE_GROUP, 1..8, default 4: faster than 8 at 32^4)
+    int rg = 4;
+    if (const char *e = getenv("STG_REFINE_GROUP")) rg = std::max(1, std::min(kMaxRhs, atoi(e)));
+    DPlan p2, p64, p64f;  // p64: residuals with gh; p64f: the same with the F64 gauge (verification)
     for (int k = 0; k < ninst; ++k) {
         const int first = ii[k].sys0 * ns, cnt = ii[k].nrhs * ns;
-        for (int q0 = 0; q0 < cnt; q0 += kMaxRhs) {
+        for (int q0 = 0; q0 < cnt; q0 += rg) {
             DGroup Goe, Geo, Hoe, Heo;
             memset(&Goe, 0, sizeof(Goe));
             Goe.g = ii[k].gr->g;
             Goe.links = ii[k].gr->links;
-            Goe.nrhs = std::min(kMaxRhs, cnt - q0);
+            Goe.nrhs = std::min(rg, cnt - q0);
             Geo = Goe;
             Hoe = Goe;
-            Hoe.links = ii[k].g64->links;
+            Hoe.links = ii[k].gh->links;
             Heo = Hoe;
             for (int j = 0; j < Goe.nrhs; ++j) {
                 const int pidx = first + q0 + j;
@@ -713,23 +839,59 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
             add_group(p2.eo, Geo, 0);
             add_group(p64.oe, Hoe, 1);
             add_group(p64.eo, Heo, 0);
+            Hoe.links = Heo.links = ii[k].g64->links;
+            add_group(p64f.oe, Hoe, 1);
+            add_group(p64f.eo, Heo, 0);
         }
     }
 
     const dim3 vgrid1(nblkv_max, nsys), vgrid2(nblkv_max, npair);
 
-    auto iterate = [&](int kind, const DPlan &pl, SysScal *dS, SysVecs *dV, int *dn, int *nr, int n, dim3 vg,
+    // work lists of the persistent per-iteration vector kernels (phase 1: systems, phase 2: pairs)
+    WorkList wl1, wl2;
+    {
+        std::vector<int> st1(nsys + 1, 0), st2(npair + 1, 0);
+        for (int s = 0; s < nsys; ++s) st1[s + 1] = st1[s] + v1[s].nblk_v;
+        for (int q = 0; q < npair; ++q) st2[q + 1] = st2[q] + v2[q].nblk_v;
+        int *d_st = static_cast<int *>(mem.alloc(sizeof(int) * (nsys + npair + 2)));
+        if (mem.err != cudaSuccess) return cuda_error(mem.err, "stg_mscg_solve: workspace allocation");
+        STG_CUDA_TRY(cudaMemcpyAsync(d_st, st1.data(), sizeof(int) * (nsys + 1), cudaMemcpyHostToDevice, ws));
+        STG_CUDA_TRY(cudaMemcpyAsync(d_st + nsys + 1, st2.data(), sizeof(int) * (npair + 1), cudaMemcpyHostToDevice, ws));
+        wl1 = WorkList{d_st, nsys, st1[nsys]};
+        wl2 = WorkList{d_st + nsys + 1, npair, st2[npair]};
+    }
+    int nsm = 152;
+    {
+        int dev = 0;
+        if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    }
+    const int pgrid_max = nsm * (2048 / kVecBlock);  // one full wave of resident blocks
+    const dim3 pgrid1(std::min(wl1.total, pgrid_max)), pgrid2(std::min(wl2.total, pgrid_max));
+
+    auto iterate = [&](int kind, const DPlan &pl, SysScal *dS, SysVecs *dV, int *dn, int *nr, int n, dim3 /*vg*/,
                        double *log, int log_rows) -> cudaError_t {
         cudaError_t e;
+        const bool ph1 = &pl == &p1;
+        const WorkList &wl = ph1 ? wl1 : wl2;
+        const dim3 vg = ph1 ? pgrid1 : pgrid2;
         for (const DArgs &a : pl.oe)
             if ((e = launch_dslash(kind, a, 0, ws)) != cudaSuccess) return e;
         for (const DArgs &a : pl.eo)
             if ((e = launch_dslash(kind, a, 1, ws)) != cudaSuccess) return e;
-        k_alpha<<<n, 32, 0, ws>>>(dS, dV, dn);
-        k_update_r<R><<<vg, kVecBlock, 0, ws>>>(dS, dV);
-        k_beta<<<n, 32, 0, ws>>>(dS, dV, dn, nr, log, log_rows);
-        k_update_shifts<R><<<vg, kVecBlock, 0, ws>>>(dS, dV);
-        return cudaGetLastError();
+        if ((e = launch_pdl(k_alpha, dim3(n), dim3(kScalBlock), ws, dS, (const SysVecs *)dV, (const int *)dn)) !=
+            cudaSuccess)
+            return e;
+        if ((e = launch_pdl(k_update_r<R>, vg, dim3(kVecBlock), ws, (const SysScal *)dS, (const SysVecs *)dV, wl)) !=
+            cudaSuccess)
+            return e;
+        if ((e = launch_pdl(k_beta, dim3(n), dim3(kScalBlock), ws, dS, (const SysVecs *)dV, dn, nr, log, log_rows)) !=
+            cudaSuccess)
+            return e;
+        if (ph1)  // multi-shift phase: solutions in H
+            e = launch_pdl(k_update_shifts<R, H>, vg, dim3(kVecBlock), ws, (const SysScal *)dS, (const SysVecs *)dV, wl);
+        else      // refinement: the correction y in R
+            e = launch_pdl(k_update_shifts<R, R>, vg, dim3(kVecBlock), ws, (const SysScal *)dS, (const SysVecs *)dV, wl);
+        return e;
     };
 
     // Chunks of `kChunk` iterations are captured once per phase into a CUDA graph and replayed;
@@ -790,24 +952,21 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     };
     GraphCache gc1, gc2;
 
+    if (verbose) {
+        cudaStreamSynchronize(ws);
+        stamp("workspace ready");
+    }
     // ---------------- phase 1
-    k_p1_init<R><<<vgrid1, kVecBlock, 0, ws>>>(d_v1, ns);
+    k_p1_init<R, H><<<vgrid1, kVecBlock, 0, ws>>>(d_v1, ns);
     k_p1_init_scal<<<nsys, 32, 0, ws>>>(d_s1, d_v1, done1, inner_tol);
     STG_CUDA_TRY(cudaGetLastError());
     std::vector<int> h_done1(nsys), h_need1(nsys);
     stg_status st = run_until_done(gc1, kind_i, p1, d_s1, d_v1, done1, need1, nsys, vgrid1, d_log, prm->log_rows, false,
                                    h_done1, h_need1);
     if (st != STG_OK) return st;
+    stamp("phase 1 (multi-shift CG) done");
 
-    // ---------------- phase 2: FP64 true residuals, refinement with reliable updates
-    if (mixed) {
-        std::vector<ConvPair> cp(npair);
-        for (int s = 0; s < nsys; ++s)
-            for (int i = 0; i < ns; ++i) cp[s * ns + i] = ConvPair{v1[s].x[i], v2[s * ns + i].xhi, v1[s].Vh};
-        STG_CUDA_TRY(cudaMemcpyAsync(d_pairs, cp.data(), sizeof(ConvPair) * npair, cudaMemcpyHostToDevice, ws));
-        k_convert_to_f64<R><<<vgrid2, kVecBlock, 0, ws>>>(d_pairs);
-        STG_CUDA_TRY(cudaGetLastError());
-    }
+    // ---------------- phase 2: true residuals (precision H), refinement with reliable updates
     // per-pair |b|^2 and tolerances from phase 1
     {
         std::vector<SysScal> tmp(nsys);
@@ -827,11 +986,11 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     std::vector<int> h_done2(npair, 1), h_need2(npair, 1), h_fin(npair, 0), h_noupd(npair, 0);
     auto reliable_update = [&](bool start) -> stg_status {
         STG_CUDA_TRY(cudaMemcpyAsync(noupd, h_noupd.data(), sizeof(int) * npair, cudaMemcpyHostToDevice, ws));
-        if (!start) k_rel_fold<R><<<vgrid2, kVecBlock, 0, ws>>>(d_v2, noupd);
-        for (const DArgs &a : p64.oe) STG_CUDA_TRY(launch_dslash(kind_64, a, 0, ws));
-        for (const DArgs &a : p64.eo) STG_CUDA_TRY(launch_dslash(kind_64, a, 2, ws));
+        if (!start) k_rel_fold<R, H><<<vgrid2, kVecBlock, 0, ws>>>(d_v2, noupd);
+        for (const DArgs &a : p64.oe) STG_CUDA_TRY(launch_dslash(kind_h, a, 0, ws));
+        for (const DArgs &a : p64.eo) STG_CUDA_TRY(launch_dslash(kind_h, a, 2, ws));
         k_rel_finish<<<npair, 32, 0, ws>>>(d_s2, d_v2, noupd, done2, need2, finished, d_true_rr, relcnt);
-        k_rel_copy<R><<<vgrid2, kVecBlock, 0, ws>>>(d_v2, noupd, finished, start ? 1 : 0);
+        k_rel_copy<R, H><<<vgrid2, kVecBlock, 0, ws>>>(d_v2, noupd, finished, start ? 1 : 0);
         k_rel_scal<<<npair, 32, 0, ws>>>(d_s2, d_v2, noupd, finished, start ? 1 : 0);
         STG_CUDA_TRY(cudaGetLastError());
         STG_CUDA_TRY(cudaMemcpyAsync(h_fin.data(), finished, sizeof(int) * npair, cudaMemcpyDeviceToHost, ws));
@@ -841,6 +1000,10 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     // every pair starts with a true-residual check
     st = reliable_update(true);
     if (st != STG_OK) return st;
+    stamp("FP64 residuals of the multi-shift solutions done");
+    std::vector<double> trr0(npair);
+    STG_CUDA_TRY(cudaMemcpy(trr0.data(), d_true_rr, sizeof(double) * npair, cudaMemcpyDeviceToHost));
+    int rounds = 0, chunks_before = 0;
     const long long rel_cap = 4LL * prm->max_iter + 64;
     for (long long round = 0; round < rel_cap; ++round) {
         bool all = true;
@@ -862,6 +1025,44 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         }
         st = reliable_update(false);
         if (st != STG_OK) return st;
+        ++rounds;
+    }
+    if (verbose) {
+        char buf[96];
+        snprintf(buf, sizeof buf, "phase 2 (refinement) done: %d reliable-update rounds", rounds);
+        stamp(buf);
+    }
+    (void)chunks_before;
+
+    // ---------------- FP64 verification of double-single results
+    if (kDS) {
+        // x_hi (per pair) and b (per system) to FP64 in place: same 48-byte site layout
+        std::vector<ConvPair> cp;
+        for (int q = 0; q < npair; ++q) cp.push_back(ConvPair{v2[q].xhi, v2[q].xhi, v2[q].Vh});
+        for (int s = 0; s < nsys; ++s) cp.push_back(ConvPair{v1[s].b64, v1[s].b64, v1[s].Vh});
+        STG_CUDA_TRY(cudaMemcpyAsync(d_pairs, cp.data(), sizeof(ConvPair) * cp.size(), cudaMemcpyHostToDevice, ws));
+        k_convert_pairs<dsf, double><<<dim3(nblkv_max, (unsigned)cp.size()), kVecBlock, 0, ws>>>(d_pairs);
+        STG_CUDA_TRY(cudaGetLastError());
+        std::fill(h_noupd.begin(), h_noupd.end(), 0);
+        STG_CUDA_TRY(cudaMemcpyAsync(noupd, h_noupd.data(), sizeof(int) * npair, cudaMemcpyHostToDevice, ws));
+        for (const DArgs &a : p64f.oe) STG_CUDA_TRY(launch_dslash(kind_64, a, 0, ws));
+        for (const DArgs &a : p64f.eo) STG_CUDA_TRY(launch_dslash(kind_64, a, 2, ws));
+        k_verify<<<npair, 32, 0, ws>>>(d_v2, d_true_rr);
+        STG_CUDA_TRY(cudaGetLastError());
+        std::vector<double> trr_f64(npair);
+        STG_CUDA_TRY(cudaMemcpyAsync(trr_f64.data(), d_true_rr, sizeof(double) * npair, cudaMemcpyDeviceToHost, ws));
+        STG_CUDA_TRY(cudaStreamSynchronize(ws));
+        for (int q = 0; q < npair; ++q)
+            if (trr_f64[q] > s2[q].tol2_true && h_fin[q]) {
+                std::vector<SysScal> one(1);
+                STG_CUDA_TRY(cudaMemcpy(one.data(), d_s2 + q, sizeof(SysScal), cudaMemcpyDeviceToHost));
+                if (one[0].iters < prm->max_iter) *retry_f64 = true;  // converged in DS, not in FP64
+            }
+        if (*retry_f64) {
+            stamp("FP64 verification failed: repeating with FP64 reliable updates");
+            return STG_OK;
+        }
+        stamp("FP64 verification done");
     }
 
     // ---------------- outputs and statistics
@@ -874,7 +1075,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
                     cp[pidx] = ConvPair{v2[pidx].xhi, inst[k].x[r * ns + i], v2[pidx].Vh};
                 }
         STG_CUDA_TRY(cudaMemcpyAsync(d_pairs, cp.data(), sizeof(ConvPair) * npair, cudaMemcpyHostToDevice, ws));
-        k_unpack_pairs<<<vgrid2, kVecBlock, 0, ws>>>(d_pairs);
+        k_unpack_pairs<double><<<vgrid2, kVecBlock, 0, ws>>>(d_pairs);  // x_hi is FP64 here
         STG_CUDA_TRY(cudaGetLastError());
     }
     std::vector<SysScal> f1(nsys), f2(npair);
@@ -907,16 +1108,19 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
                 rel += std::max(0, rc[pidx] - 1);
                 ref = std::max(ref, f2[pidx].iters);
                 if (S && S->true_resid) S->true_resid[i] = res;
+                if (S && S->inner_resid) S->inner_resid[i] = bb > 0 ? std::sqrt(trr0[pidx] / bb) : 0.0;
                 if (S && S->shift_iters) S->shift_iters[i] = f1[s].shift_iters[i] ? f1[s].shift_iters[i] : f1[s].iters;
             }
             if (S) {
                 S->iters = f1[s].iters;
                 S->reliable_updates = rel;
                 S->refine_iters = ref;
+                S->fp64_fallback = mixed && !kDS ? 1 : 0;
             }
         }
     STG_CUDA_TRY(cudaEventRecord(ev, ws));
     STG_CUDA_TRY(cudaStreamWaitEvent(user_st, ev, 0));
+    stamp("outputs written");
     if (!conv) return set_error(STG_ERR_NOCONV, "stg_mscg_solve: a shift is above tol after max_iter");
     return STG_OK;
 }
@@ -981,8 +1185,13 @@ stg_status stg_mscg_solve_batched(int32_t ninst, const stg_instance *inst, const
     bool mixed = false;
     stg_status s = validate(ninst, inst, params, mixed);
     if (s != STG_OK) return s;
-    return mixed ? solve_impl<float>(ninst, inst, params, (cudaStream_t)stream)
-                 : solve_impl<double>(ninst, inst, params, (cudaStream_t)stream);
+    bool retry = false;
+    if (!mixed) return solve_impl<double, double>(ninst, inst, params, (cudaStream_t)stream, &retry);
+    // mixed: reliable updates in double-single, every result verified in FP64; if a shift passes
+    // in double-single but not in FP64 (a very ill-conditioned shift), redo with FP64 updates
+    s = solve_impl<float, dsf>(ninst, inst, params, (cudaStream_t)stream, &retry);
+    if (s != STG_OK || !retry) return s;
+    return solve_impl<float, double>(ninst, inst, params, (cudaStream_t)stream, &retry);
 }
 
 stg_status stg_mscg_solve(const stg_gauge *g_f64, const stg_gauge *g_inner, const stg_mscg_params *params,

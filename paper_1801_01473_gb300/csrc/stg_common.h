@@ -13,10 +13,13 @@
 namespace stg {
 
 // Link storage kinds (precision x compression); index of the dslash instantiation.
-enum LinkKind { kF64R18 = 0, kF64R12 = 1, kF32R18 = 2, kF32R12 = 3, kBF16R12 = 4, kF16R12 = 5 };
+enum LinkKind { kF64R18 = 0, kF64R12 = 1, kF32R18 = 2, kF32R12 = 3, kBF16R12 = 4, kF16R12 = 5, kDSR18 = 6, kDSR12 = 7 };
 
 int link_bytes(int kind);
 inline bool kind_is_f64(int kind) { return kind == kF64R18 || kind == kF64R12; }
+inline bool kind_is_ds(int kind) { return kind == kDSR18 || kind == kDSR12; }
+// bytes per site of the fields a gauge of this kind works on
+inline int kind_vec_bytes(int kind) { return kind_is_f64(kind) || kind_is_ds(kind) ? 48 : 24; }
 
 // Launchers, one per storage kind, implemented in dslash_f64.cu / dslash_f32.cu / dslash_h16.cu;
 // `bs` is the thread-block size (64, 128 or 256).
@@ -26,6 +29,8 @@ cudaError_t launch_dslash_f32r18(const DArgs &a, int mode, int bs, cudaStream_t 
 cudaError_t launch_dslash_f32r12(const DArgs &a, int mode, int bs, cudaStream_t st);
 cudaError_t launch_dslash_bf16r12(const DArgs &a, int mode, int bs, cudaStream_t st);
 cudaError_t launch_dslash_f16r12(const DArgs &a, int mode, int bs, cudaStream_t st);
+cudaError_t launch_dslash_dsr18(const DArgs &a, int mode, int bs, cudaStream_t st);
+cudaError_t launch_dslash_dsr12(const DArgs &a, int mode, int bs, cudaStream_t st);
 // Launches the D kernel for storage `kind` with the autotuned block size (stg_core.cu).
 cudaError_t launch_dslash(int kind, const DArgs &a, int mode, cudaStream_t st);
 cudaError_t launch_dslash_bs(int kind, const DArgs &a, int mode, int bs, cudaStream_t st);
@@ -36,6 +41,9 @@ cudaError_t launch_pack_links(int kind, const Geom &g, const void *canon, void *
 // F32 12-real copy of an F64 gauge (created on first use, owned by the F64 gauge): the operator
 // of the refinement iterations when the multi-shift phase runs on 16-bit links.
 stg_status f32_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge **out);
+// Double-single copy of an F64 gauge, same compression (created on first use, owned by the F64
+// gauge): the operator of the mixed solver's FP64-accurate residuals, run on the FP32 pipes.
+stg_status ds_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge **out);
 
 // Error reporting (thread-local message read by stg_last_error).
 stg_status set_error(stg_status s, const std::string &msg);
@@ -59,6 +67,7 @@ struct stg_gauge {
     double *scratch;       // per-block partial sums of stg_normal_op's reduction
     size_t scratch_count;  // doubles in scratch
     mutable stg_gauge *f32_copy;  // lazily created F32 12-real companion (F64 gauges only)
+    mutable stg_gauge *ds_copy;   // lazily created double-single companion (F64 gauges only)
 };
 
 #define STG_CUDA_TRY(call)                                       \

@@ -36,6 +36,8 @@ int link_bytes(int kind)
     case kF32R12: return LinkF32R12::kBytes;
     case kBF16R12: return Link16R12<__nv_bfloat16>::kBytes;
     case kF16R12: return Link16R12<__half>::kBytes;
+    case kDSR18: return LinkDSR18::kBytes;
+    case kDSR12: return LinkDSR12::kBytes;
     }
     return 0;
 }
@@ -49,8 +51,19 @@ cudaError_t launch_dslash_bs(int kind, const DArgs &a, int mode, int bs, cudaStr
     case kF32R12: return launch_dslash_f32r12(a, mode, bs, st);
     case kBF16R12: return launch_dslash_bf16r12(a, mode, bs, st);
     case kF16R12: return launch_dslash_f16r12(a, mode, bs, st);
+    case kDSR18: return launch_dslash_dsr18(a, mode, bs, st);
+    case kDSR12: return launch_dslash_dsr12(a, mode, bs, st);
     }
     return cudaErrorInvalidValue;
+}
+
+bool pdl_enabled()
+{
+    static const bool on = [] {
+        const char *e = getenv("STG_PDL");
+        return !(e && e[0] == '0');
+    }();
+    return on;
 }
 
 // Block-size autotuner of the D kernel.  Keyed by (device, storage kind, epilogue, rhs
@@ -159,6 +172,8 @@ cudaError_t launch_pack_links(int kind, const Geom &g, const void *canon, void *
     case kF32R12: return pack_links_t<LinkF32R12>(g, canon, links, st);
     case kBF16R12: return pack_links_t<Link16R12<__nv_bfloat16>>(g, canon, links, st);
     case kF16R12: return pack_links_t<Link16R12<__half>>(g, canon, links, st);
+    case kDSR18: return pack_links_t<LinkDSR18>(g, canon, links, st);
+    case kDSR12: return pack_links_t<LinkDSR12>(g, canon, links, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -178,7 +193,56 @@ __global__ void k_links_to_f32r12(Geom g, const void *__restrict__ src, void *__
     LinkF32R12::pack(static_cast<char *>(dst) + (size_t)blk * Vh * LinkF32R12::kBytes, Vh, h, m);
 }
 
+// internal F64 links -> internal double-single links of the same compression
+template <typename SrcT, typename DstT>
+__global__ void k_links_to_ds(Geom g, const void *__restrict__ src, void *__restrict__ dst)
+{
+    const int Vh = g.Vh;
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= 8LL * Vh) return;
+    const int blk = (int)(tid / Vh), h = (int)(tid - (long long)blk * Vh);
+    const double2 *p = reinterpret_cast<const double2 *>(static_cast<const char *>(src) + (size_t)blk * Vh * SrcT::kBytes);
+    double2 m[9];
+    for (int k = 0; k < DstT::kBytes / 16; ++k) m[k] = p[(size_t)k * Vh + h];
+    DstT::pack(static_cast<char *>(dst) + (size_t)blk * Vh * DstT::kBytes, Vh, h, m);
+}
+
 static std::mutex g_companion_mu;
+
+stg_status ds_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge **out)
+{
+    std::lock_guard<std::mutex> lk(g_companion_mu);
+    if (!g64->ds_copy) {
+        stg_gauge *g = new (std::nothrow) stg_gauge;
+        if (!g) return set_error(STG_ERR_OOM, "ds_companion: host allocation");
+        *g = *g64;
+        g->kind = g64->kind == kF64R18 ? kDSR18 : kDSR12;
+        g->bytes = (size_t)4 * g64->lat->V * link_bytes(g->kind);
+        g->scratch = nullptr;
+        g->links = nullptr;
+        g->f32_copy = nullptr;
+        g->ds_copy = nullptr;
+        cudaError_t e = cudaMalloc(&g->links, g->bytes);
+        if (e == cudaSuccess) e = cudaMalloc(&g->scratch, g->scratch_count * sizeof(double));
+        if (e == cudaSuccess) {
+            long long n = 8LL * g->g.Vh;
+            if (g64->kind == kF64R18)
+                k_links_to_ds<LinkF64R18, LinkDSR18><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->g, g64->links, g->links);
+            else
+                k_links_to_ds<LinkF64R12, LinkDSR12><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->g, g64->links, g->links);
+            e = cudaGetLastError();
+        }
+        if (e != cudaSuccess) {
+            cudaFree(g->links);
+            cudaFree(g->scratch);
+            delete g;
+            return cuda_error(e, "ds_companion");
+        }
+        g64->ds_copy = g;
+    }
+    *out = g64->ds_copy;
+    return STG_OK;
+}
 
 stg_status f32_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge **out)
 {
@@ -194,6 +258,7 @@ stg_status f32_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge 
         g->scratch = nullptr;
         g->links = nullptr;
         g->f32_copy = nullptr;
+        g->ds_copy = nullptr;
         cudaError_t e = cudaMalloc(&g->links, g->bytes);
         if (e == cudaSuccess) e = cudaMalloc(&g->scratch, g->scratch_count * sizeof(double));
         if (e == cudaSuccess) {
@@ -322,6 +387,7 @@ stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, 
     case STG_F32: kind = recon == STG_RECON18 ? kF32R18 : kF32R12; break;
     case STG_BF16: kind = recon == STG_RECON12 ? kBF16R12 : -1; break;
     case STG_F16: kind = recon == STG_RECON12 ? kF16R12 : -1; break;
+    case STG_DS: kind = recon == STG_RECON18 ? kDSR18 : kDSR12; break;
     default: break;
     }
     if (kind < 0) return set_error(STG_ERR_ARG, "stg_gauge_create: unsupported precision/compression pair");
@@ -337,6 +403,7 @@ stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, 
     g->links = nullptr;
     g->scratch = nullptr;
     g->f32_copy = nullptr;
+    g->ds_copy = nullptr;
     g->scratch_count = (size_t)dslash_partials(lat->g.Vh);
     cudaError_t e = cudaMalloc(&g->links, g->bytes);
     if (e == cudaSuccess) e = cudaMalloc(&g->scratch, g->scratch_count * sizeof(double));
@@ -356,6 +423,7 @@ void stg_gauge_destroy(stg_gauge *g)
 {
     if (!g) return;
     if (g->f32_copy) stg_gauge_destroy(g->f32_copy);
+    if (g->ds_copy) stg_gauge_destroy(g->ds_copy);
     cudaFree(g->links);
     cudaFree(g->scratch);
     delete g;
@@ -367,6 +435,7 @@ size_t stg_field_bytes(const stg_lattice *lat, stg_prec vec_prec)
 {
     if (!lat) return 0;
     if (vec_prec == STG_F64) return (size_t)lat->g.Vh * Field<double>::kBytesPerSite;
+    if (vec_prec == STG_DS) return (size_t)lat->g.Vh * Field<dsf>::kBytesPerSite;
     if (vec_prec == STG_F32) return (size_t)lat->g.Vh * Field<float>::kBytesPerSite;
     return 0;
 }
@@ -384,8 +453,11 @@ stg_status stg_field_pack(const stg_lattice *lat, stg_prec vec_prec, const void 
     else if (vec_prec == STG_F32)
         k_pack_field<float><<<(Vh + bs - 1) / bs, bs, 0, (cudaStream_t)stream>>>(Vh, (const double2 *)canon_c128_dev,
                                                                                  internal_dev);
+    else if (vec_prec == STG_DS)
+        k_pack_field<dsf><<<(Vh + bs - 1) / bs, bs, 0, (cudaStream_t)stream>>>(Vh, (const double2 *)canon_c128_dev,
+                                                                               internal_dev);
     else
-        return set_error(STG_ERR_ARG, "stg_field_pack: vector precision must be F64 or F32");
+        return set_error(STG_ERR_ARG, "stg_field_pack: vector precision must be F64, DS or F32");
     STG_CUDA_TRY(cudaGetLastError());
     return STG_OK;
 }
@@ -403,8 +475,11 @@ stg_status stg_field_unpack(const stg_lattice *lat, stg_prec vec_prec, const voi
     else if (vec_prec == STG_F32)
         k_unpack_field<float><<<(Vh + bs - 1) / bs, bs, 0, (cudaStream_t)stream>>>(Vh, internal_dev,
                                                                                    (double2 *)canon_c128_dev);
+    else if (vec_prec == STG_DS)
+        k_unpack_field<dsf><<<(Vh + bs - 1) / bs, bs, 0, (cudaStream_t)stream>>>(Vh, internal_dev,
+                                                                                 (double2 *)canon_c128_dev);
     else
-        return set_error(STG_ERR_ARG, "stg_field_unpack: vector precision must be F64 or F32");
+        return set_error(STG_ERR_ARG, "stg_field_unpack: vector precision must be F64, DS or F32");
     STG_CUDA_TRY(cudaGetLastError());
     return STG_OK;
 }
@@ -415,7 +490,7 @@ stg_status stg_dslash_multi(const stg_gauge *g, int32_t out_parity, int32_t nrhs
     if (!g || !out_dev || !in_dev) return set_error(STG_ERR_ARG, "stg_dslash: null pointer");
     if (out_parity != 0 && out_parity != 1) return set_error(STG_ERR_ARG, "stg_dslash: out_parity must be 0 or 1");
     if (nrhs < 1 || nrhs > 64) return set_error(STG_ERR_ARG, "stg_dslash: nrhs must be in 1..64");
-    size_t fb = (size_t)g->g.Vh * (kind_is_f64(g->kind) ? 48 : 24);
+    size_t fb = (size_t)g->g.Vh * kind_vec_bytes(g->kind);
     if (nrhs > 1 && (stride_bytes < fb || (stride_bytes & 15)))
         return set_error(STG_ERR_ARG, "stg_dslash: stride must be >= the field size and a multiple of 16 bytes");
     if (!aligned16(out_dev) || !aligned16(in_dev)) return set_error(STG_ERR_ARG, "stg_dslash: pointers must be 16-byte aligned");

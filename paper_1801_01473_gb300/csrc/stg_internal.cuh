@@ -74,6 +74,89 @@ __device__ __forceinline__ void reconstruct_row3(cx<R> U[3][3])
     U[2][2] = cx<R>{a.re - b.re, -(a.im - b.im)};
 }
 
+// ------------------------------------------------------------------ double-single numbers
+// A value hi + lo held in two floats with |lo| <= ulp(hi)/2: a 48-bit significand (relative
+// rounding ~2^-47) computed on the FP32 pipes, which GB300 runs ~64x faster than FP64.
+// Sums use Knuth's TwoSum and Dekker's Fast2Sum, products the FMA form of Dekker's
+// TwoProduct (Dekker 1971, "A floating-point technique for extending the available
+// precision"; Knuth, TAOCP vol. 2, 4.2.2).  The _rn intrinsics keep the compiler from
+// contracting or reassociating the error-free transformations.
+struct dsf {
+    float hi, lo;
+    dsf() = default;
+    __device__ __forceinline__ constexpr dsf(float h, float l) : hi(h), lo(l) {}
+    __device__ __forceinline__ dsf(int i) : hi((float)i), lo(0.f) {}
+    __device__ __forceinline__ explicit dsf(float f) : hi(f), lo(0.f) {}
+    __device__ __forceinline__ explicit dsf(double d)
+    {
+        hi = __double2float_rn(d);
+        lo = __double2float_rn(d - (double)hi);
+    }
+    __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
+    __device__ __forceinline__ explicit operator float() const { return __fadd_rn(hi, lo); }
+};
+
+__device__ __forceinline__ dsf ds_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    const float bb = __fsub_rn(s, a);
+    const float e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
+    return dsf(s, e);
+}
+
+// requires |a| >= |b| (or a == 0)
+__device__ __forceinline__ dsf ds_fast_two_sum(float a, float b)
+{
+    const float s = __fadd_rn(a, b);
+    return dsf(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+
+__device__ __forceinline__ dsf operator-(const dsf &a) { return dsf(-a.hi, -a.lo); }
+
+__device__ __forceinline__ dsf operator+(const dsf &a, const dsf &b)
+{
+    const dsf s = ds_two_sum(a.hi, b.hi);
+    return ds_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(a.lo, b.lo)));
+}
+
+__device__ __forceinline__ dsf operator-(const dsf &a, const dsf &b) { return a + (-b); }
+
+__device__ __forceinline__ dsf operator*(const dsf &a, const dsf &b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    return ds_fast_two_sum(p, e);
+}
+
+// a * b + c  (the float/double overloads of fma stay visible inside this namespace)
+using ::fma;
+__device__ __forceinline__ dsf fma(const dsf &a, const dsf &b, const dsf &c)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const dsf s = ds_two_sum(p, c.hi);
+    return ds_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
+}
+
+// FP64 accumulator of products of two values of type R: plain double for float/double,
+// a double-single running sum for dsf (one conversion at the end instead of one per term).
+template <typename R>
+struct ProdSum {
+    double s = 0.0;
+    __device__ __forceinline__ void add(R a, R b) { s += (double)a * (double)b; }
+    __device__ __forceinline__ double value() const { return s; }
+};
+template <>
+struct ProdSum<dsf> {
+    dsf s = dsf(0.f, 0.f);
+    __device__ __forceinline__ void add(const dsf &a, const dsf &b) { s = fma(a, b, s); }
+    __device__ __forceinline__ double value() const { return (double)s; }
+};
+
 // ------------------------------------------------------------------ geometry
 
 struct Geom {
@@ -200,6 +283,36 @@ struct Field<float> {
         v[0] = cx<float>{u.x, u.y};
         v[1] = cx<float>{u.z, u.w};
         v[2] = cx<float>{w.x, w.y};
+    }
+};
+
+// double-single field: 3 arrays of Vh float4 (re.hi, re.lo, im.hi, im.lo), 48 B/site
+template <>
+struct Field<dsf> {
+    static constexpr int kBytesPerSite = 48;
+    __device__ __forceinline__ static void load(const void *base, int Vh, int h, cx<dsf> v[3])
+    {
+        const float4 *p = static_cast<const float4 *>(base);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float4 d = __ldg(p + (size_t)c * Vh + h);
+            v[c] = cx<dsf>{dsf(d.x, d.y), dsf(d.z, d.w)};
+        }
+    }
+    __device__ __forceinline__ static void store(void *base, int Vh, int h, const cx<dsf> v[3])
+    {
+        float4 *p = static_cast<float4 *>(base);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[(size_t)c * Vh + h] = make_float4(v[c].re.hi, v[c].re.lo, v[c].im.hi, v[c].im.lo);
+    }
+    __device__ __forceinline__ static void load_rw(const void *base, int Vh, int h, cx<dsf> v[3])
+    {
+        const float4 *p = static_cast<const float4 *>(base);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            float4 d = p[(size_t)c * Vh + h];
+            v[c] = cx<dsf>{dsf(d.x, d.y), dsf(d.z, d.w)};
+        }
     }
 };
 
@@ -338,11 +451,49 @@ struct Link16R12 {
     }
 };
 
+// double-single links: one float4 (re.hi, re.lo, im.hi, im.lo) per complex entry
+template <int NCHUNK>
+struct LinkDS {
+    using R = dsf;
+    static constexpr int kBytes = 16 * NCHUNK;
+    __device__ __forceinline__ static void load(const void *blk, int Vh, int h, cx<dsf> U[3][3])
+    {
+        const float4 *p = static_cast<const float4 *>(blk);
+#pragma unroll
+        for (int k = 0; k < NCHUNK; ++k) {
+            float4 d = __ldg(p + (size_t)k * Vh + h);
+            U[k / 3][k % 3] = cx<dsf>{dsf(d.x, d.y), dsf(d.z, d.w)};
+        }
+        if (NCHUNK == 6) reconstruct_row3(U);
+    }
+    __device__ __forceinline__ static void pack(void *blk, int Vh, int h, const double2 *m)
+    {
+        float4 *p = static_cast<float4 *>(blk);
+        for (int k = 0; k < NCHUNK; ++k) {
+            const dsf re(m[k].x), im(m[k].y);
+            p[(size_t)k * Vh + h] = make_float4(re.hi, re.lo, im.hi, im.lo);
+        }
+    }
+};
+using LinkDSR18 = LinkDS<9>;
+using LinkDSR12 = LinkDS<6>;
+
 // Base of the (mu, parity) block of an internal link array.
 template <typename LinkT>
 __device__ __forceinline__ const void *link_block(const void *links, int Vh, int mu, int par)
 {
     return static_cast<const char *>(links) + (size_t)(mu * 2 + par) * Vh * LinkT::kBytes;
+}
+
+// ------------------------------------------------------------------ programmatic dependent launch
+// Kernels launched with launch_pdl may start while the previous kernel of the stream is still
+// draining: each block first lets the next kernel launch, then waits until every earlier grid of
+// the stream has completed and its writes are visible, before touching global memory.  Without
+// the launch attribute both instructions are no-ops.
+__device__ __forceinline__ void pdl_enter()
+{
+    asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+    asm volatile("griddepcontrol.wait;" ::: "memory");
 }
 
 // ------------------------------------------------------------------ reductions

@@ -13,10 +13,10 @@ LIB_PATH = os.path.join(HERE, "libstg.so")
 
 # enums of stg.h
 STG_OK, STG_ERR_ARG, STG_ERR_SHAPE, STG_ERR_CUDA, STG_ERR_NOCONV, STG_ERR_TIMEOUT, STG_ERR_OOM = 0, -1, -2, -3, -4, -5, -6
-STG_F64, STG_F32, STG_BF16, STG_F16 = 0, 1, 2, 3
+STG_F64, STG_F32, STG_BF16, STG_F16, STG_DS = 0, 1, 2, 3, 4
 STG_RECON18, STG_RECON12 = 18, 12
 
-PREC = {"f64": STG_F64, "f32": STG_F32, "bf16": STG_BF16, "f16": STG_F16}
+PREC = {"f64": STG_F64, "f32": STG_F32, "bf16": STG_BF16, "f16": STG_F16, "ds": STG_DS}
 
 # every symbol include/stg.h declares
 EXPORTS = [
@@ -38,7 +38,8 @@ class MscgParams(ctypes.Structure):
 
 class MscgStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("reliable_updates", ctypes.c_int32), ("refine_iters", ctypes.c_int32),
-                ("true_resid", ctypes.POINTER(ctypes.c_double)), ("shift_iters", ctypes.POINTER(ctypes.c_int32))]
+                ("true_resid", ctypes.POINTER(ctypes.c_double)), ("shift_iters", ctypes.POINTER(ctypes.c_int32)),
+                ("inner_resid", ctypes.POINTER(ctypes.c_double)), ("fp64_fallback", ctypes.c_int32)]
 
 
 class Instance(ctypes.Structure):

@@ -50,6 +50,7 @@ def test_lattice_geometry_and_sizes(L):
     # FP64 pseudofermion: 3 double complex = 48 bytes per site (Sec. 3.1)
     assert L.stg_field_bytes(h, 0) == 192 * sizes["fermion_bytes_per_site_fp64"]["value"]
     assert L.stg_field_bytes(h, 1) == 192 * 24
+    assert L.stg_field_bytes(h, 4) == 192 * 48  # double-single: two floats per real
     assert L.stg_field_bytes(h, 2) == 0
     L.stg_lattice_destroy(h)
 

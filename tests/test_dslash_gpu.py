@@ -2,6 +2,7 @@
 
 Tolerances (relative max-norm error over the output vector):
   F64 links, 18 or 12 real    1e-12  (spec bar for FP64 paths)
+  DS (FP32 pairs), 18 or 12   1e-12  (48-bit significand; measured well below this)
   F32 links                   2e-6   (FP32 rounding of links, vectors and 8-term sums)
   F16 links                   4e-3   (11-bit mantissa of the stored link rows)
   BF16 links                  3e-2   (8-bit mantissa of the stored link rows)
@@ -15,8 +16,8 @@ import synthetic as S
 torch = pytest.importorskip("torch")
 pytestmark = pytest.mark.gpu
 
-TOL = {("f64", 18): 1e-12, ("f64", 12): 1e-12, ("f32", 18): 2e-6, ("f32", 12): 2e-6,
-       ("f16", 12): 4e-3, ("bf16", 12): 3e-2}
+TOL = {("f64", 18): 1e-12, ("f64", 12): 1e-12, ("ds", 18): 1e-12, ("ds", 12): 1e-12, ("f32", 18): 2e-6,
+       ("f32", 12): 2e-6, ("f16", 12): 4e-3, ("bf16", 12): 3e-2}
 VARIANTS = list(TOL)
 # several tiles of 128 sites plus ragged tails; odd-shaped extents
 LATTICES = [(4, 4, 4, 4), (6, 4, 2, 8), (2, 6, 4, 10), (8, 8, 8, 8), (12, 10, 6, 4)]
@@ -79,7 +80,7 @@ def test_normal_op_and_fused_dot(variant):
     assert abs(pq.item() - pq_ref) <= 4 * TOL[variant] * abs(pq_ref)
 
 
-@pytest.mark.parametrize("variant", [("f64", 18), ("f32", 12), ("bf16", 12)])
+@pytest.mark.parametrize("variant", [("f64", 18), ("ds", 12), ("f32", 12), ("bf16", 12)])
 @pytest.mark.parametrize("nrhs", [1, 3, 8, 11])
 def test_multi_rhs_matches_single(variant, nrhs):
     """Shared link loads over nrhs right-hand sides give bitwise the single-rhs results."""
@@ -107,6 +108,8 @@ def test_pack_unpack_roundtrip():
     assert torch.equal(p.unpack(lat, p.pack(lat, psi, "f64")), psi)
     back = p.unpack(lat, p.pack(lat, psi, "f32"))
     assert torch.equal(back, psi.to(torch.complex64).to(torch.complex128))
+    back = p.unpack(lat, p.pack(lat, psi, "ds"))  # hi + lo keeps 48 of the 53 significand bits
+    assert ((back - psi).abs() <= 2.0 ** -47 * psi.abs()).all()
 
 
 def test_full_size_32x32x32x32_sampled():
@@ -120,7 +123,7 @@ def test_full_size_32x32x32x32_sampled():
     ref = oracle.dslash(dims, u, 0, psi)
     lat = p.Lattice(dims)
     ut = torch.from_numpy(u).cuda()
-    for prec, recon in [("f32", 12), ("f64", 18), ("bf16", 12)]:
+    for prec, recon in [("f32", 12), ("f64", 18), ("ds", 18), ("bf16", 12)]:
         g = p.Gauge(lat, ut, prec, recon)
         got = p.dslash_eo(g, torch.from_numpy(psi).cuda()).cpu().numpy()
         assert rel(got, ref) <= TOL[(prec, recon)], (prec, recon, rel(got, ref))

@@ -188,3 +188,20 @@ def test_batched_uneven_matches_separate_solves():
             assert oracle.true_residual(dims, u, cfg["mass"], shifts[i], b1, x[1, i].cpu().numpy()) <= cfg["tol"]
             rel = (torch.linalg.vector_norm(x[1, i] - xs[i]) / torch.linalg.vector_norm(xs[i])).item()
             assert rel <= 1e-7
+
+
+def test_ill_conditioned_mixed_verified_in_fp64():
+    """A shift whose condition number (~1.6e5: Haar links, m = 0.01, sigma = 0) puts the
+    double-single residual error near tol: the mixed solve must still return every shift with an
+    FP64 true residual <= tol (re-checked by the oracle), falling back to FP64 reliable updates
+    when the FP64 verification fails."""
+    p = stg()
+    dims = (4, 4, 4, 4)
+    u = S.gauge_links(dims, "haar", 1001)
+    b = S.gaussian_field(dims, 2001)
+    shifts = [0.0, 1e-3, 0.1]
+    _, g64, gi = gauges(p, dims, u, ("f32", 12))
+    x, st = p.mscg(g64, torch.from_numpy(b).cuda(), shifts, 0.01, tol=1e-10, g_inner=gi)
+    tr = oracle_true_resid(dims, u, 0.01, shifts, b, x.cpu().numpy())
+    assert np.all(tr <= 1e-10), (tr, st)
+    assert st["fp64_fallback"] in (0, 1)

@@ -71,6 +71,23 @@ def dist_env():
     return ws, rank, local
 
 
+def max_over_ranks(t: float) -> float:
+    """The largest of the ranks' timed-region durations (every rank gets it); t itself on one rank."""
+    import torch
+    import torch.distributed as dist
+    if not (dist.is_available() and dist.is_initialized()) or dist.get_world_size() == 1:
+        return t
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    tt = torch.tensor([t], dtype=torch.float64, device=dev)
+    dist.all_reduce(tt, op=dist.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def replica_throughput(bytes_per_rank: float, t_max: float, ws: int) -> float:
+    """Whole-job GB/s of `ws` independent replicas that each moved bytes_per_rank in at most t_max s."""
+    return ws * bytes_per_rank / t_max / 1e9
+
+
 def measured_peaks():
     path = os.path.join(ROOT, "MEASURED_PEAKS.json")
     if os.path.exists(path):
@@ -236,6 +253,7 @@ def time_mscg(torch, p, reps=3):
     res = {}
     for name, inner in [("fp32", ("f32", 12)), ("fp16", ("f16", 12)), ("bf16", ("bf16", 12)), ("fp64", None)]:
         gi = p.Gauge(lat, ut, inner[0], inner[1]) if inner else None
+        p.mscg(g64, b, shifts, cfg["mass"], tol=cfg["tol"], g_inner=gi, allow_noconv=True)  # autotune, untimed
         ts = []
         st = None
         for _ in range(reps):
@@ -263,6 +281,10 @@ def time_batched(torch, p, reps=2):
         bs = [torch.from_numpy(S.gaussian_field(dims, 2000 + 10 * cfg["k"] + 4 * li + r)).cuda()
               for r in range(cfg["nrhs"])]
         insts.append((p.Gauge(lat, ut, "f64", 18), p.Gauge(lat, ut, "f32", 12), bs))
+    # one untimed call of each shape first: the library autotunes launch shapes on first use
+    p.mscg_batched(insts, shifts, cfg["mass"], tol=cfg["tol"])
+    for g64, gi, bs in insts:
+        p.mscg(g64, bs[0], shifts, cfg["mass"], tol=cfg["tol"], g_inner=gi)
     tb = []
     for _ in range(reps):
         torch.cuda.synchronize()
@@ -351,13 +373,9 @@ def run_gpu(args):
     if ws > 1:
         torch.distributed.barrier()
     clocks = clk.stop()
-    t = e0.elapsed_time(e1) * 1e-3
-    if ws > 1:
-        tt = torch.tensor([t], dtype=torch.float64, device="cuda")
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t = float(tt.item())
+    t = max_over_ranks(e0.elapsed_time(e1) * 1e-3)
     launches = args.steps * B
-    value = ws * alg * launches / t / 1e9
+    value = replica_throughput(alg * launches, t, ws)
     per_launch = t / launches
     peak, peak_kind = measured_peaks()
     achieved = alg / per_launch / 1e9

@@ -39,6 +39,14 @@ namespace stg {
 
 constexpr int kVecBlock = 256;
 
+// Vector-kernel partial sums are per warp: one FP64 value per 32 consecutive sites, in site
+// order, written by lane 0 without block barriers (fixed-order, so still deterministic).
+__device__ __forceinline__ void warp_partial(double v, int h, int Vh, double *part)
+{
+    v = warp_sum(v);
+    if ((threadIdx.x & 31) == 0 && h < Vh) part[h >> 5] = v;
+}
+
 struct SysScal {
     double rr, alpha, alpha_old, beta_old, bnorm2, tol2, tol2_true, rr_last, delta2, coef, rr_best;
     double zeta[kMaxShifts], zeta_old[kMaxShifts], zeta_new[kMaxShifts], s[kMaxShifts];
@@ -52,8 +60,8 @@ struct SysVecs {
     void *x[kMaxShifts], *p[kMaxShifts];     // inner precision
     void *xhi, *rhi, *t64, *b64;             // phase 2: FP64 solution, residual, odd temp, source
     const double2 *bcanon;                   // canonical source (phase 1)
-    double *part_d, *part_v, *part_v2;       // partial sums (dslash blocks / vector blocks)
-    int Vh, nblk_d, nblk_v, pad;
+    double *part_d, *part_v, *part_v2;       // partial sums (64-site dslash chunks / 32-site warps)
+    int Vh, nblk_d, nblk_v, npart_v;  // nblk_v: kVecBlock-site blocks; npart_v: partials (one per 32 sites)
 };
 
 // ------------------------------------------------------------------ vector kernels
@@ -101,11 +109,8 @@ __global__ void __launch_bounds__(kVecBlock) k_p1_init(const SysVecs *__restrict
             Field<H>::store(V.b64, V.Vh, h, w);
         }
     }
-    __shared__ double sh[32];
-    double t = block_sum(pr, sh);
-    if (threadIdx.x == 0) V.part_v[blockIdx.x] = t;
-    t = block_sum(pb, sh);
-    if (threadIdx.x == 0) V.part_v2[blockIdx.x] = t;
+    warp_partial(pr, h, V.Vh, V.part_v);
+    warp_partial(pb, h, V.Vh, V.part_v2);
 }
 
 // Work list of the per-iteration vector kernels: the kVecBlock-site blocks of every system laid
@@ -131,7 +136,6 @@ __global__ void __launch_bounds__(kVecBlock) k_update_r(const SysScal *__restric
                                                          const WorkList w)
 {
     pdl_enter();
-    __shared__ double sh[32];
     int s = 0;
     for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
         s = advance_sys(w, s, b);
@@ -151,8 +155,7 @@ __global__ void __launch_bounds__(kVecBlock) k_update_r(const SysScal *__restric
             Field<R>::store(V.r, V.Vh, h, r);
             pr = norm2_site(r);
         }
-        double t = block_sum(pr, sh);
-        if (threadIdx.x == 0) V.part_v[lb] = t;
+        warp_partial(pr, h, V.Vh, V.part_v);
     }
 }
 
@@ -260,8 +263,8 @@ __global__ void k_p1_init_scal(SysScal *sc, const SysVecs *sv, int *done, double
 {
     SysScal &S = sc[blockIdx.x];
     const SysVecs &V = sv[blockIdx.x];
-    const double rr = warp_sum_strided(V.part_v, V.nblk_v);
-    const double bb = warp_sum_strided(V.part_v2, V.nblk_v);
+    const double rr = warp_sum_strided(V.part_v, V.npart_v);
+    const double bb = warp_sum_strided(V.part_v2, V.npart_v);
     for (int i = threadIdx.x; i < S.nshift; i += 32) {
         S.zeta[i] = S.zeta_old[i] = S.zeta_new[i] = 1.0;
         S.active[i] = bb > 0.0;
@@ -318,7 +321,7 @@ __global__ void __launch_bounds__(kScalBlock) k_beta(SysScal *sc, const SysVecs 
     if (!S.running) return;
     const SysVecs &V = sv[blockIdx.x];
     __shared__ double sh[33];
-    const double rr_new = block_sum_strided(V.part_v, V.nblk_v, sh);
+    const double rr_new = block_sum_strided(V.part_v, V.npart_v, sh);
     if (threadIdx.x >= 32) return;  // the per-shift recurrences run in warp 0
     const double beta = rr_new / S.rr;
     const int ns = S.nshift;
@@ -455,9 +458,7 @@ __global__ void __launch_bounds__(kVecBlock) k_rel_copy(const SysVecs *__restric
         }
         pr = norm2_site(r);
     }
-    __shared__ double sh[32];
-    double t = block_sum(pr, sh);
-    if (threadIdx.x == 0) V.part_v[blockIdx.x] = t;
+    warp_partial(pr, h, V.Vh, V.part_v);
 }
 
 __global__ void k_rel_scal(SysScal *sc, const SysVecs *sv, const int *noupd, const int *finished, int start)
@@ -465,7 +466,7 @@ __global__ void k_rel_scal(SysScal *sc, const SysVecs *sv, const int *noupd, con
     const int s = blockIdx.x;
     if (noupd[s] || finished[s]) return;
     SysScal &S = sc[s];
-    const double rr = warp_sum_strided(sv[s].part_v, sv[s].nblk_v);
+    const double rr = warp_sum_strided(sv[s].part_v, sv[s].npart_v);
     if (threadIdx.x == 0) {
         S.rr = rr;
         S.rr_last = rr;
@@ -682,7 +683,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     int nblkv_max = 0;
     for (int k = 0; k < ninst; ++k) {
         const int Vh = ii[k].g64->g.Vh;
-        const int nbd = dslash_partials(Vh), nbv = (Vh + kVecBlock - 1) / kVecBlock;
+        const int nbd = dslash_partials(Vh), nbv = (Vh + kVecBlock - 1) / kVecBlock, npv = (Vh + 31) / 32;
         nblkv_max = std::max(nblkv_max, nbv);
         const size_t fb = (size_t)Vh * vb, f64b = (size_t)Vh * 48;
         for (int r = 0; r < ii[k].nrhs; ++r) {
@@ -691,6 +692,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
             V.Vh = Vh;
             V.nblk_d = nbd;
             V.nblk_v = nbv;
+            V.npart_v = npv;
             V.r = mem.alloc(fb);
             V.q = mem.alloc(fb);
             V.t = mem.alloc(fb);
@@ -701,8 +703,8 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
             V.b64 = mem.alloc(f64b);
             V.bcanon = static_cast<const double2 *>(inst[k].b[r]);
             V.part_d = static_cast<double *>(mem.alloc(sizeof(double) * nbd));
-            V.part_v = static_cast<double *>(mem.alloc(sizeof(double) * nbv));
-            V.part_v2 = static_cast<double *>(mem.alloc(sizeof(double) * nbv));
+            V.part_v = static_cast<double *>(mem.alloc(sizeof(double) * npv));
+            V.part_v2 = static_cast<double *>(mem.alloc(sizeof(double) * npv));
             SysScal &S = s1[s];
             S.nshift = ns;
             S.i0 = i0;
@@ -715,13 +717,14 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
                 W.Vh = Vh;
                 W.nblk_d = nbd;
                 W.nblk_v = nbv;
+                W.npart_v = npv;
                 W.xhi = mem.alloc(f64b);
                 V.x[i] = W.xhi;
                 W.rhi = mem.alloc(f64b);
                 W.t64 = mem.alloc(f64b);
                 W.b64 = V.b64;
                 W.part_d = static_cast<double *>(mem.alloc(sizeof(double) * nbd));
-                W.part_v = static_cast<double *>(mem.alloc(sizeof(double) * nbv));
+                W.part_v = static_cast<double *>(mem.alloc(sizeof(double) * npv));
                 SysScal &P = s2[pidx];
                 P.nshift = 1;
                 P.i0 = 0;
@@ -865,15 +868,23 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         int dev = 0;
         if (cudaGetDevice(&dev) == cudaSuccess) cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     }
-    const int pgrid_max = nsm * (2048 / kVecBlock);  // one full wave of resident blocks
-    const dim3 pgrid1(std::min(wl1.total, pgrid_max)), pgrid2(std::min(wl2.total, pgrid_max));
+    // persistent grids: exactly the blocks that fit at once (one wave), per kernel
+    auto wave = [&](const void *kernel, int total) -> dim3 {
+        int per_sm = 0;
+        if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kernel, kVecBlock, 0) != cudaSuccess || per_sm < 1)
+            per_sm = 1;
+        return dim3(std::max(1, std::min(total, per_sm * nsm)));
+    };
+    const dim3 g_r1 = wave((const void *)k_update_r<R>, wl1.total), g_r2 = wave((const void *)k_update_r<R>, wl2.total);
+    const dim3 g_s1 = wave((const void *)k_update_shifts<R, H>, wl1.total);
+    const dim3 g_s2 = wave((const void *)k_update_shifts<R, R>, wl2.total);
+    cudaGetLastError();
 
     auto iterate = [&](int kind, const DPlan &pl, SysScal *dS, SysVecs *dV, int *dn, int *nr, int n, dim3 /*vg*/,
                        double *log, int log_rows) -> cudaError_t {
         cudaError_t e;
         const bool ph1 = &pl == &p1;
         const WorkList &wl = ph1 ? wl1 : wl2;
-        const dim3 vg = ph1 ? pgrid1 : pgrid2;
         for (const DArgs &a : pl.oe)
             if ((e = launch_dslash(kind, a, 0, ws)) != cudaSuccess) return e;
         for (const DArgs &a : pl.eo)
@@ -881,16 +892,17 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         if ((e = launch_pdl(k_alpha, dim3(n), dim3(kScalBlock), ws, dS, (const SysVecs *)dV, (const int *)dn)) !=
             cudaSuccess)
             return e;
-        if ((e = launch_pdl(k_update_r<R>, vg, dim3(kVecBlock), ws, (const SysScal *)dS, (const SysVecs *)dV, wl)) !=
+        if ((e = launch_pdl(k_update_r<R>, ph1 ? g_r1 : g_r2, dim3(kVecBlock), ws, (const SysScal *)dS,
+                            (const SysVecs *)dV, wl)) !=
             cudaSuccess)
             return e;
         if ((e = launch_pdl(k_beta, dim3(n), dim3(kScalBlock), ws, dS, (const SysVecs *)dV, dn, nr, log, log_rows)) !=
             cudaSuccess)
             return e;
         if (ph1)  // multi-shift phase: solutions in H
-            e = launch_pdl(k_update_shifts<R, H>, vg, dim3(kVecBlock), ws, (const SysScal *)dS, (const SysVecs *)dV, wl);
+            e = launch_pdl(k_update_shifts<R, H>, g_s1, dim3(kVecBlock), ws, (const SysScal *)dS, (const SysVecs *)dV, wl);
         else      // refinement: the correction y in R
-            e = launch_pdl(k_update_shifts<R, R>, vg, dim3(kVecBlock), ws, (const SysScal *)dS, (const SysVecs *)dV, wl);
+            e = launch_pdl(k_update_shifts<R, R>, g_s2, dim3(kVecBlock), ws, (const SysScal *)dS, (const SysVecs *)dV, wl);
         return e;
     };
 

@@ -220,7 +220,9 @@ stg_status stg_mscg_solve_batched(int32_t ninst, const stg_instance *inst, const
  *   kind 0: F = TA(U W) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6,  Z = U W   (dS/deps = tr(X F) along
  *           U -> exp(eps X) U, X in su(3)), or
  *   kind 1: W^dag = dS/dRe U + i dS/dIm U.
- * Accumulated in FP64.  x_c128_dev[nshift]: canonical complex128 even fields (device);
+ * y_i is computed with a double-single (FP32-pair, 48-bit significand) copy of the links, which
+ * the F64 gauge creates on first use and keeps; W and F are accumulated in FP64.
+ * x_c128_dev[nshift]: canonical complex128 even fields (device);
  * out_c128_dev: canonical complex128 [4][V][3][3] (device).  g_f64 must be an F64 gauge. */
 stg_status stg_fermion_force(const stg_gauge *g_f64, int32_t nshift, const double *residues,
                              const void *const *x_c128_dev, void *out_c128_dev, int32_t kind, void *stream);

@@ -170,13 +170,21 @@ def normal_op_noalloc_(gauge: Gauge, mass: float, shift: float, out: torch.Tenso
 
 # ------------------------------------------------------------------ operator (canonical layout)
 
+def _to_host(t: torch.Tensor) -> torch.Tensor:
+    """Device -> pinned host copy (torch caches pinned buffers), synchronised on the current stream."""
+    out = torch.empty(t.shape, dtype=t.dtype, pin_memory=True)
+    out.copy_(t, non_blocking=True)
+    torch.cuda.current_stream().synchronize()
+    return out
+
+
 def _canon_apply(gauge: Gauge, canon: torch.Tensor, fn) -> torch.Tensor:
     host = not canon.is_cuda
     lat = gauge.lattice
     x = pack(lat, canon, gauge.vec_prec)
     y = fn(x)
     out = unpack(lat, y)
-    return out.cpu() if host else out
+    return _to_host(out) if host else out
 
 
 def dslash_eo(gauge: Gauge, psi_odd: torch.Tensor) -> torch.Tensor:
@@ -241,7 +249,7 @@ def mscg(g_f64: Gauge, b: torch.Tensor, shifts, mass: float, tol: float = 1e-10,
     if log_rows > 0:
         import numpy as np
         stats["scalar_log"] = np.array(log[:]).reshape(log_rows, 2 + ns)[:min(log_rows, st.iters)]
-    return (x.cpu() if host else x), stats
+    return (_to_host(x) if host else x), stats
 
 
 def mscg_batched(instances, shifts, mass: float, tol: float = 1e-10, max_iter: int = 20000, inner_tol: float = 0.0,

@@ -77,7 +77,43 @@ std::mutex g_tune_mu;
 std::map<std::tuple<int, int, int, int, int>, int> g_tuned;
 }  // namespace
 
+static cudaError_t launch_dslash_tuned(int kind, const DArgs &a, int mode, cudaStream_t st);
+
+// Double-single D is bound by the FP32 pipes, not by link traffic: several right-hand sides per
+// thread only cost registers and occupancy (measured: 4 rhs per thread run at half the per-rhs
+// speed of 1).  Its multi-rhs launches are therefore split into one-rhs groups.
 cudaError_t launch_dslash(int kind, const DArgs &a, int mode, cudaStream_t st)
+{
+    int maxv, maxr;
+    dslash_extent(a, maxv, maxr);
+    if (!kind_is_ds(kind) || maxr <= 1) return launch_dslash_tuned(kind, a, mode, st);
+    DArgs b;
+    memset(&b, 0, sizeof(b));
+    b.out_par = a.out_par;
+    for (int k = 0; k < a.ngroups; ++k) {
+        const DGroup &G = a.grp[k];
+        for (int j = 0; j < G.nrhs; ++j) {
+            DGroup &H = b.grp[b.ngroups++];
+            H = G;
+            H.nrhs = 1;
+            H.in[0] = G.in[j];
+            H.out[0] = G.out[j];
+            H.epi_p[0] = G.epi_p[j];
+            H.epi_b[0] = G.epi_b[j];
+            H.coef[0] = G.coef[j];
+            H.partial[0] = G.partial[j];
+            H.skip[0] = G.skip[j];
+            if (b.ngroups == kMaxGroups) {
+                cudaError_t e = launch_dslash_tuned(kind, b, mode, st);
+                if (e != cudaSuccess) return e;
+                b.ngroups = 0;
+            }
+        }
+    }
+    return b.ngroups ? launch_dslash_tuned(kind, b, mode, st) : cudaSuccess;
+}
+
+static cudaError_t launch_dslash_tuned(int kind, const DArgs &a, int mode, cudaStream_t st)
 {
     int maxv, maxr;
     dslash_extent(a, maxv, maxr);

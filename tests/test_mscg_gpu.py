@@ -205,3 +205,40 @@ def test_ill_conditioned_mixed_verified_in_fp64():
     tr = oracle_true_resid(dims, u, 0.01, shifts, b, x.cpu().numpy())
     assert np.all(tr <= 1e-10), (tr, st)
     assert st["fp64_fallback"] in (0, 1)
+
+
+@pytest.mark.parametrize("inner", [None, ("f32", 12)])
+def test_many_rhs_and_max_shifts(inner):
+    """Limits of the batch: 10 sources on one lattice (two link-sharing groups of the multi-shift
+    phase) and the maximum of 32 shifts, on a ragged lattice; every system checked by the oracle."""
+    p = stg()
+    dims = (6, 4, 4, 8)
+    u = S.gauge_links(dims, "expih", 91)
+    shifts = list(S.log_poles(1e-4, 5.0, 32))
+    lat, g64, gi = gauges(p, dims, u, inner)
+    bs = [torch.from_numpy(S.gaussian_field(dims, 920 + r)).cuda() for r in range(10)]
+    (x, stats), = p.mscg_batched([(g64, gi, bs)], shifts, 0.05, tol=1e-10)
+    assert x.shape == (10, 32, lat.Vh, 3)
+    for r in (0, 9):
+        b = bs[r].cpu().numpy()
+        tr = oracle_true_resid(dims, u, 0.05, shifts, b, x[r].cpu().numpy())
+        assert np.all(tr <= 1e-10), (r, tr.max())
+        assert max(stats[r]["true_resid"]) <= 1e-10
+
+
+def test_batched_fp64_matches_single():
+    """Pure-FP64 batch of two lattices: each system's solution equals its single solve bitwise
+    (the per-system arithmetic and reduction order do not depend on the batch)."""
+    p = stg()
+    shifts = [1e-3, 0.05, 1.0]
+    insts, singles = [], []
+    for li, dims in enumerate([(4, 4, 4, 4), (6, 4, 2, 8)]):
+        u = S.gauge_links(dims, "haar", 95 + li)
+        _, g64, _ = gauges(p, dims, u, None)
+        bs = [torch.from_numpy(S.gaussian_field(dims, 960 + 2 * li + r)).cuda() for r in range(2)]
+        insts.append((g64, None, bs))
+        singles.append([p.mscg(g64, b, shifts, 0.1, tol=1e-11)[0] for b in bs])
+    res = p.mscg_batched(insts, shifts, 0.1, tol=1e-11)
+    for (x, _), ref in zip(res, singles):
+        for r in range(2):
+            assert torch.equal(x[r], ref[r])

@@ -111,3 +111,16 @@ def expm_su3(x: np.ndarray) -> np.ndarray:
     """exp of an anti-Hermitian 3x3 via the Hermitian eigendecomposition of -iX."""
     w, v = np.linalg.eigh(-1j * x)
     return (v * np.exp(1j * w)[None, :]) @ v.conj().T
+
+
+def plaquette_sum(dims, links: np.ndarray) -> float:
+    """sum over x and mu < nu of Re tr U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag."""
+    total = 0.0
+    for mu in range(4):
+        fm = shift_index(dims, mu, +1)
+        for nu in range(mu + 1, 4):
+            fn = shift_index(dims, nu, +1)
+            for s in range(len(fm)):
+                p = links[mu][s] @ links[nu][fm[s]] @ links[mu][fn[s]].conj().T @ links[nu][s].conj().T
+                total += np.trace(p).real
+    return total

@@ -329,6 +329,44 @@ def time_force(torch, p):
             "note": "D_oe on the 12 solutions + per-link gather, FP64"}
 
 
+# Algorithmic FP64 flops per link of one stout step (complex 3x3 product = 27 complex
+# multiply-adds = 216 flops): forward = 12 staple products + C U^dag + Q^2 + exp(iQ) U = 15
+# products; the chain rule = the forward's 14 before the exp, E^dag G', G' U^dag, M Q + Q M,
+# G_Omega^dag C, G_Omega U (6 more) + the 18 two-product staple terms (36).
+STOUT_FWD_FLOPS = 15 * 216
+STOUT_BWD_FLOPS = (14 + 6 + 36) * 216
+
+
+def time_stout(torch, p):
+    cfg = S.CONFIGS["force_48x48x48x48"]
+    dims = cfg["dims"]
+    lat = p.Lattice(dims)
+    ut = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
+    rho, nstep = 0.15, 2
+    g = torch.Generator(device="cuda").manual_seed(3000 + cfg["k"])
+    z = torch.complex(torch.randn(ut.shape, dtype=torch.float64, device="cuda", generator=g),
+                      torch.randn(ut.shape, dtype=torch.float64, device="cuda", generator=g))
+    levels = p.stout_smear(lat, ut, rho, nstep)
+    f = p.stout_force(lat, ut, levels, rho, z, kind=1)
+    torch.cuda.synchronize()
+    e0, e1, e2 = events(torch) + (torch.cuda.Event(enable_timing=True),)
+    e0.record()
+    for _ in range(3):
+        levels = p.stout_smear(lat, ut, rho, nstep)
+    e1.record()
+    for _ in range(3):
+        f = p.stout_force(lat, ut, levels, rho, z, kind=1)
+    e2.record()
+    torch.cuda.synchronize()
+    t_s, t_f = e0.elapsed_time(e1) / 3, e1.elapsed_time(e2) / 3
+    links = 4 * lat.V * nstep
+    del f, levels, z, ut
+    return {"lattice": "48^4", "steps": nstep, "rho": rho, "smear_ms": round(t_s, 3), "force_ms": round(t_f, 3),
+            "smear_fp64_tflops": round(links * STOUT_FWD_FLOPS / t_s / 1e9, 3),
+            "force_fp64_tflops": round(links * STOUT_BWD_FLOPS / t_f / 1e9, 3),
+            "note": "FP64, canonical link layout; flops algorithmic (216 per complex 3x3 product)"}
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = dist_env()
@@ -409,6 +447,7 @@ def run_gpu(args):
         line["mscg"] = time_mscg(torch, p)
         line["batched"] = time_batched(torch, p)
         line["force"] = time_force(torch, p)
+        line["stout"] = time_stout(torch, p)
         line["cpu_baseline"] = cpu_baseline()
     if ws > 1:
         torch.distributed.barrier()

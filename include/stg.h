@@ -227,6 +227,39 @@ stg_status stg_mscg_solve_batched(int32_t ninst, const stg_instance *inst, const
 stg_status stg_fermion_force(const stg_gauge *g_f64, int32_t nshift, const double *residues,
                              const void *const *x_c128_dev, void *out_c128_dev, int32_t kind, void *stream);
 
+/* ---- stout smearing ----------------------------------------------------------------------------- */
+
+/* k-times stout-smeared links U^(k) from U^(0) (the Dirac operator's links, Sec. 2; the smearing
+ * step is Morningstar and Peardon's).  One step, per link (x, mu), all links in parallel:
+ *   C = rho sum_{nu != mu} [U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag + U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)]
+ *   i Q = TA(C U^dag),   U' = exp(i Q) U
+ * with periodic links in all four directions.  exp(i Q) = f0 + f1 Q + f2 Q^2, the f_j summed
+ * from the Taylor series of exp reduced by the Cayley-Hamilton identity Q^3 = c1 Q + c0
+ * (c0 = det Q, c1 = tr Q^2 / 2) to full FP64 accuracy.  FP64 throughout.
+ * links_c128_dev: canonical complex128 [4][V][3][3] U^(0) (device, read only);
+ * levels_c128_dev: nstep consecutive canonical arrays U^(1) .. U^(nstep) (device, written).
+ * 1 <= nstep <= 16, |rho| <= 0.5 (larger rho is refused: the series would cancel digits);
+ * no aliasing between the two buffers; both 16-byte aligned.  Async on `stream`. */
+stg_status stg_stout_smear(const stg_lattice *lat, int32_t nstep, double rho, const void *links_c128_dev,
+                           void *levels_c128_dev, void *stream);
+
+/* Force chain rule through the smearing (Sec. 3: the MD evolves U^(0) while the fermion action
+ * depends on U^(k)).  Given G_k = dS/dRe U^(k) + i dS/dIm U^(k) (e.g. stg_fermion_force kind 1
+ * evaluated on U^(k)), pulls it back one step at a time, per link, with G' the gradient of U':
+ *   M = G' U^dag,  G_Q = K1 Q + K0 Q^2 + conj(f1) M + conj(f2) (M Q + Q M),
+ *   K1 = sum_j Re(tr(M^dag Q^j) df_j/dc1),  K0 = sum_j Re(tr(M^dag Q^j) df_j/dc0),
+ *   G_Omega = TA(i G_Q),  G = exp(iQ)^dag G' + G_Omega^dag C + (staple terms of rho G_Omega U)
+ * where the staple terms collect, for every link, the product-rule terms of the six staples of
+ * the three other directions that contain it (a gather: no atomics, deterministic).
+ * links_c128_dev: U^(0); levels_c128_dev: the stg_stout_smear output (U^(1) .. U^(nstep-1) are
+ * read); grad_c128_dev: G_k; out_c128_dev: kind 1: G_0 = dS/dRe U^(0) + i dS/dIm U^(0),
+ * kind 0: F = TA(U^(0) G_0^dag) (dS/deps = tr(X F) along U^(0) -> exp(eps X) U^(0)).
+ * All canonical complex128 [4][V][3][3] device arrays; out must not alias the inputs.  Allocates
+ * 2 link-sized FP64 work arrays from the stream-ordered allocator.  Same limits as smearing. */
+stg_status stg_stout_force(const stg_lattice *lat, int32_t nstep, double rho, const void *links_c128_dev,
+                           const void *levels_c128_dev, const void *grad_c128_dev, void *out_c128_dev,
+                           int32_t kind, void *stream);
+
 #ifdef __cplusplus
 }
 #endif

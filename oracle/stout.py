@@ -152,3 +152,39 @@ def lie_force(links, grad):
     """F = TA(U G^dag): dS/deps = tr(X F) along U -> exp(eps X) U, X in su(3)."""
     u = np.asarray(links, dtype=np.complex128).reshape(4, -1, 3, 3)
     return ta(u @ _dag(np.asarray(grad).reshape(u.shape)))
+
+
+def _neighbour(dims, site: int, mu: int, step: int) -> int:
+    c = [site % dims[0], (site // dims[0]) % dims[1], (site // (dims[0] * dims[1])) % dims[2],
+         site // (dims[0] * dims[1] * dims[2])]
+    c[mu] = (c[mu] + step) % dims[mu]
+    return c[0] + dims[0] * (c[1] + dims[1] * (c[2] + dims[2] * c[3]))
+
+
+def smeared_link(dims, links, rho: float, nstep: int, mu: int, site: int, _memo=None) -> np.ndarray:
+    """U^(nstep)_mu(site) alone, from the links it depends on (for sampled checks on lattices
+    too large for the whole-lattice routines); same formulas as stout_step."""
+    memo = {} if _memo is None else _memo
+    key = (nstep, mu, site)
+    if key in memo:
+        return memo[key]
+    u = np.asarray(links).reshape(4, -1, 3, 3)
+    if nstep == 0:
+        return u[mu, site]
+
+    def lk(nu, s):
+        return smeared_link(dims, u, rho, nstep - 1, nu, s, memo)
+
+    c = np.zeros((3, 3), np.complex128)
+    for nu in range(4):
+        if nu == mu:
+            continue
+        xp_nu, xp_mu = _neighbour(dims, site, nu, 1), _neighbour(dims, site, mu, 1)
+        c += lk(nu, site) @ lk(mu, xp_nu) @ lk(nu, xp_mu).conj().T
+        xm = _neighbour(dims, site, nu, -1)
+        c += lk(nu, xm).conj().T @ lk(mu, xm) @ lk(nu, _neighbour(dims, xm, mu, 1))
+    u_prev = lk(mu, site)
+    q = -1j * ta(rho * c @ u_prev.conj().T)
+    out = _exp_i_hermitian(q) @ u_prev
+    memo[key] = out
+    return out

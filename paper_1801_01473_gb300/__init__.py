@@ -1,6 +1,7 @@
 """GB300-native staggered-fermion hot path (arXiv:1801.01473): the even/odd
 staggered Dirac operator D_eo / D_oe, the multi-shift CG solve of
-(m^2 - D_eo D_oe + sigma_i) x_i = b and the fermion force, as hand-written
+(m^2 - D_eo D_oe + sigma_i) x_i = b, the fermion force and the stout smearing of the
+links with its force chain rule, as hand-written
 CUDA kernels for sm_103a behind the C ABI of include/stg.h (libstg.so).
 
 This package is the thin Python binding over that library; torch provides
@@ -8,10 +9,11 @@ device memory and streams.  Build the library with
 ``python -m paper_1801_01473_gb300.build``.
 """
 from .api import (Gauge, Lattice, dslash_eo, dslash_eo_, dslash_multi_, dslash_oe, dslash_oe_, fermion_force,
-                  mscg, mscg_batched, normal_op, normal_op_, normal_op_noalloc_, pack, unpack)
-from .autograd import PseudofermionAction, pseudofermion_action
+                  mscg, mscg_batched, normal_op, normal_op_, normal_op_noalloc_, pack, stout_force, stout_smear, unpack)
+from .autograd import PseudofermionAction, StoutSmear, pseudofermion_action, stout_smear_links
 from .lib import StgError, lib
 
 __all__ = ["Lattice", "Gauge", "pack", "unpack", "dslash_eo", "dslash_oe", "dslash_eo_", "dslash_oe_",
            "dslash_multi_", "normal_op", "normal_op_", "normal_op_noalloc_", "mscg", "mscg_batched", "fermion_force",
-           "PseudofermionAction", "pseudofermion_action", "StgError", "lib"]
+           "stout_smear", "stout_force", "PseudofermionAction", "pseudofermion_action", "StoutSmear",
+           "stout_smear_links", "StgError", "lib"]

@@ -298,3 +298,27 @@ def fermion_force(g_f64: Gauge, residues, x: torch.Tensor, kind: int = 0, stream
     check(lib().stg_fermion_force(g_f64.handle, ns, res, ctypes.cast(xp, ctypes.POINTER(ctypes.c_void_p)), _ptr(out),
                                   int(kind), _stream(stream)), "stg_fermion_force")
     return out
+
+
+def stout_smear(lattice: Lattice, links: torch.Tensor, rho: float, nstep: int, stream=None) -> torch.Tensor:
+    """Stout-smeared levels U^(1) .. U^(nstep), [nstep, 4, V, 3, 3] complex128, from U^(0)
+    [4, V, 3, 3] (canonical layout, FP64)."""
+    u = _dev(links).reshape(4, lattice.V, 3, 3)
+    out = torch.empty((int(nstep), 4, lattice.V, 3, 3), dtype=torch.complex128, device="cuda")
+    check(lib().stg_stout_smear(lattice.handle, int(nstep), float(rho), _ptr(u), _ptr(out), _stream(stream)),
+          "stg_stout_smear")
+    return out
+
+
+def stout_force(lattice: Lattice, links: torch.Tensor, levels: torch.Tensor, rho: float, grad: torch.Tensor,
+                kind: int = 1, stream=None) -> torch.Tensor:
+    """Pulls dS/dU^(k) (torch convention, [4, V, 3, 3]) back through k = len(levels) stout steps:
+    kind 1 -> dS/dRe U^(0) + i dS/dIm U^(0), kind 0 -> TA(U^(0) G^dag) (Lie-algebra force)."""
+    u = _dev(links).reshape(4, lattice.V, 3, 3)
+    lv = _dev(levels)
+    nstep = int(lv.shape[0])
+    gr = _dev(grad).reshape(4, lattice.V, 3, 3)
+    out = torch.empty((4, lattice.V, 3, 3), dtype=torch.complex128, device="cuda")
+    check(lib().stg_stout_force(lattice.handle, nstep, float(rho), _ptr(u), _ptr(lv), _ptr(gr), _ptr(out), int(kind),
+                                _stream(stream)), "stg_stout_force")
+    return out

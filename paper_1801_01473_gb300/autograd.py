@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import torch
 
-from .api import Gauge, Lattice, fermion_force, mscg
+from .api import Gauge, Lattice, fermion_force, mscg, stout_force, stout_smear
 
 
 class PseudofermionAction(torch.autograd.Function):
@@ -35,3 +35,30 @@ class PseudofermionAction(torch.autograd.Function):
 def pseudofermion_action(links, b, lattice, shifts, residues, mass, tol=1e-12):
     """S(U) with autograd support with respect to the links (complex128 [4, V, 3, 3] on cuda)."""
     return PseudofermionAction.apply(links, b, lattice, shifts, residues, mass, tol)
+
+
+class StoutSmear(torch.autograd.Function):
+    """U^(0) -> U^(nstep) by nstep stout steps (stg_stout_smear); backward pulls the incoming
+    gradient back through the steps with the hand-written chain-rule kernels (stg_stout_force,
+    kind 1), in the same convention."""
+
+    @staticmethod
+    def forward(ctx, links, lattice: Lattice, rho: float, nstep: int):
+        u = links.detach()
+        levels = stout_smear(lattice, u, rho, nstep)
+        ctx.save_for_backward(u, levels)
+        ctx.lattice = lattice
+        ctx.rho = float(rho)
+        ctx.shape = links.shape
+        return levels[-1].clone().reshape(links.shape)
+
+    @staticmethod
+    def backward(ctx, grad_out):
+        u, levels = ctx.saved_tensors
+        g = stout_force(ctx.lattice, u, levels, ctx.rho, grad_out.contiguous(), kind=1)
+        return g.reshape(ctx.shape), None, None, None
+
+
+def stout_smear_links(links, lattice, rho, nstep):
+    """U^(nstep)(U^(0)) with autograd support (complex128 [4, V, 3, 3] on cuda)."""
+    return StoutSmear.apply(links, lattice, rho, nstep)

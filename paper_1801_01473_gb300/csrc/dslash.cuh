@@ -154,7 +154,7 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
         }
         if (MODE != 0 && G.partial[j] != nullptr) {
             // two warps per 64-site chunk: warp sums, then pairs of warps
-            double pv = warp_sum(part.value());
+            const double pv = part.warp_total();
             __syncthreads();
             if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = pv;
             __syncthreads();

@@ -46,6 +46,12 @@ __device__ __forceinline__ void warp_partial(double v, int h, int Vh, double *pa
     v = warp_sum(v);
     if ((threadIdx.x & 31) == 0 && h < Vh) part[h >> 5] = v;
 }
+template <typename R>
+__device__ __forceinline__ void warp_partial(const ProdSum<R> &a, int h, int Vh, double *part)
+{
+    const double v = a.warp_total();
+    if ((threadIdx.x & 31) == 0 && h < Vh) part[h >> 5] = v;
+}
 
 struct SysScal {
     double rr, alpha, alpha_old, beta_old, bnorm2, tol2, tol2_true, rr_last, delta2, coef, rr_best;
@@ -66,13 +72,15 @@ struct SysVecs {
 
 // ------------------------------------------------------------------ vector kernels
 
+// |v|^2 of one site added to a partial-sum accumulator of the iteration precision
 template <typename R>
-__device__ __forceinline__ double norm2_site(const cx<R> v[3])
+__device__ __forceinline__ void norm2_site(ProdSum<R> &acc, const cx<R> v[3])
 {
-    double s = 0.0;
 #pragma unroll
-    for (int c = 0; c < 3; ++c) s += (double)v[c].re * (double)v[c].re + (double)v[c].im * (double)v[c].im;
-    return s;
+    for (int c = 0; c < 3; ++c) {
+        acc.add(v[c].re, v[c].re);
+        acc.add(v[c].im, v[c].im);
+    }
 }
 
 // phase-1 start: r = p_i = b (rounded to R), x_i = 0, b64 = b (in H); partials |r|^2 (R) and |b|^2 (FP64)
@@ -82,7 +90,8 @@ __global__ void __launch_bounds__(kVecBlock) k_p1_init(const SysVecs *__restrict
     const SysVecs &V = sv[blockIdx.y];
     if ((int)(blockIdx.x * kVecBlock) >= V.Vh) return;
     int h = blockIdx.x * kVecBlock + threadIdx.x;
-    double pr = 0.0, pb = 0.0;
+    ProdSum<R> pr;
+    double pb = 0.0;
     if (h < V.Vh) {
         cx<R> v[3];
         cx<H> z[3];
@@ -93,7 +102,7 @@ __global__ void __launch_bounds__(kVecBlock) k_p1_init(const SysVecs *__restrict
             v[c] = cx<R>{(R)d.x, (R)d.y};
             z[c] = cx<H>{H(0), H(0)};
         }
-        pr = norm2_site(v);
+        norm2_site(pr, v);
         Field<R>::store(V.r, V.Vh, h, v);
         for (int i = 0; i < nshift; ++i) {
             Field<R>::store(V.p[i], V.Vh, h, v);
@@ -144,7 +153,7 @@ __global__ void __launch_bounds__(kVecBlock) k_update_r(const SysScal *__restric
         const SysVecs &V = sv[s];
         const int lb = b - w.start[s];
         const int h = lb * kVecBlock + threadIdx.x;
-        double pr = 0.0;
+        ProdSum<R> pr;
         if (h < V.Vh) {
             const R a = (R)S.alpha;
             cx<R> r[3], q[3];
@@ -153,7 +162,7 @@ __global__ void __launch_bounds__(kVecBlock) k_update_r(const SysScal *__restric
 #pragma unroll
             for (int c = 0; c < 3; ++c) r[c] = cx<R>{fma(-a, q[c].re, r[c].re), fma(-a, q[c].im, r[c].im)};
             Field<R>::store(V.r, V.Vh, h, r);
-            pr = norm2_site(r);
+            norm2_site(pr, r);
         }
         warp_partial(pr, h, V.Vh, V.part_v);
     }
@@ -441,7 +450,7 @@ __global__ void __launch_bounds__(kVecBlock) k_rel_copy(const SysVecs *__restric
     const SysVecs &V = sv[s];
     if (noupd[s] || finished[s] || (int)(blockIdx.x * kVecBlock) >= V.Vh) return;
     int h = blockIdx.x * kVecBlock + threadIdx.x;
-    double pr = 0.0;
+    ProdSum<R> pr;
     if (h < V.Vh) {
         cx<H> rh[3];
         cx<R> r[3];
@@ -456,7 +465,7 @@ __global__ void __launch_bounds__(kVecBlock) k_rel_copy(const SysVecs *__restric
             Field<R>::store(V.p[0], V.Vh, h, r);
             Field<R>::store(V.x[0], V.Vh, h, z);
         }
-        pr = norm2_site(r);
+        norm2_site(pr, r);
     }
     warp_partial(pr, h, V.Vh, V.part_v);
 }

@@ -142,19 +142,50 @@ __device__ __forceinline__ dsf fma(const dsf &a, const dsf &b, const dsf &c)
     return ds_fast_two_sum(s.hi, __fadd_rn(s.lo, __fadd_rn(e, c.lo)));
 }
 
-// FP64 accumulator of products of two values of type R: plain double for float/double,
-// a double-single running sum for dsf (one conversion at the end instead of one per term).
+__device__ __forceinline__ double warp_sum(double v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// Sum over a warp of a double-single value (xor butterfly: every lane ends with the same sum).
+__device__ __forceinline__ dsf warp_sum_ds(dsf v)
+{
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1)
+        v = v + dsf(__shfl_xor_sync(0xffffffffu, v.hi, o), __shfl_xor_sync(0xffffffffu, v.lo, o));
+    return v;
+}
+
+// Accumulator of products of two values of type R for the FP64 partial sums (<p,q>, |r|^2):
+// FP64 for double; for float and double-single a double-single sum of the exact products
+// (rounding ~2^-44 per operation) reduced over the warp on the FP32 pipes, with one conversion
+// to FP64 per warp.  GB300 issues FP64 (and FP32<->FP64 conversion) ~64x slower than FP32, so
+// converting every site's terms to FP64 made the FP32 vector kernels ALU-bound.
 template <typename R>
 struct ProdSum {
     double s = 0.0;
-    __device__ __forceinline__ void add(R a, R b) { s += (double)a * (double)b; }
-    __device__ __forceinline__ double value() const { return s; }
+    __device__ __forceinline__ void add(R a, R b) { s = fma((double)a, (double)b, s); }
+    __device__ __forceinline__ double warp_total() const { return warp_sum(s); }
+};
+template <>
+struct ProdSum<float> {
+    dsf s = dsf(0.f, 0.f);
+    __device__ __forceinline__ void add(float a, float b)
+    {
+        const float p = __fmul_rn(a, b);
+        const float e = __fmaf_rn(a, b, -p);  // a b = p + e exactly
+        const dsf t = ds_two_sum(p, s.hi);
+        s = ds_fast_two_sum(t.hi, __fadd_rn(t.lo, __fadd_rn(e, s.lo)));
+    }
+    __device__ __forceinline__ double warp_total() const { return (double)warp_sum_ds(s); }
 };
 template <>
 struct ProdSum<dsf> {
     dsf s = dsf(0.f, 0.f);
     __device__ __forceinline__ void add(const dsf &a, const dsf &b) { s = fma(a, b, s); }
-    __device__ __forceinline__ double value() const { return (double)s; }
+    __device__ __forceinline__ double warp_total() const { return (double)warp_sum_ds(s); }
 };
 
 // ------------------------------------------------------------------ geometry
@@ -498,12 +529,6 @@ __device__ __forceinline__ void pdl_enter()
 
 // ------------------------------------------------------------------ reductions
 
-__device__ __forceinline__ double warp_sum(double v)
-{
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-    return v;
-}
 
 // Deterministic block sum (fixed tree); result valid in thread 0.  `sh` holds >= 32 doubles.
 __device__ __forceinline__ double block_sum(double v, double *sh)

@@ -1,0 +1,494 @@
+// stout.cu -- stout smearing of the gauge links and the force chain rule through it (Sec. 2:
+// the Dirac operator uses the k-times stout-smeared links U^(k); Sec. 3: the MD evolves U^(0),
+// so the fermion force is pulled back through the k smearing steps).
+//
+// One step, per link (x, mu):  C = rho * (sum of the six staples around the link),
+// i Q = TA(C U^dag), U' = exp(iQ) U.  exp(iQ) = f0 + f1 Q + f2 Q^2: Q^n reduces to
+// a_n + b_n Q + c_n Q^2 by the Cayley-Hamilton identity Q^3 = c1 Q + c0 (c0 = det Q,
+// c1 = tr Q^2 / 2, Q traceless Hermitian), so the f_j are the Taylor series of exp with
+// scalar coefficient recursions -- no transcendental functions, and entire in (c0, c1), so the
+// chain rule needs no special case at degenerate eigenvalues.  The recursion also carries
+// d/dc0 and d/dc1 of the coefficients for the backward pass.
+//
+// Gradients follow torch's convention (G = dS/dRe U + i dS/dIm U, dS = Re tr(G^dag dU)).  The
+// backward step is two kernels: k_stout_back_link (per link: the exp/TA/Omega part, writes the
+// link's own gradient terms and Y = rho G_Omega U, the gradient of the unweighted staple sum)
+// and k_stout_back_staples (per link: adds the product-rule terms of every staple of the other
+// links' C that contains this link, gathered from Y -- each output is written by one thread).
+//
+// Layout: canonical complex128 [4][V][3][3] (site index x + Lx (y + Ly (z + Lz t))); one thread
+// per link.  All arithmetic FP64 (GB300's FP64 rate bounds these kernels, not HBM).
+#include <cmath>
+#include <cstring>
+#include <string>
+
+#include "stg_common.h"
+
+namespace stg {
+namespace {
+
+struct M3 {
+    cx<double> m[3][3];
+};
+
+struct LinkGeo {
+    int L[4];
+    long long stride[4];
+    long long V;
+};
+
+__device__ __forceinline__ long long nb(const LinkGeo &g, long long i, int mu, int step)
+{
+    const int xm = (int)((i / g.stride[mu]) % g.L[mu]);
+    long long j = i + step * g.stride[mu];
+    if (xm + step >= g.L[mu]) j -= g.L[mu] * g.stride[mu];
+    if (xm + step < 0) j += g.L[mu] * g.stride[mu];
+    return j;
+}
+
+__device__ __forceinline__ void ld(const double2 *__restrict__ base, const LinkGeo &g, int mu, long long i, M3 &a)
+{
+    const double2 *p = base + ((long long)mu * g.V + i) * 9;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) {
+        const double2 v = p[k];
+        a.m[k / 3][k % 3] = cx<double>{v.x, v.y};
+    }
+}
+
+__device__ __forceinline__ void st(double2 *__restrict__ base, const LinkGeo &g, int mu, long long i, const M3 &a)
+{
+    double2 *p = base + ((long long)mu * g.V + i) * 9;
+#pragma unroll
+    for (int k = 0; k < 9; ++k) p[k] = make_double2(a.m[k / 3][k % 3].re, a.m[k / 3][k % 3].im);
+}
+
+// element (r, c) of a or of a^dag
+template <bool D>
+__device__ __forceinline__ cx<double> el(const M3 &a, int r, int c)
+{
+    return D ? cconj(a.m[c][r]) : a.m[r][c];
+}
+
+// acc (+)= op(a) op(b)
+template <bool DA, bool DB>
+__device__ __forceinline__ void mul_acc(M3 &acc, const M3 &a, const M3 &b)
+{
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c)
+#pragma unroll
+            for (int k = 0; k < 3; ++k) cmac(acc.m[r][c], el<DA>(a, r, k), el<DB>(b, k, c));
+}
+
+template <bool DA, bool DB>
+__device__ __forceinline__ M3 mul(const M3 &a, const M3 &b)
+{
+    M3 z;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) z.m[r][c] = cx<double>{0.0, 0.0};
+    mul_acc<DA, DB>(z, a, b);
+    return z;
+}
+
+__device__ __forceinline__ M3 zero3()
+{
+    M3 z;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) z.m[r][c] = cx<double>{0.0, 0.0};
+    return z;
+}
+
+// TA(X) = (X - X^dag)/2 - tr(X - X^dag)/6
+__device__ __forceinline__ M3 ta(const M3 &x)
+{
+    M3 y;
+    const double im_tr = (x.m[0][0].im + x.m[1][1].im + x.m[2][2].im) / 3.0;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            y.m[r][c] = cx<double>{0.5 * (x.m[r][c].re - x.m[c][r].re), 0.5 * (x.m[r][c].im + x.m[c][r].im)};
+            if (r == c) y.m[r][c].im -= im_tr;
+        }
+    return y;
+}
+
+// Weighted staple sum C_mu(x) = rho * sum_{nu != mu} (upper + lower staple).
+__device__ M3 staple_sum(const double2 *__restrict__ U, const LinkGeo &g, int mu, long long i, double rho)
+{
+    M3 c = zero3();
+#pragma unroll 1
+    for (int nu = 0; nu < 4; ++nu) {
+        if (nu == mu) continue;
+        M3 a, b, t;
+        // U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
+        ld(U, g, nu, i, a);
+        ld(U, g, mu, nb(g, i, nu, 1), b);
+        t = mul<false, false>(a, b);
+        ld(U, g, nu, nb(g, i, mu, 1), a);
+        mul_acc<false, true>(c, t, a);
+        // U_nu(x-nu)^dag U_mu(x-nu) U_nu(x-nu+mu)
+        const long long xm = nb(g, i, nu, -1);
+        ld(U, g, nu, xm, a);
+        ld(U, g, mu, xm, b);
+        t = mul<true, false>(a, b);
+        ld(U, g, nu, nb(g, xm, mu, 1), a);
+        mul_acc<false, false>(c, t, a);
+    }
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int k = 0; k < 3; ++k) c.m[r][k] = cx<double>{rho * c.m[r][k].re, rho * c.m[r][k].im};
+    return c;
+}
+
+// f_j of exp(iQ) = f0 + f1 Q + f2 Q^2 and (DERIV) df_j/dc0, df_j/dc1.
+struct ExpCoef {
+    cx<double> f[3], d0[3], d1[3];
+};
+
+template <bool DERIV>
+__device__ ExpCoef exp_coef(double c0, double c1)
+{
+    ExpCoef e;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) e.f[j] = e.d0[j] = e.d1[j] = cx<double>{0.0, 0.0};
+    e.f[0].re = 1.0;  // n = 0
+    double a = 1.0, b = 0.0, c = 0.0;                        // Q^n = a + b Q + c Q^2
+    double a0 = 0.0, b0 = 0.0, cc0 = 0.0, a1 = 0.0, b1 = 0.0, cc1 = 0.0;  // d/dc0, d/dc1
+    const double r = fmax(sqrt(fmax(2.0 * c1, 0.0)), 1.0);  // >= spectral radius of Q, >= 1
+    double w = 1.0, bound = 1.0;                             // 1/n!, r^n/n!
+#pragma unroll 1
+    for (int n = 1; n < 128; ++n) {
+        if (DERIV) {
+            const double na0 = c + c0 * cc0, nb0 = a0 + c1 * cc0, nc0 = b0;
+            const double na1 = c0 * cc1, nb1 = a1 + c + c1 * cc1, nc1 = b1;
+            a0 = na0; b0 = nb0; cc0 = nc0; a1 = na1; b1 = nb1; cc1 = nc1;
+        }
+        const double na = c0 * c, nb = a + c1 * c, nc = b;
+        a = na; b = nb; c = nc;
+        w /= n;
+        bound *= r / n;
+        // i^n / n!
+        const double s = (n & 2) ? -w : w;
+        if (n & 1) {
+            e.f[0].im += s * a; e.f[1].im += s * b; e.f[2].im += s * c;
+            if (DERIV) {
+                e.d0[0].im += s * a0; e.d0[1].im += s * b0; e.d0[2].im += s * cc0;
+                e.d1[0].im += s * a1; e.d1[1].im += s * b1; e.d1[2].im += s * cc1;
+            }
+        } else {
+            e.f[0].re += s * a; e.f[1].re += s * b; e.f[2].re += s * c;
+            if (DERIV) {
+                e.d0[0].re += s * a0; e.d0[1].re += s * b0; e.d0[2].re += s * cc0;
+                e.d1[0].re += s * a1; e.d1[1].re += s * b1; e.d1[2].re += s * cc1;
+            }
+        }
+        // remaining terms of the coefficients (and of their c-derivatives, polynomial in n
+        // times r^n/n!) are below FP64 resolution
+        const double m = (double)(n + 1);
+        if (n >= 6 && bound * m * m * m < 1e-18) break;
+    }
+    return e;
+}
+
+// c0 = det Q, c1 = tr Q^2 / 2 of a Hermitian Q (both real)
+__device__ __forceinline__ void char_coefs(const M3 &q, const M3 &q2, double &c0, double &c1)
+{
+    c1 = 0.5 * (q2.m[0][0].re + q2.m[1][1].re + q2.m[2][2].re);
+    // det = q00 (q11 q22 - q12 q21) - q01 (q10 q22 - q12 q20) + q02 (q10 q21 - q11 q20)
+    cx<double> t = cmul(q.m[1][1], q.m[2][2]), u = cmul(q.m[1][2], q.m[2][1]);
+    const cx<double> d = cmul(q.m[0][0], cx<double>{t.re - u.re, t.im - u.im});
+    t = cmul(q.m[1][0], q.m[2][2]); u = cmul(q.m[1][2], q.m[2][0]);
+    const cx<double> e1 = cmul(q.m[0][1], cx<double>{t.re - u.re, t.im - u.im});
+    t = cmul(q.m[1][0], q.m[2][1]); u = cmul(q.m[1][1], q.m[2][0]);
+    const cx<double> e2 = cmul(q.m[0][2], cx<double>{t.re - u.re, t.im - u.im});
+    c0 = d.re - e1.re + e2.re;
+}
+
+// E = f0 + f1 Q + f2 Q^2
+__device__ __forceinline__ M3 poly3(const cx<double> f[3], const M3 &q, const M3 &q2)
+{
+    M3 e;
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cx<double> v = cmul(f[1], q.m[r][c]);
+            cmac(v, f[2], q2.m[r][c]);
+            if (r == c) { v.re += f[0].re; v.im += f[0].im; }
+            e.m[r][c] = v;
+        }
+    return e;
+}
+
+// Q = -i TA(C U^dag) and its square; returns nothing else
+__device__ __forceinline__ void make_q(const M3 &C, const M3 &u, M3 &q, M3 &q2)
+{
+    const M3 a = ta(mul<false, true>(C, u));  // = i Q
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) q.m[r][c] = cx<double>{a.m[r][c].im, -a.m[r][c].re};
+    q2 = mul<false, false>(q, q);
+}
+
+struct StoutArgs {
+    LinkGeo g;
+    double rho;
+    const double2 *U;     // links of this step
+    const double2 *G;     // gradient of the step's output (backward)
+    double2 *out;         // smeared links (forward) / gradient of U (backward)
+    double2 *Y;           // rho G_Omega U (backward)
+};
+
+constexpr int kStoutBlock = 128;
+
+__global__ void __launch_bounds__(kStoutBlock) k_stout_fwd(const __grid_constant__ StoutArgs a)
+{
+    const int mu = blockIdx.y;
+    const long long i = (long long)blockIdx.x * kStoutBlock + threadIdx.x;
+    if (i >= a.g.V) return;
+    M3 q, q2, u;
+    {
+        const M3 C = staple_sum(a.U, a.g, mu, i, a.rho);
+        ld(a.U, a.g, mu, i, u);
+        make_q(C, u, q, q2);
+    }
+    double c0, c1;
+    char_coefs(q, q2, c0, c1);
+    const ExpCoef e = exp_coef<false>(c0, c1);
+    const M3 E = poly3(e.f, q, q2);
+    st(a.out, a.g, mu, i, mul<false, false>(E, u));
+}
+
+__global__ void __launch_bounds__(kStoutBlock) k_stout_back_link(const __grid_constant__ StoutArgs a)
+{
+    const int mu = blockIdx.y;
+    const long long i = (long long)blockIdx.x * kStoutBlock + threadIdx.x;
+    if (i >= a.g.V) return;
+    M3 u, q, q2, gp;
+    const M3 C = staple_sum(a.U, a.g, mu, i, a.rho);
+    ld(a.U, a.g, mu, i, u);
+    make_q(C, u, q, q2);
+    double c0, c1;
+    char_coefs(q, q2, c0, c1);
+    const ExpCoef e = exp_coef<true>(c0, c1);
+    ld(a.G, a.g, mu, i, gp);
+    // the link's own terms: E^dag G' (later + G_Omega^dag C)
+    M3 gu = mul<true, false>(poly3(e.f, q, q2), gp);
+    const M3 M = mul<false, true>(gp, u);  // gradient of E
+    // T_j = tr(M^dag Q^j);  K = sum_j Re(T_j df_j/dc)
+    cx<double> T[3] = {cx<double>{0.0, 0.0}, cx<double>{0.0, 0.0}, cx<double>{0.0, 0.0}};
+#pragma unroll
+    for (int r = 0; r < 3; ++r) {
+        T[0] = cx<double>{T[0].re + M.m[r][r].re, T[0].im - M.m[r][r].im};
+#pragma unroll
+        for (int k = 0; k < 3; ++k) {
+            cmac_conj(T[1], M.m[k][r], q.m[k][r]);
+            cmac_conj(T[2], M.m[k][r], q2.m[k][r]);
+        }
+    }
+    double K0 = 0.0, K1 = 0.0;
+#pragma unroll
+    for (int j = 0; j < 3; ++j) {
+        K0 += T[j].re * e.d0[j].re - T[j].im * e.d0[j].im;
+        K1 += T[j].re * e.d1[j].re - T[j].im * e.d1[j].im;
+    }
+    // G_Q = K1 Q + K0 Q^2 + conj(f1) M + conj(f2) (M Q + Q M)
+    M3 gq = mul<false, false>(M, q);
+    mul_acc<false, false>(gq, q, M);
+    const cx<double> f1c = cconj(e.f[1]), f2c = cconj(e.f[2]);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            cx<double> v = cmul(f2c, gq.m[r][c]);
+            cmac(v, f1c, M.m[r][c]);
+            v.re += K1 * q.m[r][c].re + K0 * q2.m[r][c].re;
+            v.im += K1 * q.m[r][c].im + K0 * q2.m[r][c].im;
+            gq.m[r][c] = cx<double>{-v.im, v.re};  // i G_Q
+        }
+    const M3 go = ta(gq);  // G_Omega
+    mul_acc<true, false>(gu, go, C);
+    st(a.out, a.g, mu, i, gu);
+    M3 y = mul<false, false>(go, u);
+#pragma unroll
+    for (int r = 0; r < 3; ++r)
+#pragma unroll
+        for (int c = 0; c < 3; ++c) y.m[r][c] = cx<double>{a.rho * y.m[r][c].re, a.rho * y.m[r][c].im};
+    st(a.Y, a.g, mu, i, y);
+}
+
+// Adds to the gradient of link (y, nu) the staple terms: for every mu != nu, the link sits in
+//   C_mu(y)       as the first factor of the upper staple      -> Y_mu(y) U_nu(y+mu) U_mu(y+nu)^dag
+//   C_mu(y+nu)    as the first factor of the lower staple      -> U_mu(y) U_nu(y+mu) Y_mu(y+nu)^dag
+//   C_nu(y+mu)    as the middle factor of the lower staple     -> U_mu(y) Y_nu(y+mu) U_mu(y+nu)^dag
+//   C_mu(y-mu)    as the last factor of the upper staple       -> Y_mu(y-mu)^dag U_nu(y-mu) U_mu(y-mu+nu)
+//   C_mu(y-mu+nu) as the last factor of the lower staple       -> U_mu(y-mu)^dag U_nu(y-mu) Y_mu(y-mu+nu)
+//   C_nu(y-mu)    as the middle factor of the upper staple     -> U_mu(y-mu)^dag Y_nu(y-mu) U_mu(y-mu+nu)
+// with Y the gradient of the unweighted staple sums.
+__global__ void __launch_bounds__(kStoutBlock) k_stout_back_staples(const __grid_constant__ StoutArgs a)
+{
+    const int nu = blockIdx.y;
+    const long long i = (long long)blockIdx.x * kStoutBlock + threadIdx.x;
+    if (i >= a.g.V) return;
+    M3 acc;
+    ld(a.out, a.g, nu, i, acc);
+#pragma unroll 1
+    for (int mu = 0; mu < 4; ++mu) {
+        if (mu == nu) continue;
+        const long long yp = nb(a.g, i, mu, 1), yn = nb(a.g, i, nu, 1);
+        const long long ym = nb(a.g, i, mu, -1), ymn = nb(a.g, ym, nu, 1);
+        M3 p, q, t;
+        // forward side: U_nu(y+mu) shared by the first two terms
+        ld(a.U, a.g, nu, yp, p);   // U_nu(y+mu)
+        ld(a.U, a.g, mu, yn, q);   // U_mu(y+nu)
+        t = mul<false, true>(p, q);
+        ld(a.Y, a.g, mu, i, q);    // Y_mu(y)
+        mul_acc<false, false>(acc, q, t);
+        ld(a.U, a.g, mu, i, q);    // U_mu(y)
+        t = mul<false, false>(q, p);
+        ld(a.Y, a.g, mu, yn, p);   // Y_mu(y+nu)
+        mul_acc<false, true>(acc, t, p);
+        ld(a.Y, a.g, nu, yp, p);   // Y_nu(y+mu)
+        t = mul<false, false>(q, p);
+        ld(a.U, a.g, mu, yn, q);   // U_mu(y+nu)
+        mul_acc<false, true>(acc, t, q);
+        // backward side: U_mu(y-mu)^dag leads the last two terms
+        ld(a.U, a.g, nu, ym, p);   // U_nu(y-mu)
+        ld(a.U, a.g, mu, ymn, q);  // U_mu(y-mu+nu)
+        t = mul<false, false>(p, q);
+        ld(a.Y, a.g, mu, ym, q);   // Y_mu(y-mu)
+        mul_acc<true, false>(acc, q, t);
+        ld(a.Y, a.g, mu, ymn, q);  // Y_mu(y-mu+nu)
+        t = mul<false, false>(p, q);
+        ld(a.Y, a.g, nu, ym, p);   // Y_nu(y-mu)
+        ld(a.U, a.g, mu, ymn, q);  // U_mu(y-mu+nu)
+        mul_acc<false, false>(t, p, q);
+        ld(a.U, a.g, mu, ym, p);   // U_mu(y-mu)
+        mul_acc<true, false>(acc, p, t);
+    }
+    st(a.out, a.g, nu, i, acc);
+}
+
+// F = TA(U G^dag) in place over G
+__global__ void __launch_bounds__(kStoutBlock) k_lie_force(const __grid_constant__ StoutArgs a)
+{
+    const int mu = blockIdx.y;
+    const long long i = (long long)blockIdx.x * kStoutBlock + threadIdx.x;
+    if (i >= a.g.V) return;
+    M3 u, gr;
+    ld(a.U, a.g, mu, i, u);
+    ld(a.out, a.g, mu, i, gr);
+    st(a.out, a.g, mu, i, ta(mul<false, true>(u, gr)));
+}
+
+LinkGeo link_geo(const stg_lattice *lat)
+{
+    LinkGeo g;
+    long long s = 1;
+    for (int mu = 0; mu < 4; ++mu) {
+        g.L[mu] = lat->g.L[mu];
+        g.stride[mu] = s;
+        s *= g.L[mu];
+    }
+    g.V = s;
+    return g;
+}
+
+stg_status check_common(const stg_lattice *lat, int nstep, double rho, const char *fn)
+{
+    const std::string f(fn);
+    if (!lat) return set_error(STG_ERR_ARG, f + ": null lattice");
+    if (nstep < 1 || nstep > 16) return set_error(STG_ERR_ARG, f + ": nstep must be in 1..16");
+    if (!(fabs(rho) <= 0.5)) return set_error(STG_ERR_ARG, f + ": |rho| must be <= 0.5");
+    return STG_OK;
+}
+
+bool misaligned(const void *p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15) != 0; }
+
+}  // namespace
+}  // namespace stg
+
+using namespace stg;
+
+extern "C" stg_status stg_stout_smear(const stg_lattice *lat, int32_t nstep, double rho, const void *links_c128_dev,
+                                      void *levels_c128_dev, void *stream)
+{
+    stg_status s = check_common(lat, nstep, rho, "stg_stout_smear");
+    if (s != STG_OK) return s;
+    if (misaligned(links_c128_dev) || misaligned(levels_c128_dev))
+        return set_error(STG_ERR_ARG, "stg_stout_smear: buffers must be non-null and 16-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    StoutArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = link_geo(lat);
+    a.rho = rho;
+    const size_t level = (size_t)4 * a.g.V * 9;  // double2 per level
+    const dim3 grid((unsigned)((a.g.V + kStoutBlock - 1) / kStoutBlock), 4);
+    for (int k = 0; k < nstep; ++k) {
+        a.U = k == 0 ? static_cast<const double2 *>(links_c128_dev)
+                     : static_cast<const double2 *>(levels_c128_dev) + (size_t)(k - 1) * level;
+        a.out = static_cast<double2 *>(levels_c128_dev) + (size_t)k * level;
+        k_stout_fwd<<<grid, kStoutBlock, 0, st>>>(a);
+        STG_CUDA_TRY(cudaGetLastError());
+    }
+    return STG_OK;
+}
+
+extern "C" stg_status stg_stout_force(const stg_lattice *lat, int32_t nstep, double rho, const void *links_c128_dev,
+                                      const void *levels_c128_dev, const void *grad_c128_dev, void *out_c128_dev,
+                                      int32_t kind, void *stream)
+{
+    stg_status s = check_common(lat, nstep, rho, "stg_stout_force");
+    if (s != STG_OK) return s;
+    if (misaligned(links_c128_dev) || misaligned(grad_c128_dev) || misaligned(out_c128_dev) ||
+        (nstep > 1 && misaligned(levels_c128_dev)))
+        return set_error(STG_ERR_ARG, "stg_stout_force: buffers must be non-null and 16-byte aligned");
+    if (kind != 0 && kind != 1) return set_error(STG_ERR_ARG, "stg_stout_force: kind must be 0 or 1");
+    if (out_c128_dev == grad_c128_dev || out_c128_dev == links_c128_dev)
+        return set_error(STG_ERR_ARG, "stg_stout_force: out must not alias the inputs");
+    cudaStream_t st = (cudaStream_t)stream;
+    StoutArgs a;
+    memset(&a, 0, sizeof(a));
+    a.g = link_geo(lat);
+    a.rho = rho;
+    const size_t level = (size_t)4 * a.g.V * 9;
+    double2 *ws = nullptr;
+    STG_CUDA_TRY(cudaMallocAsync((void **)&ws, 2 * level * sizeof(double2), st));
+    struct Free {
+        void *p;
+        cudaStream_t s;
+        ~Free() { cudaFreeAsync(p, s); }
+    } fr{ws, st};
+    double2 *Y = ws, *tmp = ws + level, *out = static_cast<double2 *>(out_c128_dev);
+    const dim3 grid((unsigned)((a.g.V + kStoutBlock - 1) / kStoutBlock), 4);
+    const double2 *g_in = static_cast<const double2 *>(grad_c128_dev);
+    for (int k = nstep - 1; k >= 0; --k) {
+        // the last step (k = 0) lands in out; earlier ones alternate so that it does
+        double2 *dst = (k % 2 == 0) ? out : tmp;
+        a.U = k == 0 ? static_cast<const double2 *>(links_c128_dev)
+                     : static_cast<const double2 *>(levels_c128_dev) + (size_t)(k - 1) * level;
+        a.G = g_in;
+        a.out = dst;
+        a.Y = Y;
+        k_stout_back_link<<<grid, kStoutBlock, 0, st>>>(a);
+        k_stout_back_staples<<<grid, kStoutBlock, 0, st>>>(a);
+        STG_CUDA_TRY(cudaGetLastError());
+        g_in = dst;
+    }
+    if (kind == 0) {
+        a.U = static_cast<const double2 *>(links_c128_dev);
+        a.out = out;
+        k_lie_force<<<grid, kStoutBlock, 0, st>>>(a);
+        STG_CUDA_TRY(cudaGetLastError());
+    }
+    return STG_OK;
+}

@@ -26,6 +26,7 @@ EXPORTS = [
     "stg_field_bytes", "stg_field_pack", "stg_field_unpack",
     "stg_dslash_eo", "stg_dslash_oe", "stg_dslash_multi", "stg_normal_op", "stg_normal_op_noalloc",
     "stg_mscg_solve", "stg_mscg_solve_batched", "stg_fermion_force",
+    "stg_stout_smear", "stg_stout_force",
 ]
 
 
@@ -91,12 +92,15 @@ def lib() -> ctypes.CDLL:
     L.stg_mscg_solve.argtypes = [P, P, ctypes.POINTER(MscgParams), P, PP, ctypes.POINTER(MscgStats), P]
     L.stg_mscg_solve_batched.argtypes = [I32, ctypes.POINTER(Instance), ctypes.POINTER(MscgParams), P]
     L.stg_fermion_force.argtypes = [P, I32, ctypes.POINTER(D), PP, P, I32, P]
+    L.stg_stout_smear.argtypes = [P, I32, D, P, P, P]
+    L.stg_stout_force.argtypes = [P, I32, D, P, P, P, P, I32, P]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is ctypes.c_int or name in ("stg_lattice_create", "stg_gauge_create", "stg_field_pack",
                                                  "stg_field_unpack", "stg_dslash_eo", "stg_dslash_oe",
                                                  "stg_dslash_multi", "stg_normal_op", "stg_normal_op_noalloc", "stg_mscg_solve",
-                                                 "stg_mscg_solve_batched", "stg_fermion_force"):
+                                                 "stg_mscg_solve_batched", "stg_fermion_force",
+                                                 "stg_stout_smear", "stg_stout_force"):
             f.restype = ctypes.c_int
     _lib = L
     return L

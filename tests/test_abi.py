@@ -82,6 +82,24 @@ def test_null_arguments_rejected_before_launch(L):
     L.stg_lattice_destroy(h)
 
 
+def test_stout_arguments_rejected_before_launch(L):
+    rc, h = _lat(L, (4, 4, 4, 4))
+    a, b, c, d = (ctypes.c_void_p(v) for v in (256, 512, 768, 1024))
+    smear, force = L.stg_stout_smear, L.stg_stout_force
+    assert smear(None, 1, 0.1, a, b, None) == -1
+    assert smear(h, 0, 0.1, a, b, None) == -1 and b"nstep" in L.stg_last_error()
+    assert smear(h, 17, 0.1, a, b, None) == -1
+    assert smear(h, 1, 0.6, a, b, None) == -1 and b"rho" in L.stg_last_error()
+    assert smear(h, 1, float("nan"), a, b, None) == -1
+    assert smear(h, 1, 0.1, ctypes.c_void_p(8), b, None) == -1
+    assert smear(h, 1, 0.1, a, None, None) == -1
+    assert force(h, 2, 0.1, a, b, c, d, 2, None) == -1 and b"kind" in L.stg_last_error()
+    assert force(h, 2, 0.1, a, b, c, c, 1, None) == -1 and b"alias" in L.stg_last_error()
+    assert force(h, 2, 0.1, a, None, c, d, 1, None) == -1
+    assert force(h, 2, -0.51, a, b, c, d, 1, None) == -1
+    L.stg_lattice_destroy(h)
+
+
 def test_status_strings(L):
     for s in (0, -1, -2, -3, -4, -5, -6, 99):
         assert L.stg_status_string(s)

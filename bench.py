@@ -457,6 +457,50 @@ def run_gpu(args):
     return 0
 
 
+def run_case(name):
+    """One small workload for a profiler to capture (no timing, no JSON line): `mscg` runs two mixed
+    FP32-inner solves of the 32^4 msCG workload; `force32` three double-single D_eo applications and
+    one 4-shift fermion force at 32^4; `stout24` one stout step and its chain rule at 24^4."""
+    import torch
+    import paper_1801_01473_gb300 as p
+    if name == "mscg":
+        cfg = S.CONFIGS["mscg_32x32x32x32"]
+        dims = cfg["dims"]
+        lat = p.Lattice(dims)
+        ut = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
+        b = torch.from_numpy(S.gaussian_field(dims, 2000 + cfg["k"])).cuda()
+        g64, gi = p.Gauge(lat, ut, "f64", 18), p.Gauge(lat, ut, "f32", 12)
+        for _ in range(2):
+            x, st = p.mscg(g64, b, cfg["shifts"](), cfg["mass"], tol=1e-10, g_inner=gi)
+        print("mscg", st["iters"], st["refine_iters"], max(st["true_resid"]))
+    elif name == "force32":
+        dims = (32, 32, 32, 32)
+        lat = p.Lattice(dims)
+        ut = torch.from_numpy(S.gauge_links(dims, "expih", 1002)).cuda()
+        g64, gds = p.Gauge(lat, ut, "f64", 18), p.Gauge(lat, ut, "ds", 18)
+        x = p.pack(lat, torch.from_numpy(S.gaussian_field(dims, 2002)).cuda(), "ds")
+        y = torch.empty_like(x)
+        for _ in range(3):
+            p.dslash_eo_(gds, y, x)
+        gen = torch.Generator(device="cuda").manual_seed(2002)
+        xs = torch.randn((4, lat.Vh, 3), dtype=torch.complex128, device="cuda", generator=gen)
+        f = p.fermion_force(g64, [0.5, 0.4, 0.3, 0.2], xs)
+        print("force32", float(f.abs().max()))
+    elif name == "stout24":
+        dims = (24, 24, 24, 24)
+        lat = p.Lattice(dims)
+        ut = torch.from_numpy(S.gauge_links(dims, "expih", 1005)).cuda()
+        levels = p.stout_smear(lat, ut, 0.15, 1)
+        gen = torch.Generator(device="cuda").manual_seed(3005)
+        z = torch.randn(ut.shape, dtype=torch.complex128, device="cuda", generator=gen)
+        g = p.stout_force(lat, ut, levels, 0.15, z, kind=1)
+        print("stout24", float(g.abs().max()))
+    else:
+        raise SystemExit(f"unknown case {name}")
+    torch.cuda.synchronize()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -465,7 +509,11 @@ def main():
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--impl", default="stg", choices=["stg", "reference"])
     ap.add_argument("--no-extras", action="store_true")
+    ap.add_argument("--case", default=None, choices=["mscg", "force32", "stout24"],
+                    help="run one small workload for a profiler instead of the benchmark")
     args = ap.parse_args()
+    if args.case:
+        return run_case(args.case)
     if args.impl == "reference":
         return run_reference(args)
     return run_gpu(args)

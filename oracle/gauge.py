@@ -124,3 +124,52 @@ def force(dims, links, beta: float, c0: float = C_PLAQ, c1: float = C_RECT) -> n
     """F = TA(U G^dag) per link, [4][V][3][3]."""
     u = np.asarray(links, dtype=np.complex128).reshape(4, -1, 3, 3)
     return _ta(u @ _dag(gradient(dims, links, beta, c0, c1)))
+
+
+def _site_step(dims, site: int, d: int, step: int) -> int:
+    c = [site % dims[0], (site // dims[0]) % dims[1], (site // (dims[0] * dims[1])) % dims[2],
+         site // (dims[0] * dims[1] * dims[2])]
+    c[d] = (c[d] + step) % dims[d]
+    return c[0] + dims[0] * (c[1] + dims[1] * (c[2] + dims[2] * c[3]))
+
+
+def link_gradient(dims, links, beta: float, mu: int, site: int) -> np.ndarray:
+    """G_mu(site) alone (for sampled checks on lattices too large for `gradient`): every loop of
+    the action that passes through the link, walked site by site, contributes its rest B^dag (or
+    B for a daggered passage), as in `gradient`."""
+    u = np.asarray(links).reshape(4, -1, 3, 3)
+    g = np.zeros((3, 3), np.complex128)
+    for a in range(4):
+        for b in range(4):
+            if a == b:
+                continue
+            for c, path in loops(a, b):
+                n = len(path)
+                # every base point whose loop uses the link: walk the path from each candidate
+                # base y = site - (offset of step k), k over the steps along mu
+                for k in range(n):
+                    d, s = path[k]
+                    if d != mu:
+                        continue
+                    off = np.zeros(4, dtype=int)
+                    for j in range(k):
+                        off[path[j][0]] += path[j][1]
+                    if s < 0:
+                        off[d] -= 1  # a -mu step uses U_mu at (position - mu)
+                    y = site
+                    for e in range(4):
+                        y = _site_step(dims, y, e, -int(off[e]))
+                    # factors of the loop based at y
+                    facs, pos = [], y
+                    for dd, ss in path:
+                        if ss > 0:
+                            facs.append(u[dd, pos])
+                            pos = _site_step(dims, pos, dd, 1)
+                        else:
+                            pos = _site_step(dims, pos, dd, -1)
+                            facs.append(u[dd, pos].conj().T)
+                    rest = np.eye(3, dtype=np.complex128)
+                    for j in list(range(k + 1, n)) + list(range(k)):
+                        rest = rest @ facs[j]
+                    g += (-beta / 3.0 * c) * (rest if s < 0 else rest.conj().T)
+    return g

@@ -87,3 +87,10 @@ def test_gradient_finite_differences(links, direction):
     if direction == "algebra":
         f = og.force(DIMS, links, BETA)
         assert np.einsum("lsab,lsba->", x, f).real == pytest.approx(fd, rel=1e-8)
+
+
+def test_link_gradient_matches_whole_lattice(links):
+    g = og.gradient(DIMS, links, BETA)
+    v = links.shape[1]
+    for mu, s in [(0, 0), (1, 5), (2, v - 1), (3, 77), (0, 143)]:
+        assert np.abs(og.link_gradient(DIMS, links, BETA, mu, s) - g[mu, s]).max() < 1e-12

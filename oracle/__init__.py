@@ -191,3 +191,20 @@ def action(residues, b, x) -> float:
     """S = sum_i r_i Re(b^dag x_i)."""
     b = np.asarray(b).reshape(-1)
     return float(sum(r * np.vdot(b, np.asarray(xi).reshape(-1)).real for r, xi in zip(residues, x)))
+
+
+def u1_links(links, theta) -> np.ndarray:
+    """Links times their U(1) phases: exp(i theta_mu(x)) U_mu(x), theta [4][V] in radians (the
+    per-flavour phase field u_mu = exp(i theta_mu) of Sec. 4.1, on top of the staggered signs)."""
+    return _c128(links).reshape(4, -1, 3, 3) * np.exp(1j * np.asarray(theta, dtype=np.float64))[..., None, None]
+
+
+def force_u1(dims, links, theta, residues, x, kind: int = 0, antiperiodic: bool = True) -> np.ndarray:
+    """Fermion force with respect to U when D uses exp(i theta) U: kind 0 -> TA(U W) (equal to the
+    force of the phased links V = exp(i theta) U), kind 1 -> dS/dRe U + i dS/dIm U =
+    exp(-i theta) times the gradient with respect to V (V = exp(i theta) U, dV = exp(i theta) dU)."""
+    v = u1_links(links, theta)
+    f = force(dims, v, residues, x, kind=kind, antiperiodic=antiperiodic)
+    if kind == 1:
+        f = f * np.exp(-1j * np.asarray(theta, dtype=np.float64))[..., None, None]
+    return f

@@ -218,9 +218,11 @@ def time_deo_sweep(torch, p, dims, reps=50):
     psi = torch.from_numpy(S.gaussian_field(dims, 2000 + 2)).cuda()
     flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
     out = []
-    for prec, recon in [("f64", 18), ("f64", 12), ("ds", 18), ("ds", 12), ("f32", 18), ("f32", 12), ("f16", 12),
-                        ("bf16", 12)]:
-        g = p.Gauge(lat, ut, prec, recon)
+    theta = torch.from_numpy(np.random.default_rng(4000 + 2).uniform(-np.pi, np.pi, (4, lat.V))).cuda()
+    for prec, recon, u1 in [("f64", 18, False), ("f64", 12, False), ("ds", 18, False), ("ds", 12, False),
+                            ("f32", 18, False), ("f32", 12, False), ("f16", 12, False), ("bf16", 12, False),
+                            ("f64", 18, True), ("ds", 18, True), ("f32", 12, True), ("f16", 12, True)]:
+        g = p.Gauge(lat, ut, prec, recon, theta=theta if u1 else None)
         x = p.pack(lat, psi, g.vec_prec)
         y = torch.empty_like(x)
         for _ in range(5):
@@ -235,9 +237,10 @@ def time_deo_sweep(torch, p, dims, reps=50):
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1) * 1e-3)
         t = float(np.median(ts))
-        byt = bytes_per_site(prec, recon) * lat.Vh
-        out.append({"lattice": "x".join(map(str, dims)), "links": f"{prec}-{recon}", "us": round(t * 1e6, 2),
-                    "GBs": round(byt / t / 1e9, 1)})
+        # a U(1) phase field adds one stored angle per link (double for f64/ds, float otherwise)
+        byt = (bytes_per_site(prec, recon) + (8 * (8 if prec in ("f64", "ds") else 4) if u1 else 0)) * lat.Vh
+        out.append({"lattice": "x".join(map(str, dims)), "links": f"{prec}-{recon}" + ("+u1" if u1 else ""),
+                    "us": round(t * 1e6, 2), "GBs": round(byt / t / 1e9, 1)})
         del g
     return out
 
@@ -367,6 +370,40 @@ def time_stout(torch, p):
             "note": "FP64, canonical link layout; flops algorithmic (216 per complex 3x3 product)"}
 
 
+# Tree-level Symanzik gauge force: 6 plaquette + 18 rectangle staples per link = 84 complex 3x3
+# products; action: per site and plane one plaquette and two rectangles = 10 products + 3 traces.
+GAUGE_FORCE_FLOPS = 84 * 216
+GAUGE_ACTION_FLOPS = 6 * (10 * 216 + 3 * 36)
+
+
+def time_gauge(torch, p):
+    cfg = S.CONFIGS["force_48x48x48x48"]
+    dims = cfg["dims"]
+    lat = p.Lattice(dims)
+    ut = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
+    beta = 5.6
+    f = p.gauge_force(lat, ut, beta, kind=0)
+    p.gauge_action(lat, ut, beta)
+    torch.cuda.synchronize()
+    e0, e1, e2 = events(torch) + (torch.cuda.Event(enable_timing=True),)
+    e0.record()
+    for _ in range(3):
+        f = p.gauge_force(lat, ut, beta, kind=0)
+    e1.record()
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
+    for _ in range(3):
+        p.lib().stg_gauge_action(lat.handle, beta, ut.data_ptr(), out.data_ptr(),
+                                 torch.cuda.current_stream().cuda_stream)
+    e2.record()
+    torch.cuda.synchronize()
+    t_f, t_a = e0.elapsed_time(e1) / 3, e1.elapsed_time(e2) / 3
+    del f, ut
+    return {"lattice": "48^4", "force_ms": round(t_f, 3), "action_ms": round(t_a, 3),
+            "force_fp64_tflops": round(4 * lat.V * GAUGE_FORCE_FLOPS / t_f / 1e9, 3),
+            "action_fp64_tflops": round(lat.V * GAUGE_ACTION_FLOPS / t_a / 1e9, 3),
+            "note": "tree-level Symanzik, FP64, canonical link layout; flops algorithmic"}
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = dist_env()
@@ -448,6 +485,7 @@ def run_gpu(args):
         line["batched"] = time_batched(torch, p)
         line["force"] = time_force(torch, p)
         line["stout"] = time_stout(torch, p)
+        line["gauge"] = time_gauge(torch, p)
         line["cpu_baseline"] = cpu_baseline()
     if ws > 1:
         torch.distributed.barrier()
@@ -460,7 +498,8 @@ def run_gpu(args):
 def run_case(name):
     """One small workload for a profiler to capture (no timing, no JSON line): `mscg` runs two mixed
     FP32-inner solves of the 32^4 msCG workload; `force32` three double-single D_eo applications and
-    one 4-shift fermion force at 32^4; `stout24` one stout step and its chain rule at 24^4."""
+    one 4-shift fermion force at 32^4; `stout24` one stout step and its chain rule at 24^4;
+    `gauge24` the gauge force and action at 24^4."""
     import torch
     import paper_1801_01473_gb300 as p
     if name == "mscg":
@@ -495,6 +534,12 @@ def run_case(name):
         z = torch.randn(ut.shape, dtype=torch.complex128, device="cuda", generator=gen)
         g = p.stout_force(lat, ut, levels, 0.15, z, kind=1)
         print("stout24", float(g.abs().max()))
+    elif name == "gauge24":
+        dims = (24, 24, 24, 24)
+        lat = p.Lattice(dims)
+        ut = torch.from_numpy(S.gauge_links(dims, "expih", 1005)).cuda()
+        f = p.gauge_force(lat, ut, 5.6, kind=0)
+        print("gauge24", p.gauge_action(lat, ut, 5.6)["action"], float(f.abs().max()))
     else:
         raise SystemExit(f"unknown case {name}")
     torch.cuda.synchronize()
@@ -509,7 +554,7 @@ def main():
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--impl", default="stg", choices=["stg", "reference"])
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--case", default=None, choices=["mscg", "force32", "stout24"],
+    ap.add_argument("--case", default=None, choices=["mscg", "force32", "stout24", "gauge24"],
                     help="run one small workload for a profiler instead of the benchmark")
     args = ap.parse_args()
     if args.case:

@@ -8,7 +8,10 @@
  *     r3 = (r1 x r2)^* (Sec. 4.1);
  *   - the shifted normal operator  A_sigma = m^2 + sigma - D_eo D_oe  (Eq. shift_eo);
  *   - the multi-shift CG solve of A_sigma_i x_i = b for all poles sigma_i (Sec. 2);
- *   - the fermion force of S = sum_i r_i Re(b^dag x_i) with respect to the links.
+ *   - the fermion force of S = sum_i r_i Re(b^dag x_i) with respect to the links;
+ *   - the k-times stout smearing of the links that D uses, and the chain rule that maps a
+ *     force on the smeared links back to the unsmeared ones (Sec. 2-3);
+ *   - the tree-level Symanzik gauge action and its force (Sec. 2-3).
  *
  * Conventions.
  *   site      i = x + Lx*(y + Ly*(z + Lz*t)), mu = 0..3 = x, y, z, t; all extents even.
@@ -96,6 +99,15 @@ int64_t stg_lattice_sites(const stg_lattice *lat, int32_t parity);
  * `stream` is.  The lattice must outlive the gauge. */
 stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, stg_prec prec, stg_recon recon,
                             void *stream, stg_gauge **out);
+/* As stg_gauge_create, with a U(1) phase field: theta_dev (device, FP64, canonical [4][V], radians)
+ * gives every link the phase u = exp(i theta_mu(x)) on top of the staggered and boundary signs,
+ * so that D uses exp(i theta) U forward and exp(-i theta) U^dag backward (Sec. 4.1: imaginary
+ * chemical potential and background fields as a per-flavour U(1) field).  The angles are stored
+ * beside the links (float for F32/BF16/F16 links, double for F64 and DS) and turned into
+ * cos + i sin on line; 12-real compression applies to the SU(3) part only.  Every operation
+ * accepts such a gauge; the solvers need the inner gauge to carry the same phases. */
+stg_status stg_gauge_create_u1(const stg_lattice *lat, const void *links_c128_dev, const double *theta_dev,
+                               stg_prec prec, stg_recon recon, void *stream, stg_gauge **out);
 void stg_gauge_destroy(stg_gauge *g);
 /* Bytes of the internal link copy (4 V links). */
 size_t stg_gauge_bytes(const stg_gauge *g);
@@ -259,6 +271,47 @@ stg_status stg_stout_smear(const stg_lattice *lat, int32_t nstep, double rho, co
 stg_status stg_stout_force(const stg_lattice *lat, int32_t nstep, double rho, const void *links_c128_dev,
                            const void *levels_c128_dev, const void *grad_c128_dev, void *out_c128_dev,
                            int32_t kind, void *stream);
+
+/* ---- gauge action and force --------------------------------------------------------------------- */
+
+/* Tree-level Symanzik gauge action of the unsmeared links (Sec. 2; its force is the gauge term of the
+ * MD force, Sec. 3), links periodic in all four directions:
+ *   S_g = -(beta/3) sum_x sum_{mu != nu} [ 5/6 Re tr P_{mu nu}(x) - 1/12 Re tr R_{mu nu}(x) ]
+ *   P_{mu nu}(x) = U_mu(x) U_nu(x+mu) U_mu(x+nu)^dag U_nu(x)^dag                     (1x1 plaquette)
+ *   R_{mu nu}(x) = U_mu(x) U_mu(x+mu) U_nu(x+2mu) U_mu(x+mu+nu)^dag U_mu(x+nu)^dag U_nu(x)^dag  (2x1)
+ * out3_dev (device, 3 doubles, written): S_g, the plaquette sum sum_{x, mu<nu} Re tr P (each
+ * plaquette once) and the rectangle sum sum_{x, mu!=nu} Re tr R (each rectangle once).  The block
+ * partial sums are added in a fixed order (bitwise reproducible).  FP64.  Allocates
+ * 16 bytes per 128 sites from the stream-ordered allocator; async on `stream`. */
+stg_status stg_gauge_action(const stg_lattice *lat, double beta, const void *links_c128_dev, double *out3_dev,
+                            void *stream);
+
+/* Gradient of S_g per link: G = dS_g/dRe U + i dS_g/dIm U = -(beta/3) sum c B^dag over the loops
+ * through the link (B = the rest of the loop after the link; 2 plaquettes and 6 rectangles per
+ * other direction), written as kind 1: G, or kind 0: F = TA(U G^dag) (dS/deps = tr(X F) along
+ * U -> exp(eps X) U).  links_c128_dev / out_c128_dev: canonical complex128 [4][V][3][3] (device),
+ * no aliasing.  FP64; async on `stream`. */
+stg_status stg_gauge_force(const stg_lattice *lat, double beta, const void *links_c128_dev, void *out_c128_dev,
+                           int32_t kind, void *stream);
+
+/* ---- molecular dynamics (Sec. 2-3) ----------------------------------------------------------------- */
+/* The MD evolves links U and momenta H (traceless Hermitian, one per link) under
+ * (1/2) sum tr H^2 + S(U):  U' = i H U,  H' = -i F  with F = TA(U G^dag) the Lie-algebra force of S
+ * (stg_gauge_force / stg_stout_force / stg_fermion_force kind 0 format).  All arrays canonical
+ * complex128 [4][V][3][3] (device, 16-byte aligned); FP64; async on `stream`. */
+
+/* Momentum heatbath from caller-drawn standard normal numbers xi_dev [4][V][8] (FP64, device):
+ * H = sum_a xi_a lambda_a / sqrt(2) (Gell-Mann matrices), so (1/2) tr H^2 = (1/2) sum_a xi_a^2. */
+stg_status stg_md_momenta(const stg_lattice *lat, const double *xi_dev, void *mom_c128_dev, void *stream);
+/* U <- exp(i eps H) U for every link (exp by the Cayley-Hamilton series, as in stg_stout_smear);
+ * |eps| <= 1; momenta and links must not alias. */
+stg_status stg_md_update_links(const stg_lattice *lat, double eps, const void *mom_c128_dev, void *links_c128_dev,
+                               void *stream);
+/* H <- H - eps i F for every link. */
+stg_status stg_md_update_momenta(const stg_lattice *lat, double eps, const void *force_c128_dev, void *mom_c128_dev,
+                                 void *stream);
+/* *out_dev (one device double) = (1/2) sum_links tr H^2, summed in a fixed order. */
+stg_status stg_md_kinetic(const stg_lattice *lat, const void *mom_c128_dev, double *out_dev, void *stream);
 
 #ifdef __cplusplus
 }

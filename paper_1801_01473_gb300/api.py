@@ -72,15 +72,22 @@ class Lattice:
 
 
 class Gauge:
-    """Library-owned copy of the links at precision prec ('f64', 'f32', 'bf16', 'f16'),
-    18-real or 12-real (recon=12: rows 1, 2 stored, row 3 rebuilt)."""
+    """Library-owned copy of the links at precision prec ('f64', 'f32', 'bf16', 'f16', 'ds'),
+    18-real or 12-real (recon=12: rows 1, 2 stored, row 3 rebuilt); theta [4, V] float64 (optional)
+    attaches a U(1) phase field exp(i theta) to the links."""
 
-    def __init__(self, lattice: Lattice, links: torch.Tensor, prec: str = "f64", recon: int = 18, stream=None):
+    def __init__(self, lattice: Lattice, links: torch.Tensor, prec: str = "f64", recon: int = 18, stream=None,
+                 theta: torch.Tensor | None = None):
         links = _dev(links).reshape(4, lattice.V, 3, 3)
         h = ctypes.c_void_p()
-        check(lib().stg_gauge_create(lattice.handle, _ptr(links), PREC[prec],
-                                     STG_RECON12 if recon == 12 else STG_RECON18, _stream(stream), ctypes.byref(h)),
-              "stg_gauge_create")
+        rc = STG_RECON12 if recon == 12 else STG_RECON18
+        if theta is None:
+            check(lib().stg_gauge_create(lattice.handle, _ptr(links), PREC[prec], rc, _stream(stream), ctypes.byref(h)),
+                  "stg_gauge_create")
+        else:
+            th = _dev(theta, torch.float64).reshape(4, lattice.V)
+            check(lib().stg_gauge_create_u1(lattice.handle, _ptr(links), _ptr(th), PREC[prec], rc, _stream(stream),
+                                            ctypes.byref(h)), "stg_gauge_create_u1")
         torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
         self._h = h
         self.lattice = lattice
@@ -322,3 +329,52 @@ def stout_force(lattice: Lattice, links: torch.Tensor, levels: torch.Tensor, rho
     check(lib().stg_stout_force(lattice.handle, nstep, float(rho), _ptr(u), _ptr(lv), _ptr(gr), _ptr(out), int(kind),
                                 _stream(stream)), "stg_stout_force")
     return out
+
+
+def gauge_action(lattice: Lattice, links: torch.Tensor, beta: float, stream=None) -> dict:
+    """Tree-level Symanzik S_g of the links [4, V, 3, 3] complex128, with the plaquette sum (each
+    plaquette once) and the rectangle sum (each 2x1 rectangle once).  Synchronises to read them."""
+    u = _dev(links).reshape(4, lattice.V, 3, 3)
+    out = torch.empty(3, dtype=torch.float64, device="cuda")
+    check(lib().stg_gauge_action(lattice.handle, float(beta), _ptr(u), _ptr(out), _stream(stream)), "stg_gauge_action")
+    s, p, r = _to_host(out).tolist()
+    return {"action": s, "plaquette_sum": p, "rectangle_sum": r}
+
+
+def gauge_force(lattice: Lattice, links: torch.Tensor, beta: float, kind: int = 0, stream=None) -> torch.Tensor:
+    """Per-link gradient of S_g [4, V, 3, 3] complex128: kind 1 -> dS/dRe U + i dS/dIm U,
+    kind 0 -> TA(U G^dag) (Lie-algebra force)."""
+    u = _dev(links).reshape(4, lattice.V, 3, 3)
+    out = torch.empty((4, lattice.V, 3, 3), dtype=torch.complex128, device="cuda")
+    check(lib().stg_gauge_force(lattice.handle, float(beta), _ptr(u), _ptr(out), int(kind), _stream(stream)),
+          "stg_gauge_force")
+    return out
+
+
+def md_momenta(lattice: Lattice, xi: torch.Tensor, stream=None) -> torch.Tensor:
+    """Momenta H [4, V, 3, 3] from standard normal numbers xi [4, V, 8] (float64)."""
+    x = _dev(xi, torch.float64).reshape(4, lattice.V, 8)
+    out = torch.empty((4, lattice.V, 3, 3), dtype=torch.complex128, device="cuda")
+    check(lib().stg_md_momenta(lattice.handle, _ptr(x), _ptr(out), _stream(stream)), "stg_md_momenta")
+    return out
+
+
+def md_update_links_(lattice: Lattice, eps: float, mom: torch.Tensor, links: torch.Tensor, stream=None) -> torch.Tensor:
+    """links <- exp(i eps H) links, in place (complex128 [4, V, 3, 3] on cuda)."""
+    check(lib().stg_md_update_links(lattice.handle, float(eps), _ptr(mom), _ptr(links), _stream(stream)),
+          "stg_md_update_links")
+    return links
+
+
+def md_update_momenta_(lattice: Lattice, eps: float, force: torch.Tensor, mom: torch.Tensor, stream=None) -> torch.Tensor:
+    """mom <- mom - eps i F, in place (F: Lie-algebra force, kind 0 format)."""
+    check(lib().stg_md_update_momenta(lattice.handle, float(eps), _ptr(force), _ptr(mom), _stream(stream)),
+          "stg_md_update_momenta")
+    return mom
+
+
+def md_kinetic(lattice: Lattice, mom: torch.Tensor, stream=None) -> float:
+    """(1/2) sum tr H^2 (synchronises to read it)."""
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    check(lib().stg_md_kinetic(lattice.handle, _ptr(mom), _ptr(out), _stream(stream)), "stg_md_kinetic")
+    return float(_to_host(out)[0])

@@ -7,7 +7,8 @@
 //     z even:  W = + sum_i r_i u_mu(z) y_i(z+mu) x_i(z)^dag
 //     z odd :  W = - sum_i r_i u_mu(z) x_i(z+mu) y_i(z)^dag
 // Output kind 0: F = TA(U W) (traceless anti-Hermitian; dS/deps = tr(X F) along U -> exp(eps X) U);
-// kind 1: W^dag (dS/dRe U + i dS/dIm U).
+// kind 1: W^dag (dS/dRe U + i dS/dIm U).  With a U(1) phase field u carries exp(i theta) as well
+// (D uses u U and its adjoint), and U is the SU(3) link without the phase.
 //
 // Work split: y_i = D_oe x_i for all shifts by the multi-rhs D kernel on the double-single copy of
 // the links (link loads shared; 48-bit significand, ~3x the FP64 operator's speed on GB300); then
@@ -64,11 +65,15 @@ __global__ void __launch_bounds__(kForceBlock) k_force(const __grid_constant__ F
 #pragma unroll
                 for (int c = 0; c < 3; ++c) cmac_conj(W[r][c], g[c], f[r]);  // W_rc += f_r conj(g_c)
         }
+        // u = sign * exp(i theta) (theta = 0 without a phase field)
         const double sign = par == 0 ? u : -u;
+        const void *blk = link_block<LinkT>(a.links, Vh, mu, par);
+        cx<double> ph = LinkTraits<LinkT>::phase(blk, Vh, h);
+        ph = cx<double>{sign * ph.re, sign * ph.im};
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) W[r][c] = cx<double>{sign * W[r][c].re, sign * W[r][c].im};
+            for (int c = 0; c < 3; ++c) W[r][c] = cmul(ph, W[r][c]);
         double2 *o = a.out + ((long long)mu * V + s.i) * 9;
         if (a.kind == 1) {
 #pragma unroll
@@ -78,7 +83,7 @@ __global__ void __launch_bounds__(kForceBlock) k_force(const __grid_constant__ F
             continue;
         }
         cx<double> U[3][3];
-        LinkT::load(link_block<LinkT>(a.links, Vh, mu, par), Vh, h, U);
+        LinkTraits<LinkT>::Base::load(blk, Vh, h, U);  // the SU(3) link, without its phase
         cx<double> Z[3][3];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
@@ -220,10 +225,12 @@ extern "C" stg_status stg_fermion_force(const stg_gauge *g, int32_t nshift, cons
     k_ds_to_f64_scaled<<<dim3((Vh + 255) / 256, nshift), 256, 0, st>>>(Vh, a.y[0], fb, rs);
     STG_CUDA_TRY(cudaGetLastError());
     dim3 grid((Vh + kForceBlock - 1) / kForceBlock, 2);
-    if (g->kind == kF64R18)
-        k_force<LinkF64R18><<<grid, kForceBlock, 0, st>>>(a);
-    else
-        k_force<LinkF64R12><<<grid, kForceBlock, 0, st>>>(a);
+    switch (g->kind) {
+    case kF64R18: k_force<LinkF64R18><<<grid, kForceBlock, 0, st>>>(a); break;
+    case kF64R12: k_force<LinkF64R12><<<grid, kForceBlock, 0, st>>>(a); break;
+    case kF64R18 | kU1: k_force<LinkU1<LinkF64R18, double>><<<grid, kForceBlock, 0, st>>>(a); break;
+    default: k_force<LinkU1<LinkF64R12, double>><<<grid, kForceBlock, 0, st>>>(a); break;
+    }
     STG_CUDA_TRY(cudaGetLastError());
     return STG_OK;
 }

@@ -618,7 +618,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     const int kind_i = ii[0].gi->kind, kind_64 = ii[0].g64->kind;
     // 16-bit links are too coarse for the refinement to converge on ill-conditioned shifts
     // (their rounding error times the condition number exceeds one): refine on FP32 links.
-    const bool refine_f32 = kind_i == kBF16R12 || kind_i == kF16R12;
+    const bool refine_f32 = base_kind(kind_i) == kBF16R12 || base_kind(kind_i) == kF16R12;
     if (refine_f32)
         for (int k = 0; k < ninst; ++k) {
             stg_status s = f32_companion(ii[k].g64, user_st, &ii[k].gr);
@@ -638,7 +638,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     // iterated 1e-9 costs fewer iterations than it saves in refinement; reliable updates every
     // two decades keep the FP32 recurrences well inside their accuracy
     const double inner_tol = mixed ? (prm->inner_tol > 0 ? prm->inner_tol
-                                                          : (kind_i == kBF16R12 || kind_i == kF16R12 ? 1e-4 : 1e-9))
+                                                          : (base_kind(kind_i) == kBF16R12 || base_kind(kind_i) == kF16R12 ? 1e-4 : 1e-9))
                                    : prm->tol;
     const double delta = prm->reliable_delta > 0 ? prm->reliable_delta : 0.01;
     const int vb = Field<R>::kBytesPerSite;

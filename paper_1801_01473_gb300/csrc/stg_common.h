@@ -14,16 +14,24 @@ namespace stg {
 
 // Link storage kinds (precision x compression); index of the dslash instantiation.
 enum LinkKind { kF64R18 = 0, kF64R12 = 1, kF32R18 = 2, kF32R12 = 3, kBF16R12 = 4, kF16R12 = 5, kDSR18 = 6, kDSR12 = 7 };
+// flag on a kind: the links carry a U(1) phase field theta (LinkU1 layout)
+constexpr int kU1 = 8;
+inline int base_kind(int kind) { return kind & 7; }
+inline bool kind_has_u1(int kind) { return (kind & kU1) != 0; }
 
 int link_bytes(int kind);
-inline bool kind_is_f64(int kind) { return kind == kF64R18 || kind == kF64R12; }
-inline bool kind_is_ds(int kind) { return kind == kDSR18 || kind == kDSR12; }
+inline bool kind_is_f64(int kind) { return base_kind(kind) == kF64R18 || base_kind(kind) == kF64R12; }
+inline bool kind_is_ds(int kind) { return base_kind(kind) == kDSR18 || base_kind(kind) == kDSR12; }
+// bytes of one phase angle: double for FP64 and double-single links, float otherwise
+inline int theta_bytes(int kind) { return kind_is_f64(kind) || kind_is_ds(kind) ? 8 : 4; }
 // bytes per site of the fields a gauge of this kind works on
 inline int kind_vec_bytes(int kind) { return kind_is_f64(kind) || kind_is_ds(kind) ? 48 : 24; }
 
 // Launchers, one per storage kind, implemented in dslash_f64.cu / dslash_f32.cu / dslash_h16.cu;
 // `bs` is the thread-block size (64, 128 or 256).
 cudaError_t launch_dslash_f64r18(const DArgs &a, int mode, int bs, cudaStream_t st);
+// links with a U(1) phase field, one right-hand side per group (dslash_u1.cu)
+cudaError_t launch_dslash_u1(int kind, const DArgs &a, int mode, int bs, cudaStream_t st);
 cudaError_t launch_dslash_f64r12(const DArgs &a, int mode, int bs, cudaStream_t st);
 cudaError_t launch_dslash_f32r18(const DArgs &a, int mode, int bs, cudaStream_t st);
 cudaError_t launch_dslash_f32r12(const DArgs &a, int mode, int bs, cudaStream_t st);

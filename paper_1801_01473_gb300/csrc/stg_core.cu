@@ -29,6 +29,10 @@ stg_status cuda_error(cudaError_t e, const char *where)
 
 int link_bytes(int kind)
 {
+    if (kind_has_u1(kind)) {
+        const int b = link_bytes(base_kind(kind));
+        return b ? b + theta_bytes(kind) : 0;
+    }
     switch (kind) {
     case kF64R18: return LinkF64R18::kBytes;
     case kF64R12: return LinkF64R12::kBytes;
@@ -44,6 +48,7 @@ int link_bytes(int kind)
 
 cudaError_t launch_dslash_bs(int kind, const DArgs &a, int mode, int bs, cudaStream_t st)
 {
+    if (kind_has_u1(kind)) return launch_dslash_u1(kind, a, mode, bs, st);
     switch (kind) {
     case kF64R18: return launch_dslash_f64r18(a, mode, bs, st);
     case kF64R12: return launch_dslash_f64r12(a, mode, bs, st);
@@ -81,12 +86,13 @@ static cudaError_t launch_dslash_tuned(int kind, const DArgs &a, int mode, cudaS
 
 // Double-single D is bound by the FP32 pipes, not by link traffic: several right-hand sides per
 // thread only cost registers and occupancy (measured: 4 rhs per thread run at half the per-rhs
-// speed of 1).  Its multi-rhs launches are therefore split into one-rhs groups.
+// speed of 1).  Its multi-rhs launches are therefore split into one-rhs groups, and so are those
+// of links with a U(1) phase field (instantiated for one rhs only).
 cudaError_t launch_dslash(int kind, const DArgs &a, int mode, cudaStream_t st)
 {
     int maxv, maxr;
     dslash_extent(a, maxv, maxr);
-    if (!kind_is_ds(kind) || maxr <= 1) return launch_dslash_tuned(kind, a, mode, st);
+    if ((!kind_is_ds(kind) && !kind_has_u1(kind)) || maxr <= 1) return launch_dslash_tuned(kind, a, mode, st);
     DArgs b;
     memset(&b, 0, sizeof(b));
     b.out_par = a.out_par;
@@ -199,6 +205,51 @@ static cudaError_t pack_links_t(const Geom &g, const void *canon, void *links, c
     return cudaGetLastError();
 }
 
+// canonical angles theta [4][V] (FP64) -> the theta chunk of every (mu, parity) block of a LinkU1 layout
+template <typename LinkT>
+__global__ void k_pack_theta(Geom g, const double *__restrict__ theta, void *__restrict__ links)
+{
+    using T = typename LinkT::Theta;
+    long long V = 2LL * g.Vh;
+    long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+    if (tid >= 4 * V) return;
+    int mu = (int)(tid / V);
+    int i = (int)(tid - (long long)mu * V);
+    int x = i % g.L[0], r = i / g.L[0];
+    int y = r % g.L[1], r2 = r / g.L[1];
+    int z = r2 % g.L[2], t = r2 / g.L[2];
+    int par = (x + y + z + t) & 1;
+    char *blk = static_cast<char *>(links) + (size_t)(mu * 2 + par) * g.Vh * LinkT::kBytes;
+    T *th = reinterpret_cast<T *>(blk + (size_t)LinkT::BaseLink::kBytes * g.Vh);
+    th[i >> 1] = (T)theta[tid];
+}
+
+template <typename LinkT>
+static cudaError_t pack_u1_t(const Geom &g, const void *canon, const double *theta, void *links, cudaStream_t st)
+{
+    cudaError_t e = pack_links_t<LinkT>(g, canon, links, st);
+    if (e != cudaSuccess) return e;
+    long long n = 8LL * g.Vh;
+    k_pack_theta<LinkT><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g, theta, links);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_pack_links_u1(int kind, const Geom &g, const void *canon, const double *theta, void *links,
+                                 cudaStream_t st)
+{
+    switch (base_kind(kind)) {
+    case kF64R18: return pack_u1_t<LinkU1<LinkF64R18, double>>(g, canon, theta, links, st);
+    case kF64R12: return pack_u1_t<LinkU1<LinkF64R12, double>>(g, canon, theta, links, st);
+    case kF32R18: return pack_u1_t<LinkU1<LinkF32R18, float>>(g, canon, theta, links, st);
+    case kF32R12: return pack_u1_t<LinkU1<LinkF32R12, float>>(g, canon, theta, links, st);
+    case kBF16R12: return pack_u1_t<LinkU1<Link16R12<__nv_bfloat16>, float>>(g, canon, theta, links, st);
+    case kF16R12: return pack_u1_t<LinkU1<Link16R12<__half>, float>>(g, canon, theta, links, st);
+    case kDSR18: return pack_u1_t<LinkU1<LinkDSR18, double>>(g, canon, theta, links, st);
+    case kDSR12: return pack_u1_t<LinkU1<LinkDSR12, double>>(g, canon, theta, links, st);
+    }
+    return cudaErrorInvalidValue;
+}
+
 cudaError_t launch_pack_links(int kind, const Geom &g, const void *canon, void *links, cudaStream_t st)
 {
     switch (kind) {
@@ -214,33 +265,52 @@ cudaError_t launch_pack_links(int kind, const Geom &g, const void *canon, void *
     return cudaErrorInvalidValue;
 }
 
-// internal F64 links -> internal F32 12-real links (one thread per link)
-template <typename SrcT>
+// Phase chunk copy between two LinkU1 layouts (no-op for links without phases).
+template <typename SrcT, typename DstT>
+__device__ __forceinline__ void copy_theta(const char *sblk, char *dblk, int Vh, int h)
+{
+    if constexpr (LinkTraits<SrcT>::kU1) {
+        using SB = typename LinkTraits<SrcT>::Base;
+        using DB = typename LinkTraits<DstT>::Base;
+        const double th = (double)reinterpret_cast<const typename SrcT::Theta *>(sblk + (size_t)SB::kBytes * Vh)[h];
+        reinterpret_cast<typename DstT::Theta *>(dblk + (size_t)DB::kBytes * Vh)[h] = (typename DstT::Theta)th;
+    }
+}
+
+// internal F64 links -> internal F32 12-real links (one thread per link); phases copied as floats
+template <typename SrcT, typename DstT>
 __global__ void k_links_to_f32r12(Geom g, const void *__restrict__ src, void *__restrict__ dst)
 {
     const int Vh = g.Vh;
     long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= 8LL * Vh) return;
     const int blk = (int)(tid / Vh), h = (int)(tid - (long long)blk * Vh);
+    const char *sblk = static_cast<const char *>(src) + (size_t)blk * Vh * SrcT::kBytes;
+    char *dblk = static_cast<char *>(dst) + (size_t)blk * Vh * DstT::kBytes;
     cx<double> U[3][3];
-    SrcT::load(static_cast<const char *>(src) + (size_t)blk * Vh * SrcT::kBytes, Vh, h, U);
+    LinkTraits<SrcT>::Base::load(sblk, Vh, h, U);  // without the phase
     double2 m[9];
     for (int k = 0; k < 9; ++k) m[k] = make_double2(U[k / 3][k % 3].re, U[k / 3][k % 3].im);
-    LinkF32R12::pack(static_cast<char *>(dst) + (size_t)blk * Vh * LinkF32R12::kBytes, Vh, h, m);
+    LinkF32R12::pack(dblk, Vh, h, m);
+    copy_theta<SrcT, DstT>(sblk, dblk, Vh, h);
 }
 
-// internal F64 links -> internal double-single links of the same compression
+// internal F64 links -> internal double-single links of the same compression (and phases)
 template <typename SrcT, typename DstT>
 __global__ void k_links_to_ds(Geom g, const void *__restrict__ src, void *__restrict__ dst)
 {
+    using DB = typename LinkTraits<DstT>::Base;
     const int Vh = g.Vh;
     long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
     if (tid >= 8LL * Vh) return;
     const int blk = (int)(tid / Vh), h = (int)(tid - (long long)blk * Vh);
-    const double2 *p = reinterpret_cast<const double2 *>(static_cast<const char *>(src) + (size_t)blk * Vh * SrcT::kBytes);
+    const char *sblk = static_cast<const char *>(src) + (size_t)blk * Vh * SrcT::kBytes;
+    char *dblk = static_cast<char *>(dst) + (size_t)blk * Vh * DstT::kBytes;
+    const double2 *p = reinterpret_cast<const double2 *>(sblk);
     double2 m[9];
-    for (int k = 0; k < DstT::kBytes / 16; ++k) m[k] = p[(size_t)k * Vh + h];
-    DstT::pack(static_cast<char *>(dst) + (size_t)blk * Vh * DstT::kBytes, Vh, h, m);
+    for (int k = 0; k < DB::kBytes / 16; ++k) m[k] = p[(size_t)k * Vh + h];
+    DB::pack(dblk, Vh, h, m);
+    copy_theta<SrcT, DstT>(sblk, dblk, Vh, h);
 }
 
 static std::mutex g_companion_mu;
@@ -252,7 +322,7 @@ stg_status ds_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge *
         stg_gauge *g = new (std::nothrow) stg_gauge;
         if (!g) return set_error(STG_ERR_OOM, "ds_companion: host allocation");
         *g = *g64;
-        g->kind = g64->kind == kF64R18 ? kDSR18 : kDSR12;
+        g->kind = (base_kind(g64->kind) == kF64R18 ? kDSR18 : kDSR12) | (g64->kind & kU1);
         g->bytes = (size_t)4 * g64->lat->V * link_bytes(g->kind);
         g->scratch = nullptr;
         g->links = nullptr;
@@ -262,10 +332,19 @@ stg_status ds_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge *
         if (e == cudaSuccess) e = cudaMalloc(&g->scratch, g->scratch_count * sizeof(double));
         if (e == cudaSuccess) {
             long long n = 8LL * g->g.Vh;
-            if (g64->kind == kF64R18)
-                k_links_to_ds<LinkF64R18, LinkDSR18><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->g, g64->links, g->links);
-            else
-                k_links_to_ds<LinkF64R12, LinkDSR12><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->g, g64->links, g->links);
+            const unsigned nb = (unsigned)((n + 255) / 256);
+            switch (g64->kind) {
+            case kF64R18: k_links_to_ds<LinkF64R18, LinkDSR18><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
+            case kF64R12: k_links_to_ds<LinkF64R12, LinkDSR12><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
+            case kF64R18 | kU1:
+                k_links_to_ds<LinkU1<LinkF64R18, double>, LinkU1<LinkDSR18, double>><<<nb, 256, 0, st>>>(g->g, g64->links,
+                                                                                                      g->links);
+                break;
+            default:
+                k_links_to_ds<LinkU1<LinkF64R12, double>, LinkU1<LinkDSR12, double>><<<nb, 256, 0, st>>>(g->g, g64->links,
+                                                                                                      g->links);
+                break;
+            }
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) {
@@ -289,8 +368,8 @@ stg_status f32_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge 
         *g = *g64;
         g->prec = STG_F32;
         g->recon = STG_RECON12;
-        g->kind = kF32R12;
-        g->bytes = (size_t)4 * g64->lat->V * LinkF32R12::kBytes;
+        g->kind = kF32R12 | (g64->kind & kU1);
+        g->bytes = (size_t)4 * g64->lat->V * link_bytes(g->kind);
         g->scratch = nullptr;
         g->links = nullptr;
         g->f32_copy = nullptr;
@@ -299,10 +378,18 @@ stg_status f32_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge 
         if (e == cudaSuccess) e = cudaMalloc(&g->scratch, g->scratch_count * sizeof(double));
         if (e == cudaSuccess) {
             long long n = 8LL * g->g.Vh;
-            if (g64->kind == kF64R18)
-                k_links_to_f32r12<LinkF64R18><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->g, g64->links, g->links);
-            else
-                k_links_to_f32r12<LinkF64R12><<<(unsigned)((n + 255) / 256), 256, 0, st>>>(g->g, g64->links, g->links);
+            const unsigned nb = (unsigned)((n + 255) / 256);
+            using F32U = LinkU1<LinkF32R12, float>;
+            switch (g64->kind) {
+            case kF64R18: k_links_to_f32r12<LinkF64R18, LinkF32R12><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
+            case kF64R12: k_links_to_f32r12<LinkF64R12, LinkF32R12><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
+            case kF64R18 | kU1:
+                k_links_to_f32r12<LinkU1<LinkF64R18, double>, F32U><<<nb, 256, 0, st>>>(g->g, g64->links, g->links);
+                break;
+            default:
+                k_links_to_f32r12<LinkU1<LinkF64R12, double>, F32U><<<nb, 256, 0, st>>>(g->g, g64->links, g->links);
+                break;
+            }
             e = cudaGetLastError();
         }
         if (e != cudaSuccess) {
@@ -410,8 +497,8 @@ int64_t stg_lattice_sites(const stg_lattice *lat, int32_t parity)
     return -1;
 }
 
-stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, stg_prec prec, stg_recon recon,
-                            void *stream, stg_gauge **out)
+static stg_status gauge_create(const stg_lattice *lat, const void *links_c128_dev, const double *theta_dev,
+                               stg_prec prec, stg_recon recon, void *stream, stg_gauge **out)
 {
     if (!lat || !links_c128_dev || !out) return set_error(STG_ERR_ARG, "stg_gauge_create: null pointer");
     *out = nullptr;
@@ -427,6 +514,7 @@ stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, 
     default: break;
     }
     if (kind < 0) return set_error(STG_ERR_ARG, "stg_gauge_create: unsupported precision/compression pair");
+    if (theta_dev) kind |= kU1;
 
     stg_gauge *g = new (std::nothrow) stg_gauge;
     if (!g) return set_error(STG_ERR_OOM, "stg_gauge_create: host allocation");
@@ -443,7 +531,9 @@ stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, 
     g->scratch_count = (size_t)dslash_partials(lat->g.Vh);
     cudaError_t e = cudaMalloc(&g->links, g->bytes);
     if (e == cudaSuccess) e = cudaMalloc(&g->scratch, g->scratch_count * sizeof(double));
-    if (e == cudaSuccess) e = launch_pack_links(kind, lat->g, links_c128_dev, g->links, (cudaStream_t)stream);
+    if (e == cudaSuccess)
+        e = theta_dev ? launch_pack_links_u1(kind, lat->g, links_c128_dev, theta_dev, g->links, (cudaStream_t)stream)
+                      : launch_pack_links(kind, lat->g, links_c128_dev, g->links, (cudaStream_t)stream);
     if (e != cudaSuccess) {
         stg_status s = cuda_error(e, "stg_gauge_create");
         cudaFree(g->links);
@@ -453,6 +543,20 @@ stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, 
     }
     *out = g;
     return STG_OK;
+}
+
+stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, stg_prec prec, stg_recon recon,
+                            void *stream, stg_gauge **out)
+{
+    return gauge_create(lat, links_c128_dev, nullptr, prec, recon, stream, out);
+}
+
+stg_status stg_gauge_create_u1(const stg_lattice *lat, const void *links_c128_dev, const double *theta_dev, stg_prec prec,
+                               stg_recon recon, void *stream, stg_gauge **out)
+{
+    if (!theta_dev || (reinterpret_cast<uintptr_t>(theta_dev) & 7))
+        return set_error(STG_ERR_ARG, "stg_gauge_create_u1: theta must be non-null and 8-byte aligned");
+    return gauge_create(lat, links_c128_dev, theta_dev, prec, recon, stream, out);
 }
 
 void stg_gauge_destroy(stg_gauge *g)

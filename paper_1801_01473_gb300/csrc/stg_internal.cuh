@@ -510,6 +510,64 @@ using LinkDSR18 = LinkDS<9>;
 using LinkDSR12 = LinkDS<6>;
 
 // Base of the (mu, parity) block of an internal link array.
+__device__ __forceinline__ void sincos_t(float t, float *s, float *c) { sincosf(t, s, c); }
+__device__ __forceinline__ void sincos_t(double t, double *s, double *c) { sincos(t, s, c); }
+
+// A link with a U(1) phase u = exp(i theta) (Sec. 4.1: each flavour's U(1) field -- imaginary
+// chemical potential, background fields -- stored as the angle theta and turned into cos + i sin
+// on line).  Inside each (mu, parity) block the base link's chunks are followed by one chunk of
+// Vh angles of type T (float for FP32/16-bit links, double for FP64 and double-single links).
+// load() returns exp(i theta) U, so the backward hop, which uses the conjugate transpose, gets
+// exp(-i theta) U^dag with no change to the operator kernel.  The staggered and boundary signs
+// stay separate (from coordinates).
+template <typename Base, typename T>
+struct LinkU1 {
+    using R = typename Base::R;
+    using BaseLink = Base;
+    using Theta = T;
+    static constexpr int kBytes = Base::kBytes + (int)sizeof(T);
+    __device__ __forceinline__ static const T *theta(const void *blk, int Vh)
+    {
+        return reinterpret_cast<const T *>(static_cast<const char *>(blk) + (size_t)Base::kBytes * Vh);
+    }
+    __device__ __forceinline__ static cx<R> phase(const void *blk, int Vh, int h)
+    {
+        T sn, cs;
+        sincos_t(__ldg(theta(blk, Vh) + h), &sn, &cs);
+        return cx<R>{R(cs), R(sn)};
+    }
+    __device__ __forceinline__ static void load(const void *blk, int Vh, int h, cx<R> U[3][3])
+    {
+        Base::load(blk, Vh, h, U);
+        const cx<R> e = phase(blk, Vh, h);
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) U[r][c] = cmul(e, U[r][c]);
+    }
+    __device__ __forceinline__ static void pack(void *blk, int Vh, int h, const double2 *m) { Base::pack(blk, Vh, h, m); }
+};
+
+// Base link type and phase of a (possibly phased) link type.
+template <typename L>
+struct LinkTraits {
+    using Base = L;
+    static constexpr bool kU1 = false;
+    __device__ __forceinline__ static cx<typename L::R> phase(const void *, int, int)
+    {
+        return cx<typename L::R>{typename L::R(1), typename L::R(0)};
+    }
+};
+template <typename B, typename T>
+struct LinkTraits<LinkU1<B, T>> {
+    using Base = B;
+    static constexpr bool kU1 = true;
+    __device__ __forceinline__ static cx<typename B::R> phase(const void *blk, int Vh, int h)
+    {
+        return LinkU1<B, T>::phase(blk, Vh, h);
+    }
+};
+
 template <typename LinkT>
 __device__ __forceinline__ const void *link_block(const void *links, int Vh, int mu, int par)
 {

@@ -1,0 +1,125 @@
+"""Molecular dynamics of the RHMC (Sec. 2: exp(-H^2/2 - S_g - S_f) sampled by MD plus an
+accept/reject step; Sec. 3: each MD iteration computes the forces, evolves the momenta, then
+the links).  Host-side sequencing only: every arithmetic step is a libstg kernel (gauge action and
+force, stout smearing and its chain rule, multi-shift CG, fermion force, the MD link/momentum
+updates and the kinetic energy).
+
+The fermion part is S_f = sum_pf sum_i r_i Re(b^dag x_i), x_i = (m^2 + sigma_i - D_eo D_oe)^-1 b
+on the k-times stout-smeared links (the pole part of the rational approximation; a constant
+term has no force).  Forces are Lie-algebra forces F = TA(U G^dag) on the unsmeared links.
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+from typing import Sequence
+
+import torch
+
+from .api import (Gauge, Lattice, fermion_force, gauge_action, gauge_force, md_kinetic, md_momenta,
+                  md_update_links_, md_update_momenta_, mscg, stout_force, stout_smear)
+
+# Omelyan's second-order minimum-norm parameter
+OMELYAN_LAMBDA = 0.1931833275037836
+
+
+@dataclass
+class Pseudofermion:
+    b: torch.Tensor                 # even-site source [Vh, 3] complex128 (cuda)
+    shifts: Sequence[float]
+    residues: Sequence[float]
+
+
+@dataclass
+class Action:
+    lattice: Lattice
+    beta: float
+    mass: float = 0.0
+    pseudofermions: list = field(default_factory=list)
+    stout_rho: float = 0.0
+    stout_steps: int = 0
+    tol: float = 1e-12
+    inner: str | None = None        # None: FP64 solve; "f32": mixed FP32-inner solve
+
+    def _smeared(self, links):
+        if self.stout_steps > 0:
+            levels = stout_smear(self.lattice, links, self.stout_rho, self.stout_steps)
+            return levels, levels[-1].contiguous()
+        return None, links
+
+    def _gauges(self, uk):
+        g64 = Gauge(self.lattice, uk, "f64", 18)
+        gi = Gauge(self.lattice, uk, "f32", 12) if self.inner == "f32" else None
+        return g64, gi
+
+    def value(self, links: torch.Tensor) -> float:
+        """S_g + S_f of the links."""
+        s = gauge_action(self.lattice, links, self.beta)["action"] if self.beta != 0.0 else 0.0
+        if self.pseudofermions:
+            _, uk = self._smeared(links)
+            g64, gi = self._gauges(uk)
+            for pf in self.pseudofermions:
+                x, _ = mscg(g64, pf.b, list(pf.shifts), self.mass, tol=self.tol, g_inner=gi)
+                bb = pf.b.reshape(-1)
+                s += sum(float(r) * float(torch.vdot(bb, x[i].reshape(-1)).real) for i, r in enumerate(pf.residues))
+        return s
+
+    def apply_force(self, links: torch.Tensor, mom: torch.Tensor, eps: float) -> None:
+        """mom <- mom - eps i F(links), F the total Lie-algebra force."""
+        if self.beta != 0.0:
+            md_update_momenta_(self.lattice, eps, gauge_force(self.lattice, links, self.beta, kind=0), mom)
+        if not self.pseudofermions:
+            return
+        levels, uk = self._smeared(links)
+        g64, gi = self._gauges(uk)
+        for pf in self.pseudofermions:
+            x, _ = mscg(g64, pf.b, list(pf.shifts), self.mass, tol=self.tol, g_inner=gi)
+            if levels is None:
+                f = fermion_force(g64, list(pf.residues), x, kind=0)
+            else:
+                gk = fermion_force(g64, list(pf.residues), x, kind=1)
+                f = stout_force(self.lattice, links, levels, self.stout_rho, gk, kind=0)
+            md_update_momenta_(self.lattice, eps, f, mom)
+
+
+def hamiltonian(action: Action, links: torch.Tensor, mom: torch.Tensor) -> float:
+    return md_kinetic(action.lattice, mom) + action.value(links)
+
+
+def leapfrog(action: Action, links: torch.Tensor, mom: torch.Tensor, tau: float, nsteps: int) -> None:
+    """Second-order leapfrog over trajectory length tau, in place: half momentum steps at both ends."""
+    eps = tau / nsteps
+    lat = action.lattice
+    action.apply_force(links, mom, 0.5 * eps)
+    for k in range(nsteps):
+        md_update_links_(lat, eps, mom, links)
+        action.apply_force(links, mom, eps if k < nsteps - 1 else 0.5 * eps)
+
+
+def omelyan(action: Action, links: torch.Tensor, mom: torch.Tensor, tau: float, nsteps: int,
+            lam: float = OMELYAN_LAMBDA) -> None:
+    """Omelyan's second-order minimum-norm integrator (forces at lam, 1 - 2 lam, lam of each step;
+    consecutive end forces merged), in place."""
+    eps = tau / nsteps
+    lat = action.lattice
+    action.apply_force(links, mom, lam * eps)
+    for k in range(nsteps):
+        md_update_links_(lat, 0.5 * eps, mom, links)
+        action.apply_force(links, mom, (1.0 - 2.0 * lam) * eps)
+        md_update_links_(lat, 0.5 * eps, mom, links)
+        action.apply_force(links, mom, (2.0 if k < nsteps - 1 else 1.0) * lam * eps)
+
+
+def trajectory(action: Action, links: torch.Tensor, xi: torch.Tensor, tau: float, nsteps: int,
+               uniform: float, integrator: str = "omelyan") -> dict:
+    """One RHMC trajectory from links (not modified): momentum heatbath from the standard normal
+    numbers xi [4, V, 8], MD to tau, Metropolis test against the uniform number in [0, 1).
+    Returns the new links (the old ones if rejected), dH and the decision."""
+    mom = md_momenta(action.lattice, xi)
+    h0 = hamiltonian(action, links, mom)
+    u = links.clone()
+    (omelyan if integrator == "omelyan" else leapfrog)(action, u, mom, tau, nsteps)
+    h1 = hamiltonian(action, u, mom)
+    dh = h1 - h0
+    accept = uniform < math.exp(min(0.0, -dh))
+    return {"links": u if accept else links, "dH": dh, "accepted": accept}

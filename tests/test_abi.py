@@ -103,3 +103,19 @@ def test_stout_arguments_rejected_before_launch(L):
 def test_status_strings(L):
     for s in (0, -1, -2, -3, -4, -5, -6, 99):
         assert L.stg_status_string(s)
+
+
+def test_gauge_and_md_arguments_rejected_before_launch(L):
+    rc, h = _lat(L, (4, 4, 4, 4))
+    a, b, c = (ctypes.c_void_p(v) for v in (256, 512, 768))
+    assert L.stg_gauge_action(None, 5.0, a, ctypes.c_void_p(1024), None) == -1
+    assert L.stg_gauge_action(h, 5.0, ctypes.c_void_p(8), ctypes.c_void_p(1024), None) == -1
+    assert L.stg_gauge_action(h, float("inf"), a, ctypes.c_void_p(1024), None) == -1
+    assert L.stg_gauge_force(h, 5.0, a, a, 0, None) == -1 and b"alias" in L.stg_last_error()
+    assert L.stg_gauge_force(h, 5.0, a, b, 3, None) == -1 and b"kind" in L.stg_last_error()
+    assert L.stg_md_momenta(h, None, b, None) == -1
+    assert L.stg_md_update_links(h, 0.1, a, a, None) == -1 and b"alias" in L.stg_last_error()
+    assert L.stg_md_update_links(h, 2.0, a, b, None) == -1 and b"eps" in L.stg_last_error()
+    assert L.stg_md_update_momenta(h, float("nan"), a, b, None) == -1
+    assert L.stg_md_kinetic(h, a, None, None) == -1
+    L.stg_lattice_destroy(h)

@@ -237,8 +237,8 @@ def time_deo_sweep(torch, p, dims, reps=50):
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1) * 1e-3)
         t = float(np.median(ts))
-        # a U(1) phase field adds one stored angle per link (double for f64/ds, float otherwise)
-        byt = (bytes_per_site(prec, recon) + (8 * (8 if prec in ("f64", "ds") else 4) if u1 else 0)) * lat.Vh
+        # a U(1) phase field adds one stored phase per link ((cos, sin) doubles for f64/ds, a float angle otherwise)
+        byt = (bytes_per_site(prec, recon) + (8 * (16 if prec in ("f64", "ds") else 4) if u1 else 0)) * lat.Vh
         out.append({"lattice": "x".join(map(str, dims)), "links": f"{prec}-{recon}" + ("+u1" if u1 else ""),
                     "us": round(t * 1e6, 2), "GBs": round(byt / t / 1e9, 1)})
         del g

@@ -102,9 +102,11 @@ stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, 
 /* As stg_gauge_create, with a U(1) phase field: theta_dev (device, FP64, canonical [4][V], radians)
  * gives every link the phase u = exp(i theta_mu(x)) on top of the staggered and boundary signs,
  * so that D uses exp(i theta) U forward and exp(-i theta) U^dag backward (Sec. 4.1: imaginary
- * chemical potential and background fields as a per-flavour U(1) field).  The angles are stored
- * beside the links (float for F32/BF16/F16 links, double for F64 and DS) and turned into
- * cos + i sin on line; 12-real compression applies to the SU(3) part only.  Every operation
+ * chemical potential and background fields as a per-flavour U(1) field).  The phases are stored
+ * beside the links: as float angles turned into cos + i sin on line for F32/BF16/F16 links (the
+ * paper's choice for memory-bound operators), as precomputed (cos, sin) double pairs for F64 and
+ * DS links (FP64 trigonometry is expensive on GB300); 12-real compression applies to the SU(3)
+ * part only.  Every operation
  * accepts such a gauge; the solvers need the inner gauge to carry the same phases. */
 stg_status stg_gauge_create_u1(const stg_lattice *lat, const void *links_c128_dev, const double *theta_dev,
                                stg_prec prec, stg_recon recon, void *stream, stg_gauge **out);
@@ -247,13 +249,15 @@ stg_status stg_fermion_force(const stg_gauge *g_f64, int32_t nshift, const doubl
  *   i Q = TA(C U^dag),   U' = exp(i Q) U
  * with periodic links in all four directions.  exp(i Q) = f0 + f1 Q + f2 Q^2, the f_j summed
  * from the Taylor series of exp reduced by the Cayley-Hamilton identity Q^3 = c1 Q + c0
- * (c0 = det Q, c1 = tr Q^2 / 2) to full FP64 accuracy.  FP64 throughout.
- * links_c128_dev: canonical complex128 [4][V][3][3] U^(0) (device, read only);
- * levels_c128_dev: nstep consecutive canonical arrays U^(1) .. U^(nstep) (device, written).
+ * (c0 = det Q, c1 = tr Q^2 / 2) to the precision's accuracy.
+ * prec STG_F64: complex128 arrays, FP64 arithmetic; STG_F32: complex64 arrays, FP32 arithmetic
+ * (the molecular dynamics runs in single precision, Sec. 5.3).
+ * links_dev: canonical [4][V][3][3] U^(0) (device, read only);
+ * levels_dev: nstep consecutive canonical arrays U^(1) .. U^(nstep) (device, written).
  * 1 <= nstep <= 16, |rho| <= 0.5 (larger rho is refused: the series would cancel digits);
  * no aliasing between the two buffers; both 16-byte aligned.  Async on `stream`. */
-stg_status stg_stout_smear(const stg_lattice *lat, int32_t nstep, double rho, const void *links_c128_dev,
-                           void *levels_c128_dev, void *stream);
+stg_status stg_stout_smear(const stg_lattice *lat, stg_prec prec, int32_t nstep, double rho, const void *links_dev,
+                           void *levels_dev, void *stream);
 
 /* Force chain rule through the smearing (Sec. 3: the MD evolves U^(0) while the fermion action
  * depends on U^(k)).  Given G_k = dS/dRe U^(k) + i dS/dIm U^(k) (e.g. stg_fermion_force kind 1
@@ -263,14 +267,14 @@ stg_status stg_stout_smear(const stg_lattice *lat, int32_t nstep, double rho, co
  *   G_Omega = TA(i G_Q),  G = exp(iQ)^dag G' + G_Omega^dag C + (staple terms of rho G_Omega U)
  * where the staple terms collect, for every link, the product-rule terms of the six staples of
  * the three other directions that contain it (a gather: no atomics, deterministic).
- * links_c128_dev: U^(0); levels_c128_dev: the stg_stout_smear output (U^(1) .. U^(nstep-1) are
- * read); grad_c128_dev: G_k; out_c128_dev: kind 1: G_0 = dS/dRe U^(0) + i dS/dIm U^(0),
- * kind 0: F = TA(U^(0) G_0^dag) (dS/deps = tr(X F) along U^(0) -> exp(eps X) U^(0)).
- * All canonical complex128 [4][V][3][3] device arrays; out must not alias the inputs.  Allocates
- * 2 link-sized FP64 work arrays from the stream-ordered allocator.  Same limits as smearing. */
-stg_status stg_stout_force(const stg_lattice *lat, int32_t nstep, double rho, const void *links_c128_dev,
-                           const void *levels_c128_dev, const void *grad_c128_dev, void *out_c128_dev,
-                           int32_t kind, void *stream);
+ * links_dev: U^(0); levels_dev: the stg_stout_smear output (U^(1) .. U^(nstep-1) are read);
+ * grad_dev: G_k; out_dev: kind 1: G_0 = dS/dRe U^(0) + i dS/dIm U^(0), kind 0:
+ * F = TA(U^(0) G_0^dag) (dS/deps = tr(X F) along U^(0) -> exp(eps X) U^(0)).
+ * All canonical [4][V][3][3] device arrays of prec (F64: complex128, F32: complex64); out must not
+ * alias the inputs.  Allocates 2 link-sized work arrays from the stream-ordered allocator.  Same
+ * limits as smearing. */
+stg_status stg_stout_force(const stg_lattice *lat, stg_prec prec, int32_t nstep, double rho, const void *links_dev,
+                           const void *levels_dev, const void *grad_dev, void *out_dev, int32_t kind, void *stream);
 
 /* ---- gauge action and force --------------------------------------------------------------------- */
 
@@ -289,9 +293,10 @@ stg_status stg_gauge_action(const stg_lattice *lat, double beta, const void *lin
 /* Gradient of S_g per link: G = dS_g/dRe U + i dS_g/dIm U = -(beta/3) sum c B^dag over the loops
  * through the link (B = the rest of the loop after the link; 2 plaquettes and 6 rectangles per
  * other direction), written as kind 1: G, or kind 0: F = TA(U G^dag) (dS/deps = tr(X F) along
- * U -> exp(eps X) U).  links_c128_dev / out_c128_dev: canonical complex128 [4][V][3][3] (device),
- * no aliasing.  FP64; async on `stream`. */
-stg_status stg_gauge_force(const stg_lattice *lat, double beta, const void *links_c128_dev, void *out_c128_dev,
+ * U -> exp(eps X) U).  prec STG_F64: complex128 arrays, FP64; STG_F32: complex64 arrays, FP32 (the
+ * single-precision MD, Sec. 5.3).  links_dev / out_dev: canonical [4][V][3][3] (device), no
+ * aliasing.  Async on `stream`. */
+stg_status stg_gauge_force(const stg_lattice *lat, stg_prec prec, double beta, const void *links_dev, void *out_dev,
                            int32_t kind, void *stream);
 
 /* ---- molecular dynamics (Sec. 2-3) ----------------------------------------------------------------- */
@@ -307,9 +312,15 @@ stg_status stg_md_momenta(const stg_lattice *lat, const double *xi_dev, void *mo
  * |eps| <= 1; momenta and links must not alias. */
 stg_status stg_md_update_links(const stg_lattice *lat, double eps, const void *mom_c128_dev, void *links_c128_dev,
                                void *stream);
-/* H <- H - eps i F for every link. */
-stg_status stg_md_update_momenta(const stg_lattice *lat, double eps, const void *force_c128_dev, void *mom_c128_dev,
-                                 void *stream);
+/* H <- H - eps i F for every link; the force F in complex128 (force_prec STG_F64) or complex64
+ * (STG_F32: a force computed in single precision), the momenta complex128. */
+stg_status stg_md_update_momenta(const stg_lattice *lat, stg_prec force_prec, double eps, const void *force_dev,
+                                 void *mom_c128_dev, void *stream);
+/* dst[k] = src[k] for `count` complex numbers, converting between complex128 (STG_F64) and
+ * complex64 (STG_F32) (device arrays, 16-byte aligned, no aliasing): the links and forces of the
+ * single-precision MD kernels. */
+stg_status stg_complex_convert(int64_t count, stg_prec src_prec, const void *src_dev, stg_prec dst_prec, void *dst_dev,
+                               void *stream);
 /* *out_dev (one device double) = (1/2) sum_links tr H^2, summed in a fixed order. */
 stg_status stg_md_kinetic(const stg_lattice *lat, const void *mom_c128_dev, double *out_dev, void *stream);
 

@@ -307,27 +307,57 @@ def fermion_force(g_f64: Gauge, residues, x: torch.Tensor, kind: int = 0, stream
     return out
 
 
+def _cprec(t: torch.Tensor) -> int:
+    """Library precision of a complex link array: complex128 -> F64, complex64 -> F32."""
+    if t.dtype == torch.complex128:
+        return PREC["f64"]
+    if t.dtype == torch.complex64:
+        return PREC["f32"]
+    raise TypeError(f"expected complex128 or complex64 links, got {t.dtype}")
+
+
+def _links(t, lattice: Lattice) -> torch.Tensor:
+    if not torch.is_tensor(t):
+        t = torch.as_tensor(t)
+    if not t.is_cuda:
+        t = t.cuda()
+    _cprec(t)
+    return t.contiguous().reshape(4, lattice.V, 3, 3)
+
+
 def stout_smear(lattice: Lattice, links: torch.Tensor, rho: float, nstep: int, stream=None) -> torch.Tensor:
-    """Stout-smeared levels U^(1) .. U^(nstep), [nstep, 4, V, 3, 3] complex128, from U^(0)
-    [4, V, 3, 3] (canonical layout, FP64)."""
-    u = _dev(links).reshape(4, lattice.V, 3, 3)
-    out = torch.empty((int(nstep), 4, lattice.V, 3, 3), dtype=torch.complex128, device="cuda")
-    check(lib().stg_stout_smear(lattice.handle, int(nstep), float(rho), _ptr(u), _ptr(out), _stream(stream)),
-          "stg_stout_smear")
+    """Stout-smeared levels U^(1) .. U^(nstep), [nstep, 4, V, 3, 3], from U^(0) [4, V, 3, 3]
+    (canonical layout): complex128 links run in FP64, complex64 links in FP32."""
+    u = _links(links, lattice)
+    out = torch.empty((int(nstep), 4, lattice.V, 3, 3), dtype=u.dtype, device="cuda")
+    check(lib().stg_stout_smear(lattice.handle, _cprec(u), int(nstep), float(rho), _ptr(u), _ptr(out),
+                                _stream(stream)), "stg_stout_smear")
     return out
 
 
 def stout_force(lattice: Lattice, links: torch.Tensor, levels: torch.Tensor, rho: float, grad: torch.Tensor,
                 kind: int = 1, stream=None) -> torch.Tensor:
     """Pulls dS/dU^(k) (torch convention, [4, V, 3, 3]) back through k = len(levels) stout steps:
-    kind 1 -> dS/dRe U^(0) + i dS/dIm U^(0), kind 0 -> TA(U^(0) G^dag) (Lie-algebra force)."""
-    u = _dev(links).reshape(4, lattice.V, 3, 3)
-    lv = _dev(levels)
+    kind 1 -> dS/dRe U^(0) + i dS/dIm U^(0), kind 0 -> TA(U^(0) G^dag) (Lie-algebra force).
+    All arrays complex128 (FP64) or all complex64 (FP32)."""
+    u = _links(links, lattice)
+    lv = levels.contiguous()
     nstep = int(lv.shape[0])
-    gr = _dev(grad).reshape(4, lattice.V, 3, 3)
-    out = torch.empty((4, lattice.V, 3, 3), dtype=torch.complex128, device="cuda")
-    check(lib().stg_stout_force(lattice.handle, nstep, float(rho), _ptr(u), _ptr(lv), _ptr(gr), _ptr(out), int(kind),
-                                _stream(stream)), "stg_stout_force")
+    gr = grad.contiguous().reshape(4, lattice.V, 3, 3)
+    if lv.dtype != u.dtype or gr.dtype != u.dtype:
+        raise TypeError("stout_force: links, levels and grad must share one dtype")
+    out = torch.empty((4, lattice.V, 3, 3), dtype=u.dtype, device="cuda")
+    check(lib().stg_stout_force(lattice.handle, _cprec(u), nstep, float(rho), _ptr(u), _ptr(lv), _ptr(gr), _ptr(out),
+                                int(kind), _stream(stream)), "stg_stout_force")
+    return out
+
+
+def complex_convert(src: torch.Tensor, dtype, stream=None) -> torch.Tensor:
+    """complex128 <-> complex64 copy of a device array by the library's conversion kernel."""
+    s = src.contiguous()
+    out = torch.empty(s.shape, dtype=dtype, device="cuda")
+    check(lib().stg_complex_convert(s.numel(), _cprec(s), _ptr(s), _cprec(out), _ptr(out), _stream(stream)),
+          "stg_complex_convert")
     return out
 
 
@@ -342,12 +372,12 @@ def gauge_action(lattice: Lattice, links: torch.Tensor, beta: float, stream=None
 
 
 def gauge_force(lattice: Lattice, links: torch.Tensor, beta: float, kind: int = 0, stream=None) -> torch.Tensor:
-    """Per-link gradient of S_g [4, V, 3, 3] complex128: kind 1 -> dS/dRe U + i dS/dIm U,
-    kind 0 -> TA(U G^dag) (Lie-algebra force)."""
-    u = _dev(links).reshape(4, lattice.V, 3, 3)
-    out = torch.empty((4, lattice.V, 3, 3), dtype=torch.complex128, device="cuda")
-    check(lib().stg_gauge_force(lattice.handle, float(beta), _ptr(u), _ptr(out), int(kind), _stream(stream)),
-          "stg_gauge_force")
+    """Per-link gradient of S_g [4, V, 3, 3]: kind 1 -> dS/dRe U + i dS/dIm U, kind 0 -> TA(U G^dag)
+    (Lie-algebra force); complex128 links run in FP64, complex64 links in FP32."""
+    u = _links(links, lattice)
+    out = torch.empty((4, lattice.V, 3, 3), dtype=u.dtype, device="cuda")
+    check(lib().stg_gauge_force(lattice.handle, _cprec(u), float(beta), _ptr(u), _ptr(out), int(kind),
+                                _stream(stream)), "stg_gauge_force")
     return out
 
 
@@ -367,8 +397,9 @@ def md_update_links_(lattice: Lattice, eps: float, mom: torch.Tensor, links: tor
 
 
 def md_update_momenta_(lattice: Lattice, eps: float, force: torch.Tensor, mom: torch.Tensor, stream=None) -> torch.Tensor:
-    """mom <- mom - eps i F, in place (F: Lie-algebra force, kind 0 format)."""
-    check(lib().stg_md_update_momenta(lattice.handle, float(eps), _ptr(force), _ptr(mom), _stream(stream)),
+    """mom <- mom - eps i F, in place (F: Lie-algebra force, kind 0 format, complex128 or complex64)."""
+    f = force.contiguous()
+    check(lib().stg_md_update_momenta(lattice.handle, _cprec(f), float(eps), _ptr(f), _ptr(mom), _stream(stream)),
           "stg_md_update_momenta")
     return mom
 

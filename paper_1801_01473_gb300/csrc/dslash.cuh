@@ -82,7 +82,10 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
             const Hop hp = hop_of(G.g, s, mu);
             cx<R> U[3][3];
             // forward hop: u_mu(x) U_mu(x) in(x + mu)
-            LinkT::load(link_block<LinkT>(G.links, Vh, mu, op), Vh, h, U);
+            const void *blk_f = link_block<LinkT>(G.links, Vh, mu, op);
+            LinkT::load(blk_f, Vh, h, U);
+            cx<R> ph_f;
+            if constexpr (LinkTraits<LinkT>::kU1) ph_f = LinkTraits<LinkT>::phase(blk_f, Vh, h);
 #pragma unroll
             for (int j = 0; j < NRHS; ++j) {
                 if (!act[j]) continue;
@@ -93,12 +96,16 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
                     cx<R> w = cx<R>{R(0), R(0)};
 #pragma unroll
                     for (int c = 0; c < 3; ++c) cmac(w, U[r][c], v[c]);
+                    if constexpr (LinkTraits<LinkT>::kU1) w = cmul(ph_f, w);
                     acc[j][r].re = fma(R(hp.sf), w.re, acc[j][r].re);
                     acc[j][r].im = fma(R(hp.sf), w.im, acc[j][r].im);
                 }
             }
             // backward hop: - u_mu(x - mu) U_mu(x - mu)^dag in(x - mu)
-            LinkT::load(link_block<LinkT>(G.links, Vh, mu, 1 - op), Vh, hp.hb, U);
+            const void *blk_b = link_block<LinkT>(G.links, Vh, mu, 1 - op);
+            LinkT::load(blk_b, Vh, hp.hb, U);
+            cx<R> ph_b;
+            if constexpr (LinkTraits<LinkT>::kU1) ph_b = cconj(LinkTraits<LinkT>::phase(blk_b, Vh, hp.hb));
 #pragma unroll
             for (int j = 0; j < NRHS; ++j) {
                 if (!act[j]) continue;
@@ -109,6 +116,7 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
                     cx<R> w = cx<R>{R(0), R(0)};
 #pragma unroll
                     for (int c = 0; c < 3; ++c) cmac_conj(w, U[c][r], v[c]);
+                    if constexpr (LinkTraits<LinkT>::kU1) w = cmul(ph_b, w);
                     acc[j][r].re = fma(R(-hp.sb), w.re, acc[j][r].re);
                     acc[j][r].im = fma(R(-hp.sb), w.im, acc[j][r].im);
                 }

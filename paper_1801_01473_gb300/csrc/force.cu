@@ -228,8 +228,8 @@ extern "C" stg_status stg_fermion_force(const stg_gauge *g, int32_t nshift, cons
     switch (g->kind) {
     case kF64R18: k_force<LinkF64R18><<<grid, kForceBlock, 0, st>>>(a); break;
     case kF64R12: k_force<LinkF64R12><<<grid, kForceBlock, 0, st>>>(a); break;
-    case kF64R18 | kU1: k_force<LinkU1<LinkF64R18, double>><<<grid, kForceBlock, 0, st>>>(a); break;
-    default: k_force<LinkU1<LinkF64R12, double>><<<grid, kForceBlock, 0, st>>>(a); break;
+    case kF64R18 | kU1: k_force<LinkU1<LinkF64R18, double2>><<<grid, kForceBlock, 0, st>>>(a); break;
+    default: k_force<LinkU1<LinkF64R12, double2>><<<grid, kForceBlock, 0, st>>>(a); break;
     }
     STG_CUDA_TRY(cudaGetLastError());
     return STG_OK;

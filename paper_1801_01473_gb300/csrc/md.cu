@@ -13,6 +13,7 @@
 // exp(i eps H) uses the Cayley-Hamilton series of su3.cuh (FP64).  Canonical complex128 layout
 // [4][V][3][3], one thread per link.
 #include <cmath>
+#include <algorithm>
 #include <cstring>
 
 #include "stg_common.h"
@@ -28,7 +29,7 @@ struct MdArgs {
     long long nlink;  // 4 V
     double eps;
     const double *xi;
-    const double2 *F;
+    const void *F;
     double2 *H;
     double2 *U;
     double *partial;
@@ -90,20 +91,34 @@ __global__ void __launch_bounds__(kMdBlock) k_md_update_links(const __grid_const
     stl(a.U, l, mul<false, false>(poly3(e.f, q, q2), u));
 }
 
+template <typename C>
 __global__ void __launch_bounds__(kMdBlock) k_md_update_momenta(const __grid_constant__ MdArgs a)
 {
     const long long l = (long long)blockIdx.x * kMdBlock + threadIdx.x;
     if (l >= a.nlink) return;
-    const double2 *f = a.F + l * 9;
+    const C *f = static_cast<const C *>(a.F) + l * 9;
     double2 *h = a.H + l * 9;
 #pragma unroll
     for (int k = 0; k < 9; ++k) {
-        const double2 fv = f[k];
+        const C fv = f[k];
         double2 hv = h[k];
         // H - eps i F:  i (fr + i fi) = -fi + i fr
-        hv.x = fma(a.eps, fv.y, hv.x);
-        hv.y = fma(-a.eps, fv.x, hv.y);
+        hv.x = fma(a.eps, (double)fv.y, hv.x);
+        hv.y = fma(-a.eps, (double)fv.x, hv.y);
         h[k] = hv;
+    }
+}
+
+// complex128 <-> complex64 arrays (count complex numbers)
+template <typename S, typename D>
+__global__ void k_convert(long long n, const S *__restrict__ src, D *__restrict__ dst)
+{
+    for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
+        const S v = src[k];
+        D w;
+        w.x = v.x;
+        w.y = v.y;
+        dst[k] = w;
     }
 }
 
@@ -180,17 +195,44 @@ extern "C" stg_status stg_md_update_links(const stg_lattice *lat, double eps, co
     return STG_OK;
 }
 
-extern "C" stg_status stg_md_update_momenta(const stg_lattice *lat, double eps, const void *force_c128_dev,
-                                            void *mom_c128_dev, void *stream)
+extern "C" stg_status stg_md_update_momenta(const stg_lattice *lat, stg_prec force_prec, double eps,
+                                            const void *force_dev, void *mom_c128_dev, void *stream)
 {
-    if (!lat || bad(force_c128_dev) || bad(mom_c128_dev))
+    if (!lat || bad(force_dev) || bad(mom_c128_dev))
         return set_error(STG_ERR_ARG, "stg_md_update_momenta: null or misaligned pointer");
+    if (force_prec != STG_F64 && force_prec != STG_F32)
+        return set_error(STG_ERR_ARG, "stg_md_update_momenta: force precision must be F64 or F32");
     if (!std::isfinite(eps)) return set_error(STG_ERR_ARG, "stg_md_update_momenta: eps must be finite");
     MdArgs a = md_args(lat);
     a.eps = eps;
-    a.F = static_cast<const double2 *>(force_c128_dev);
+    a.F = force_dev;
     a.H = static_cast<double2 *>(mom_c128_dev);
-    k_md_update_momenta<<<md_grid(a), kMdBlock, 0, (cudaStream_t)stream>>>(a);
+    if (force_prec == STG_F64)
+        k_md_update_momenta<double2><<<md_grid(a), kMdBlock, 0, (cudaStream_t)stream>>>(a);
+    else
+        k_md_update_momenta<float2><<<md_grid(a), kMdBlock, 0, (cudaStream_t)stream>>>(a);
+    STG_CUDA_TRY(cudaGetLastError());
+    return STG_OK;
+}
+
+extern "C" stg_status stg_complex_convert(int64_t count, stg_prec src_prec, const void *src_dev, stg_prec dst_prec,
+                                          void *dst_dev, void *stream)
+{
+    if (count < 0 || bad(src_dev) || bad(dst_dev) || src_dev == dst_dev)
+        return set_error(STG_ERR_ARG, "stg_complex_convert: bad count or null, misaligned or aliasing pointer");
+    const bool ok = (src_prec == STG_F64 || src_prec == STG_F32) && (dst_prec == STG_F64 || dst_prec == STG_F32);
+    if (!ok) return set_error(STG_ERR_ARG, "stg_complex_convert: precisions must be F64 or F32");
+    if (count == 0) return STG_OK;
+    cudaStream_t st = (cudaStream_t)stream;
+    const unsigned nb = (unsigned)std::min<long long>((count + 255) / 256, 152LL * 16);
+    if (src_prec == STG_F64 && dst_prec == STG_F32)
+        k_convert<<<nb, 256, 0, st>>>(count, static_cast<const double2 *>(src_dev), static_cast<float2 *>(dst_dev));
+    else if (src_prec == STG_F32 && dst_prec == STG_F64)
+        k_convert<<<nb, 256, 0, st>>>(count, static_cast<const float2 *>(src_dev), static_cast<double2 *>(dst_dev));
+    else if (src_prec == STG_F64)
+        k_convert<<<nb, 256, 0, st>>>(count, static_cast<const double2 *>(src_dev), static_cast<double2 *>(dst_dev));
+    else
+        k_convert<<<nb, 256, 0, st>>>(count, static_cast<const float2 *>(src_dev), static_cast<float2 *>(dst_dev));
     STG_CUDA_TRY(cudaGetLastError());
     return STG_OK;
 }

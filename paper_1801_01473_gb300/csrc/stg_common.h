@@ -22,8 +22,9 @@ inline bool kind_has_u1(int kind) { return (kind & kU1) != 0; }
 int link_bytes(int kind);
 inline bool kind_is_f64(int kind) { return base_kind(kind) == kF64R18 || base_kind(kind) == kF64R12; }
 inline bool kind_is_ds(int kind) { return base_kind(kind) == kDSR18 || base_kind(kind) == kDSR12; }
-// bytes of one phase angle: double for FP64 and double-single links, float otherwise
-inline int theta_bytes(int kind) { return kind_is_f64(kind) || kind_is_ds(kind) ? 8 : 4; }
+// bytes of one stored phase: (cos, sin) as double2 for FP64 and double-single links, a float
+// angle otherwise
+inline int theta_bytes(int kind) { return kind_is_f64(kind) || kind_is_ds(kind) ? 16 : 4; }
 // bytes per site of the fields a gauge of this kind works on
 inline int kind_vec_bytes(int kind) { return kind_is_f64(kind) || kind_is_ds(kind) ? 48 : 24; }
 

@@ -5,6 +5,7 @@
 #include <cstring>
 #include <map>
 #include <mutex>
+#include <type_traits>
 #include <new>
 #include <string>
 #include <tuple>
@@ -205,7 +206,18 @@ static cudaError_t pack_links_t(const Geom &g, const void *canon, void *links, c
     return cudaGetLastError();
 }
 
-// canonical angles theta [4][V] (FP64) -> the theta chunk of every (mu, parity) block of a LinkU1 layout
+// a phase in its stored form: the angle, or (cos, sin)
+__device__ __forceinline__ void store_phase(float *p, double theta) { *p = (float)theta; }
+__device__ __forceinline__ void store_phase(double2 *p, double theta)
+{
+    double sn, cs;
+    sincos(theta, &sn, &cs);
+    *p = make_double2(cs, sn);
+}
+__device__ __forceinline__ double angle_of(float t) { return (double)t; }
+__device__ __forceinline__ double angle_of(double2 p) { return atan2(p.y, p.x); }
+
+// canonical angles theta [4][V] (FP64) -> the phase chunk of every (mu, parity) block of a LinkU1 layout
 template <typename LinkT>
 __global__ void k_pack_theta(Geom g, const double *__restrict__ theta, void *__restrict__ links)
 {
@@ -221,7 +233,7 @@ __global__ void k_pack_theta(Geom g, const double *__restrict__ theta, void *__r
     int par = (x + y + z + t) & 1;
     char *blk = static_cast<char *>(links) + (size_t)(mu * 2 + par) * g.Vh * LinkT::kBytes;
     T *th = reinterpret_cast<T *>(blk + (size_t)LinkT::BaseLink::kBytes * g.Vh);
-    th[i >> 1] = (T)theta[tid];
+    store_phase(th + (i >> 1), theta[tid]);
 }
 
 template <typename LinkT>
@@ -238,14 +250,14 @@ cudaError_t launch_pack_links_u1(int kind, const Geom &g, const void *canon, con
                                  cudaStream_t st)
 {
     switch (base_kind(kind)) {
-    case kF64R18: return pack_u1_t<LinkU1<LinkF64R18, double>>(g, canon, theta, links, st);
-    case kF64R12: return pack_u1_t<LinkU1<LinkF64R12, double>>(g, canon, theta, links, st);
+    case kF64R18: return pack_u1_t<LinkU1<LinkF64R18, double2>>(g, canon, theta, links, st);
+    case kF64R12: return pack_u1_t<LinkU1<LinkF64R12, double2>>(g, canon, theta, links, st);
     case kF32R18: return pack_u1_t<LinkU1<LinkF32R18, float>>(g, canon, theta, links, st);
     case kF32R12: return pack_u1_t<LinkU1<LinkF32R12, float>>(g, canon, theta, links, st);
     case kBF16R12: return pack_u1_t<LinkU1<Link16R12<__nv_bfloat16>, float>>(g, canon, theta, links, st);
     case kF16R12: return pack_u1_t<LinkU1<Link16R12<__half>, float>>(g, canon, theta, links, st);
-    case kDSR18: return pack_u1_t<LinkU1<LinkDSR18, double>>(g, canon, theta, links, st);
-    case kDSR12: return pack_u1_t<LinkU1<LinkDSR12, double>>(g, canon, theta, links, st);
+    case kDSR18: return pack_u1_t<LinkU1<LinkDSR18, double2>>(g, canon, theta, links, st);
+    case kDSR12: return pack_u1_t<LinkU1<LinkDSR12, double2>>(g, canon, theta, links, st);
     }
     return cudaErrorInvalidValue;
 }
@@ -272,8 +284,12 @@ __device__ __forceinline__ void copy_theta(const char *sblk, char *dblk, int Vh,
     if constexpr (LinkTraits<SrcT>::kU1) {
         using SB = typename LinkTraits<SrcT>::Base;
         using DB = typename LinkTraits<DstT>::Base;
-        const double th = (double)reinterpret_cast<const typename SrcT::Theta *>(sblk + (size_t)SB::kBytes * Vh)[h];
-        reinterpret_cast<typename DstT::Theta *>(dblk + (size_t)DB::kBytes * Vh)[h] = (typename DstT::Theta)th;
+        const typename SrcT::Theta v = reinterpret_cast<const typename SrcT::Theta *>(sblk + (size_t)SB::kBytes * Vh)[h];
+        typename DstT::Theta *d = reinterpret_cast<typename DstT::Theta *>(dblk + (size_t)DB::kBytes * Vh) + h;
+        if constexpr (std::is_same<typename SrcT::Theta, typename DstT::Theta>::value)
+            *d = v;
+        else
+            store_phase(d, angle_of(v));
     }
 }
 
@@ -337,11 +353,11 @@ stg_status ds_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge *
             case kF64R18: k_links_to_ds<LinkF64R18, LinkDSR18><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
             case kF64R12: k_links_to_ds<LinkF64R12, LinkDSR12><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
             case kF64R18 | kU1:
-                k_links_to_ds<LinkU1<LinkF64R18, double>, LinkU1<LinkDSR18, double>><<<nb, 256, 0, st>>>(g->g, g64->links,
+                k_links_to_ds<LinkU1<LinkF64R18, double2>, LinkU1<LinkDSR18, double2>><<<nb, 256, 0, st>>>(g->g, g64->links,
                                                                                                       g->links);
                 break;
             default:
-                k_links_to_ds<LinkU1<LinkF64R12, double>, LinkU1<LinkDSR12, double>><<<nb, 256, 0, st>>>(g->g, g64->links,
+                k_links_to_ds<LinkU1<LinkF64R12, double2>, LinkU1<LinkDSR12, double2>><<<nb, 256, 0, st>>>(g->g, g64->links,
                                                                                                       g->links);
                 break;
             }
@@ -384,10 +400,10 @@ stg_status f32_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge 
             case kF64R18: k_links_to_f32r12<LinkF64R18, LinkF32R12><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
             case kF64R12: k_links_to_f32r12<LinkF64R12, LinkF32R12><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
             case kF64R18 | kU1:
-                k_links_to_f32r12<LinkU1<LinkF64R18, double>, F32U><<<nb, 256, 0, st>>>(g->g, g64->links, g->links);
+                k_links_to_f32r12<LinkU1<LinkF64R18, double2>, F32U><<<nb, 256, 0, st>>>(g->g, g64->links, g->links);
                 break;
             default:
-                k_links_to_f32r12<LinkU1<LinkF64R12, double>, F32U><<<nb, 256, 0, st>>>(g->g, g64->links, g->links);
+                k_links_to_f32r12<LinkU1<LinkF64R12, double2>, F32U><<<nb, 256, 0, st>>>(g->g, g64->links, g->links);
                 break;
             }
             e = cudaGetLastError();

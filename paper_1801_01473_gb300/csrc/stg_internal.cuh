@@ -510,16 +510,28 @@ using LinkDSR18 = LinkDS<9>;
 using LinkDSR12 = LinkDS<6>;
 
 // Base of the (mu, parity) block of an internal link array.
-__device__ __forceinline__ void sincos_t(float t, float *s, float *c) { sincosf(t, s, c); }
-__device__ __forceinline__ void sincos_t(double t, double *s, double *c) { sincos(t, s, c); }
+// Phase factor exp(i theta) from its stored form: an angle (float: cos + i sin on line, the
+// paper's trade of 4 bytes for ~15 FP32 flops) or the precomputed pair (cos, sin) (double2: FP64
+// trigonometry costs more than the 16 bytes on GB300, whose FP64 rate is 1/64 of FP32).
+template <typename R>
+__device__ __forceinline__ cx<R> phase_of(float t)
+{
+    float sn, cs;
+    sincosf(t, &sn, &cs);
+    return cx<R>{R(cs), R(sn)};
+}
+template <typename R>
+__device__ __forceinline__ cx<R> phase_of(double2 p)
+{
+    return cx<R>{R(p.x), R(p.y)};
+}
 
 // A link with a U(1) phase u = exp(i theta) (Sec. 4.1: each flavour's U(1) field -- imaginary
-// chemical potential, background fields -- stored as the angle theta and turned into cos + i sin
-// on line).  Inside each (mu, parity) block the base link's chunks are followed by one chunk of
-// Vh angles of type T (float for FP32/16-bit links, double for FP64 and double-single links).
-// load() returns exp(i theta) U, so the backward hop, which uses the conjugate transpose, gets
-// exp(-i theta) U^dag with no change to the operator kernel.  The staggered and boundary signs
-// stay separate (from coordinates).
+// chemical potential, background fields).  Inside each (mu, parity) block the base link's chunks
+// are followed by one chunk of Vh phase entries of type T (float angle for FP32/16-bit links,
+// double2 (cos, sin) for FP64 and double-single links).  load() returns the SU(3) link; the
+// operator multiplies its products U v by phase() (and by the conjugate on the backward hop),
+// 3 complex products per link instead of 9.  The staggered and boundary signs stay separate.
 template <typename Base, typename T>
 struct LinkU1 {
     using R = typename Base::R;
@@ -532,18 +544,11 @@ struct LinkU1 {
     }
     __device__ __forceinline__ static cx<R> phase(const void *blk, int Vh, int h)
     {
-        T sn, cs;
-        sincos_t(__ldg(theta(blk, Vh) + h), &sn, &cs);
-        return cx<R>{R(cs), R(sn)};
+        return phase_of<R>(__ldg(theta(blk, Vh) + h));
     }
     __device__ __forceinline__ static void load(const void *blk, int Vh, int h, cx<R> U[3][3])
     {
         Base::load(blk, Vh, h, U);
-        const cx<R> e = phase(blk, Vh, h);
-#pragma unroll
-        for (int r = 0; r < 3; ++r)
-#pragma unroll
-            for (int c = 0; c < 3; ++c) U[r][c] = cmul(e, U[r][c]);
     }
     __device__ __forceinline__ static void pack(void *blk, int Vh, int h, const double2 *m) { Base::pack(blk, Vh, h, m); }
 };

@@ -30,13 +30,15 @@ namespace {
 using namespace su3;
 
 // Weighted staple sum C_mu(x) = rho * sum_{nu != mu} (upper + lower staple).
-__device__ M3 staple_sum(const double2 *__restrict__ U, const LinkGeo &g, int mu, long long i, double rho)
+template <typename T>
+__device__ M3T<T> staple_sum(const typename C2<T>::type *__restrict__ U, const LinkGeo &g, int mu, long long i,
+                             T rho)
 {
-    M3 c = zero3();
+    M3T<T> c = zero3<T>();
 #pragma unroll 1
     for (int nu = 0; nu < 4; ++nu) {
         if (nu == mu) continue;
-        M3 a, b, t;
+        M3T<T> a, b, t;
         // U_nu(x) U_mu(x+nu) U_nu(x+mu)^dag
         ld(U, g, nu, i, a);
         ld(U, g, mu, nb(g, i, nu, 1), b);
@@ -54,105 +56,110 @@ __device__ M3 staple_sum(const double2 *__restrict__ U, const LinkGeo &g, int mu
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int k = 0; k < 3; ++k) c.m[r][k] = cx<double>{rho * c.m[r][k].re, rho * c.m[r][k].im};
+        for (int k = 0; k < 3; ++k) c.m[r][k] = cx<T>{rho * c.m[r][k].re, rho * c.m[r][k].im};
     return c;
 }
 
 // Q = -i TA(C U^dag) and its square; returns nothing else
-__device__ __forceinline__ void make_q(const M3 &C, const M3 &u, M3 &q, M3 &q2)
+template <typename T>
+__device__ __forceinline__ void make_q(const M3T<T> &C, const M3T<T> &u, M3T<T> &q, M3T<T> &q2)
 {
-    const M3 a = ta(mul<false, true>(C, u));  // = i Q
+    const M3T<T> a = ta(mul<false, true>(C, u));  // = i Q
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) q.m[r][c] = cx<double>{a.m[r][c].im, -a.m[r][c].re};
+        for (int c = 0; c < 3; ++c) q.m[r][c] = cx<T>{a.m[r][c].im, -a.m[r][c].re};
     q2 = mul<false, false>(q, q);
 }
 
+template <typename T>
 struct StoutArgs {
+    using C = typename C2<T>::type;
     LinkGeo g;
-    double rho;
-    const double2 *U;     // links of this step
-    const double2 *G;     // gradient of the step's output (backward)
-    double2 *out;         // smeared links (forward) / gradient of U (backward)
-    double2 *Y;           // rho G_Omega U (backward)
+    T rho;
+    const C *U;  // links of this step
+    const C *G;  // gradient of the step's output (backward)
+    C *out;      // smeared links (forward) / gradient of U (backward)
+    C *Y;        // rho G_Omega U (backward)
 };
 
 constexpr int kStoutBlock = 128;
 
-__global__ void __launch_bounds__(kStoutBlock) k_stout_fwd(const __grid_constant__ StoutArgs a)
+template <typename T>
+__global__ void __launch_bounds__(kStoutBlock) k_stout_fwd(const __grid_constant__ StoutArgs<T> a)
 {
     const int mu = blockIdx.y;
     const long long i = (long long)blockIdx.x * kStoutBlock + threadIdx.x;
     if (i >= a.g.V) return;
-    M3 q, q2, u;
+    M3T<T> q, q2, u;
     {
-        const M3 C = staple_sum(a.U, a.g, mu, i, a.rho);
+        const M3T<T> C = staple_sum(a.U, a.g, mu, i, a.rho);
         ld(a.U, a.g, mu, i, u);
         make_q(C, u, q, q2);
     }
-    double c0, c1;
+    T c0, c1;
     char_coefs(q, q2, c0, c1);
-    const ExpCoef e = exp_coef<false>(c0, c1);
-    const M3 E = poly3(e.f, q, q2);
+    const ExpCoefT<T> e = exp_coef<false>(c0, c1);
+    const M3T<T> E = poly3(e.f, q, q2);
     st(a.out, a.g, mu, i, mul<false, false>(E, u));
 }
 
-__global__ void __launch_bounds__(kStoutBlock) k_stout_back_link(const __grid_constant__ StoutArgs a)
+template <typename T>
+__global__ void __launch_bounds__(kStoutBlock) k_stout_back_link(const __grid_constant__ StoutArgs<T> a)
 {
     const int mu = blockIdx.y;
     const long long i = (long long)blockIdx.x * kStoutBlock + threadIdx.x;
     if (i >= a.g.V) return;
-    M3 u, q, q2, gp;
-    const M3 C = staple_sum(a.U, a.g, mu, i, a.rho);
+    M3T<T> u, q, q2, gp;
+    const M3T<T> C = staple_sum(a.U, a.g, mu, i, a.rho);
     ld(a.U, a.g, mu, i, u);
     make_q(C, u, q, q2);
-    double c0, c1;
+    T c0, c1;
     char_coefs(q, q2, c0, c1);
-    const ExpCoef e = exp_coef<true>(c0, c1);
+    const ExpCoefT<T> e = exp_coef<true>(c0, c1);
     ld(a.G, a.g, mu, i, gp);
     // the link's own terms: E^dag G' (later + G_Omega^dag C)
-    M3 gu = mul<true, false>(poly3(e.f, q, q2), gp);
-    const M3 M = mul<false, true>(gp, u);  // gradient of E
-    // T_j = tr(M^dag Q^j);  K = sum_j Re(T_j df_j/dc)
-    cx<double> T[3] = {cx<double>{0.0, 0.0}, cx<double>{0.0, 0.0}, cx<double>{0.0, 0.0}};
+    M3T<T> gu = mul<true, false>(poly3(e.f, q, q2), gp);
+    const M3T<T> M = mul<false, true>(gp, u);  // gradient of E
+    // Tr_j = tr(M^dag Q^j);  K = sum_j Re(T_j df_j/dc)
+    cx<T> Tr[3] = {cx<T>{T(0), T(0)}, cx<T>{T(0), T(0)}, cx<T>{T(0), T(0)}};
 #pragma unroll
     for (int r = 0; r < 3; ++r) {
-        T[0] = cx<double>{T[0].re + M.m[r][r].re, T[0].im - M.m[r][r].im};
+        Tr[0] = cx<T>{Tr[0].re + M.m[r][r].re, Tr[0].im - M.m[r][r].im};
 #pragma unroll
         for (int k = 0; k < 3; ++k) {
-            cmac_conj(T[1], M.m[k][r], q.m[k][r]);
-            cmac_conj(T[2], M.m[k][r], q2.m[k][r]);
+            cmac_conj(Tr[1], M.m[k][r], q.m[k][r]);
+            cmac_conj(Tr[2], M.m[k][r], q2.m[k][r]);
         }
     }
-    double K0 = 0.0, K1 = 0.0;
+    T K0 = T(0), K1 = T(0);
 #pragma unroll
     for (int j = 0; j < 3; ++j) {
-        K0 += T[j].re * e.d0[j].re - T[j].im * e.d0[j].im;
-        K1 += T[j].re * e.d1[j].re - T[j].im * e.d1[j].im;
+        K0 += Tr[j].re * e.d0[j].re - Tr[j].im * e.d0[j].im;
+        K1 += Tr[j].re * e.d1[j].re - Tr[j].im * e.d1[j].im;
     }
     // G_Q = K1 Q + K0 Q^2 + conj(f1) M + conj(f2) (M Q + Q M)
-    M3 gq = mul<false, false>(M, q);
+    M3T<T> gq = mul<false, false>(M, q);
     mul_acc<false, false>(gq, q, M);
-    const cx<double> f1c = cconj(e.f[1]), f2c = cconj(e.f[2]);
+    const cx<T> f1c = cconj(e.f[1]), f2c = cconj(e.f[2]);
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-            cx<double> v = cmul(f2c, gq.m[r][c]);
+            cx<T> v = cmul(f2c, gq.m[r][c]);
             cmac(v, f1c, M.m[r][c]);
             v.re += K1 * q.m[r][c].re + K0 * q2.m[r][c].re;
             v.im += K1 * q.m[r][c].im + K0 * q2.m[r][c].im;
-            gq.m[r][c] = cx<double>{-v.im, v.re};  // i G_Q
+            gq.m[r][c] = cx<T>{-v.im, v.re};  // i G_Q
         }
-    const M3 go = ta(gq);  // G_Omega
+    const M3T<T> go = ta(gq);  // G_Omega
     mul_acc<true, false>(gu, go, C);
     st(a.out, a.g, mu, i, gu);
-    M3 y = mul<false, false>(go, u);
+    M3T<T> y = mul<false, false>(go, u);
 #pragma unroll
     for (int r = 0; r < 3; ++r)
 #pragma unroll
-        for (int c = 0; c < 3; ++c) y.m[r][c] = cx<double>{a.rho * y.m[r][c].re, a.rho * y.m[r][c].im};
+        for (int c = 0; c < 3; ++c) y.m[r][c] = cx<T>{a.rho * y.m[r][c].re, a.rho * y.m[r][c].im};
     st(a.Y, a.g, mu, i, y);
 }
 
@@ -164,19 +171,20 @@ __global__ void __launch_bounds__(kStoutBlock) k_stout_back_link(const __grid_co
 //   C_mu(y-mu+nu) as the last factor of the lower staple       -> U_mu(y-mu)^dag U_nu(y-mu) Y_mu(y-mu+nu)
 //   C_nu(y-mu)    as the middle factor of the upper staple     -> U_mu(y-mu)^dag Y_nu(y-mu) U_mu(y-mu+nu)
 // with Y the gradient of the unweighted staple sums.
-__global__ void __launch_bounds__(kStoutBlock) k_stout_back_staples(const __grid_constant__ StoutArgs a)
+template <typename T>
+__global__ void __launch_bounds__(kStoutBlock) k_stout_back_staples(const __grid_constant__ StoutArgs<T> a)
 {
     const int nu = blockIdx.y;
     const long long i = (long long)blockIdx.x * kStoutBlock + threadIdx.x;
     if (i >= a.g.V) return;
-    M3 acc;
+    M3T<T> acc;
     ld(a.out, a.g, nu, i, acc);
 #pragma unroll 1
     for (int mu = 0; mu < 4; ++mu) {
         if (mu == nu) continue;
         const long long yp = nb(a.g, i, mu, 1), yn = nb(a.g, i, nu, 1);
         const long long ym = nb(a.g, i, mu, -1), ymn = nb(a.g, ym, nu, 1);
-        M3 p, q, t;
+        M3T<T> p, q, t;
         // forward side: U_nu(y+mu) shared by the first two terms
         ld(a.U, a.g, nu, yp, p);   // U_nu(y+mu)
         ld(a.U, a.g, mu, yn, q);   // U_mu(y+nu)
@@ -209,12 +217,13 @@ __global__ void __launch_bounds__(kStoutBlock) k_stout_back_staples(const __grid
 }
 
 // F = TA(U G^dag) in place over G
-__global__ void __launch_bounds__(kStoutBlock) k_lie_force(const __grid_constant__ StoutArgs a)
+template <typename T>
+__global__ void __launch_bounds__(kStoutBlock) k_lie_force(const __grid_constant__ StoutArgs<T> a)
 {
     const int mu = blockIdx.y;
     const long long i = (long long)blockIdx.x * kStoutBlock + threadIdx.x;
     if (i >= a.g.V) return;
-    M3 u, gr;
+    M3T<T> u, gr;
     ld(a.U, a.g, mu, i, u);
     ld(a.out, a.g, mu, i, gr);
     st(a.out, a.g, mu, i, ta(mul<false, true>(u, gr)));
@@ -231,81 +240,99 @@ stg_status check_common(const stg_lattice *lat, int nstep, double rho, const cha
 
 bool misaligned(const void *p) { return p == nullptr || (reinterpret_cast<uintptr_t>(p) & 15) != 0; }
 
+template <typename T>
+cudaError_t smear_t(const LinkGeo &g, int nstep, double rho, const void *links, void *levels, cudaStream_t st)
+{
+    using C = typename C2<T>::type;
+    StoutArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.rho = (T)rho;
+    const size_t level = (size_t)4 * g.V * 9;  // complex numbers per level
+    const dim3 grid((unsigned)((g.V + kStoutBlock - 1) / kStoutBlock), 4);
+    for (int k = 0; k < nstep; ++k) {
+        a.U = k == 0 ? static_cast<const C *>(links) : static_cast<const C *>(levels) + (size_t)(k - 1) * level;
+        a.out = static_cast<C *>(levels) + (size_t)k * level;
+        k_stout_fwd<T><<<grid, kStoutBlock, 0, st>>>(a);
+        const cudaError_t e = cudaGetLastError();
+        if (e != cudaSuccess) return e;
+    }
+    return cudaSuccess;
+}
+
+template <typename T>
+cudaError_t force_t(const LinkGeo &g, int nstep, double rho, const void *links, const void *levels, const void *grad,
+                    void *out_v, int kind, cudaStream_t st)
+{
+    using C = typename C2<T>::type;
+    StoutArgs<T> a;
+    memset(&a, 0, sizeof(a));
+    a.g = g;
+    a.rho = (T)rho;
+    const size_t level = (size_t)4 * g.V * 9;
+    C *ws = nullptr;
+    cudaError_t e = cudaMallocAsync((void **)&ws, 2 * level * sizeof(C), st);
+    if (e != cudaSuccess) return e;
+    C *Y = ws, *tmp = ws + level, *out = static_cast<C *>(out_v);
+    const dim3 grid((unsigned)((g.V + kStoutBlock - 1) / kStoutBlock), 4);
+    const C *g_in = static_cast<const C *>(grad);
+    for (int k = nstep - 1; k >= 0 && e == cudaSuccess; --k) {
+        // the last step (k = 0) lands in out; earlier ones alternate so that it does
+        C *dst = (k % 2 == 0) ? out : tmp;
+        a.U = k == 0 ? static_cast<const C *>(links) : static_cast<const C *>(levels) + (size_t)(k - 1) * level;
+        a.G = g_in;
+        a.out = dst;
+        a.Y = Y;
+        k_stout_back_link<T><<<grid, kStoutBlock, 0, st>>>(a);
+        k_stout_back_staples<T><<<grid, kStoutBlock, 0, st>>>(a);
+        e = cudaGetLastError();
+        g_in = dst;
+    }
+    if (e == cudaSuccess && kind == 0) {
+        a.U = static_cast<const C *>(links);
+        a.out = out;
+        k_lie_force<T><<<grid, kStoutBlock, 0, st>>>(a);
+        e = cudaGetLastError();
+    }
+    const cudaError_t f = cudaFreeAsync(ws, st);
+    return e != cudaSuccess ? e : f;
+}
+
 }  // namespace
 }  // namespace stg
 
 using namespace stg;
 
-extern "C" stg_status stg_stout_smear(const stg_lattice *lat, int32_t nstep, double rho, const void *links_c128_dev,
-                                      void *levels_c128_dev, void *stream)
+extern "C" stg_status stg_stout_smear(const stg_lattice *lat, stg_prec prec, int32_t nstep, double rho,
+                                      const void *links_dev, void *levels_dev, void *stream)
 {
     stg_status s = check_common(lat, nstep, rho, "stg_stout_smear");
     if (s != STG_OK) return s;
-    if (misaligned(links_c128_dev) || misaligned(levels_c128_dev))
+    if (prec != STG_F64 && prec != STG_F32) return set_error(STG_ERR_ARG, "stg_stout_smear: prec must be F64 or F32");
+    if (misaligned(links_dev) || misaligned(levels_dev))
         return set_error(STG_ERR_ARG, "stg_stout_smear: buffers must be non-null and 16-byte aligned");
+    const LinkGeo g = link_geo(lat->g);
     cudaStream_t st = (cudaStream_t)stream;
-    StoutArgs a;
-    memset(&a, 0, sizeof(a));
-    a.g = link_geo(lat->g);
-    a.rho = rho;
-    const size_t level = (size_t)4 * a.g.V * 9;  // double2 per level
-    const dim3 grid((unsigned)((a.g.V + kStoutBlock - 1) / kStoutBlock), 4);
-    for (int k = 0; k < nstep; ++k) {
-        a.U = k == 0 ? static_cast<const double2 *>(links_c128_dev)
-                     : static_cast<const double2 *>(levels_c128_dev) + (size_t)(k - 1) * level;
-        a.out = static_cast<double2 *>(levels_c128_dev) + (size_t)k * level;
-        k_stout_fwd<<<grid, kStoutBlock, 0, st>>>(a);
-        STG_CUDA_TRY(cudaGetLastError());
-    }
+    STG_CUDA_TRY(prec == STG_F64 ? smear_t<double>(g, nstep, rho, links_dev, levels_dev, st)
+                                 : smear_t<float>(g, nstep, rho, links_dev, levels_dev, st));
     return STG_OK;
 }
 
-extern "C" stg_status stg_stout_force(const stg_lattice *lat, int32_t nstep, double rho, const void *links_c128_dev,
-                                      const void *levels_c128_dev, const void *grad_c128_dev, void *out_c128_dev,
-                                      int32_t kind, void *stream)
+extern "C" stg_status stg_stout_force(const stg_lattice *lat, stg_prec prec, int32_t nstep, double rho,
+                                      const void *links_dev, const void *levels_dev, const void *grad_dev,
+                                      void *out_dev, int32_t kind, void *stream)
 {
     stg_status s = check_common(lat, nstep, rho, "stg_stout_force");
     if (s != STG_OK) return s;
-    if (misaligned(links_c128_dev) || misaligned(grad_c128_dev) || misaligned(out_c128_dev) ||
-        (nstep > 1 && misaligned(levels_c128_dev)))
+    if (prec != STG_F64 && prec != STG_F32) return set_error(STG_ERR_ARG, "stg_stout_force: prec must be F64 or F32");
+    if (misaligned(links_dev) || misaligned(grad_dev) || misaligned(out_dev) || (nstep > 1 && misaligned(levels_dev)))
         return set_error(STG_ERR_ARG, "stg_stout_force: buffers must be non-null and 16-byte aligned");
     if (kind != 0 && kind != 1) return set_error(STG_ERR_ARG, "stg_stout_force: kind must be 0 or 1");
-    if (out_c128_dev == grad_c128_dev || out_c128_dev == links_c128_dev)
+    if (out_dev == grad_dev || out_dev == links_dev)
         return set_error(STG_ERR_ARG, "stg_stout_force: out must not alias the inputs");
+    const LinkGeo g = link_geo(lat->g);
     cudaStream_t st = (cudaStream_t)stream;
-    StoutArgs a;
-    memset(&a, 0, sizeof(a));
-    a.g = link_geo(lat->g);
-    a.rho = rho;
-    const size_t level = (size_t)4 * a.g.V * 9;
-    double2 *ws = nullptr;
-    STG_CUDA_TRY(cudaMallocAsync((void **)&ws, 2 * level * sizeof(double2), st));
-    struct Free {
-        void *p;
-        cudaStream_t s;
-        ~Free() { cudaFreeAsync(p, s); }
-    } fr{ws, st};
-    double2 *Y = ws, *tmp = ws + level, *out = static_cast<double2 *>(out_c128_dev);
-    const dim3 grid((unsigned)((a.g.V + kStoutBlock - 1) / kStoutBlock), 4);
-    const double2 *g_in = static_cast<const double2 *>(grad_c128_dev);
-    for (int k = nstep - 1; k >= 0; --k) {
-        // the last step (k = 0) lands in out; earlier ones alternate so that it does
-        double2 *dst = (k % 2 == 0) ? out : tmp;
-        a.U = k == 0 ? static_cast<const double2 *>(links_c128_dev)
-                     : static_cast<const double2 *>(levels_c128_dev) + (size_t)(k - 1) * level;
-        a.G = g_in;
-        a.out = dst;
-        a.Y = Y;
-        k_stout_back_link<<<grid, kStoutBlock, 0, st>>>(a);
-        k_stout_back_staples<<<grid, kStoutBlock, 0, st>>>(a);
-        STG_CUDA_TRY(cudaGetLastError());
-        g_in = dst;
-    }
-    if (kind == 0) {
-        a.U = static_cast<const double2 *>(links_c128_dev);
-        a.out = out;
-        k_lie_force<<<grid, kStoutBlock, 0, st>>>(a);
-        STG_CUDA_TRY(cudaGetLastError());
-    }
+    STG_CUDA_TRY(prec == STG_F64 ? force_t<double>(g, nstep, rho, links_dev, levels_dev, grad_dev, out_dev, kind, st)
+                                 : force_t<float>(g, nstep, rho, links_dev, levels_dev, grad_dev, out_dev, kind, st));
     return STG_OK;
 }

@@ -27,7 +27,7 @@ EXPORTS = [
     "stg_dslash_eo", "stg_dslash_oe", "stg_dslash_multi", "stg_normal_op", "stg_normal_op_noalloc",
     "stg_mscg_solve", "stg_mscg_solve_batched", "stg_fermion_force",
     "stg_stout_smear", "stg_stout_force", "stg_gauge_action", "stg_gauge_force",
-    "stg_md_momenta", "stg_md_update_links", "stg_md_update_momenta", "stg_md_kinetic",
+    "stg_md_momenta", "stg_md_update_links", "stg_md_update_momenta", "stg_md_kinetic", "stg_complex_convert",
 ]
 
 
@@ -93,14 +93,15 @@ def lib() -> ctypes.CDLL:
     L.stg_mscg_solve.argtypes = [P, P, ctypes.POINTER(MscgParams), P, PP, ctypes.POINTER(MscgStats), P]
     L.stg_mscg_solve_batched.argtypes = [I32, ctypes.POINTER(Instance), ctypes.POINTER(MscgParams), P]
     L.stg_fermion_force.argtypes = [P, I32, ctypes.POINTER(D), PP, P, I32, P]
-    L.stg_stout_smear.argtypes = [P, I32, D, P, P, P]
-    L.stg_stout_force.argtypes = [P, I32, D, P, P, P, P, I32, P]
+    L.stg_stout_smear.argtypes = [P, ctypes.c_int, I32, D, P, P, P]
+    L.stg_stout_force.argtypes = [P, ctypes.c_int, I32, D, P, P, P, P, I32, P]
     L.stg_gauge_action.argtypes = [P, D, P, P, P]
     L.stg_gauge_create_u1.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(P)]
-    L.stg_gauge_force.argtypes = [P, D, P, P, I32, P]
+    L.stg_gauge_force.argtypes = [P, ctypes.c_int, D, P, P, I32, P]
     L.stg_md_momenta.argtypes = [P, P, P, P]
     L.stg_md_update_links.argtypes = [P, D, P, P, P]
-    L.stg_md_update_momenta.argtypes = [P, D, P, P, P]
+    L.stg_md_update_momenta.argtypes = [P, ctypes.c_int, D, P, P, P]
+    L.stg_complex_convert.argtypes = [ctypes.c_int64, ctypes.c_int, P, ctypes.c_int, P, P]
     L.stg_md_kinetic.argtypes = [P, P, P, P]
     for name in EXPORTS:
         f = getattr(L, name)
@@ -110,7 +111,7 @@ def lib() -> ctypes.CDLL:
                                                  "stg_mscg_solve_batched", "stg_fermion_force",
                                                  "stg_stout_smear", "stg_stout_force", "stg_gauge_action",
                                                  "stg_gauge_force", "stg_gauge_create_u1", "stg_md_momenta", "stg_md_update_links",
-                                                 "stg_md_update_momenta", "stg_md_kinetic"):
+                                                 "stg_md_update_momenta", "stg_md_kinetic", "stg_complex_convert"):
             f.restype = ctypes.c_int
     _lib = L
     return L

@@ -86,17 +86,19 @@ def test_stout_arguments_rejected_before_launch(L):
     rc, h = _lat(L, (4, 4, 4, 4))
     a, b, c, d = (ctypes.c_void_p(v) for v in (256, 512, 768, 1024))
     smear, force = L.stg_stout_smear, L.stg_stout_force
-    assert smear(None, 1, 0.1, a, b, None) == -1
-    assert smear(h, 0, 0.1, a, b, None) == -1 and b"nstep" in L.stg_last_error()
-    assert smear(h, 17, 0.1, a, b, None) == -1
-    assert smear(h, 1, 0.6, a, b, None) == -1 and b"rho" in L.stg_last_error()
-    assert smear(h, 1, float("nan"), a, b, None) == -1
-    assert smear(h, 1, 0.1, ctypes.c_void_p(8), b, None) == -1
-    assert smear(h, 1, 0.1, a, None, None) == -1
-    assert force(h, 2, 0.1, a, b, c, d, 2, None) == -1 and b"kind" in L.stg_last_error()
-    assert force(h, 2, 0.1, a, b, c, c, 1, None) == -1 and b"alias" in L.stg_last_error()
-    assert force(h, 2, 0.1, a, None, c, d, 1, None) == -1
-    assert force(h, 2, -0.51, a, b, c, d, 1, None) == -1
+    assert smear(None, 0, 1, 0.1, a, b, None) == -1
+    assert smear(h, 0, 0, 0.1, a, b, None) == -1 and b"nstep" in L.stg_last_error()
+    assert smear(h, 0, 17, 0.1, a, b, None) == -1
+    assert smear(h, 0, 1, 0.6, a, b, None) == -1 and b"rho" in L.stg_last_error()
+    assert smear(h, 0, 1, float("nan"), a, b, None) == -1
+    assert smear(h, 0, 1, 0.1, ctypes.c_void_p(8), b, None) == -1
+    assert smear(h, 0, 1, 0.1, a, None, None) == -1
+    assert smear(h, 2, 1, 0.1, a, b, None) == -1 and b"prec" in L.stg_last_error()
+    assert force(h, 0, 2, 0.1, a, b, c, d, 2, None) == -1 and b"kind" in L.stg_last_error()
+    assert force(h, 0, 2, 0.1, a, b, c, c, 1, None) == -1 and b"alias" in L.stg_last_error()
+    assert force(h, 1, 2, 0.1, a, None, c, d, 1, None) == -1
+    assert force(h, 0, 2, -0.51, a, b, c, d, 1, None) == -1
+    assert force(h, 4, 2, 0.1, a, b, c, d, 1, None) == -1 and b"prec" in L.stg_last_error()
     L.stg_lattice_destroy(h)
 
 
@@ -111,11 +113,16 @@ def test_gauge_and_md_arguments_rejected_before_launch(L):
     assert L.stg_gauge_action(None, 5.0, a, ctypes.c_void_p(1024), None) == -1
     assert L.stg_gauge_action(h, 5.0, ctypes.c_void_p(8), ctypes.c_void_p(1024), None) == -1
     assert L.stg_gauge_action(h, float("inf"), a, ctypes.c_void_p(1024), None) == -1
-    assert L.stg_gauge_force(h, 5.0, a, a, 0, None) == -1 and b"alias" in L.stg_last_error()
-    assert L.stg_gauge_force(h, 5.0, a, b, 3, None) == -1 and b"kind" in L.stg_last_error()
+    assert L.stg_gauge_force(h, 0, 5.0, a, a, 0, None) == -1 and b"alias" in L.stg_last_error()
+    assert L.stg_gauge_force(h, 1, 5.0, a, b, 3, None) == -1 and b"kind" in L.stg_last_error()
+    assert L.stg_gauge_force(h, 3, 5.0, a, b, 0, None) == -1 and b"prec" in L.stg_last_error()
     assert L.stg_md_momenta(h, None, b, None) == -1
     assert L.stg_md_update_links(h, 0.1, a, a, None) == -1 and b"alias" in L.stg_last_error()
     assert L.stg_md_update_links(h, 2.0, a, b, None) == -1 and b"eps" in L.stg_last_error()
-    assert L.stg_md_update_momenta(h, float("nan"), a, b, None) == -1
+    assert L.stg_md_update_momenta(h, 0, float("nan"), a, b, None) == -1
+    assert L.stg_md_update_momenta(h, 2, 0.1, a, b, None) == -1
+    assert L.stg_complex_convert(10, 0, a, 1, a, None) == -1
+    assert L.stg_complex_convert(-1, 0, a, 1, b, None) == -1
+    assert L.stg_complex_convert(10, 3, a, 1, b, None) == -1
     assert L.stg_md_kinetic(h, a, None, None) == -1
     L.stg_lattice_destroy(h)

@@ -88,3 +88,15 @@ def test_48_sampled_gradient_and_unit_action(p):
     del grad
     ud.copy_(torch.eye(3, dtype=torch.complex128, device="cuda").expand(4, v, 3, 3))
     assert p.gauge_action(lat, ud, BETA)["action"] == pytest.approx(-9.0 * BETA * v, rel=1e-14)
+
+
+@pytest.mark.parametrize("dims,kind,seed", CASES)
+@pytest.mark.parametrize("out_kind", [1, 0])
+def test_fp32_force_matches_oracle(p, dims, kind, seed, out_kind):
+    """Single-precision gauge force (complex64 links, FP32 arithmetic): 2e-5 relative."""
+    u = S.gauge_links(dims, kind, seed)
+    want = og.gradient(dims, u, BETA) if out_kind == 1 else og.force(dims, u, BETA)
+    u32 = p.complex_convert(_gpu(u), torch.complex64)
+    got = p.gauge_force(p.Lattice(dims), u32, BETA, kind=out_kind)
+    assert got.dtype == torch.complex64
+    assert np.abs(got.cpu().numpy().astype(np.complex128) - want).max() <= 2e-5 * np.abs(want).max()

@@ -133,3 +133,28 @@ def test_metropolis_decision(p):
     assert r1["accepted"] == (r1["dH"] <= 0.0 or math.nextafter(1.0, 0.0) < math.exp(-r1["dH"]))
     if not r1["accepted"]:
         assert r1["links"] is u
+
+
+def test_single_precision_forces(p):
+    """MD with single-precision forces (gauge force, smearing and chain rule in FP32): the
+    Hamiltonian is still conserved to O(eps^2), and a trajectory stays within FP32 rounding of the
+    FP64 one."""
+    dims = (4, 4, 4, 4)
+    lat = p.Lattice(dims)
+    u, a64, _ = _actions(p, dims, lat)
+    a32 = p.md.Action(lat, beta=a64.beta, mass=a64.mass, pseudofermions=a64.pseudofermions, tol=a64.tol,
+                      stout_rho=a64.stout_rho, stout_steps=a64.stout_steps, precision="f32")
+    xi = _gpu(_xi(163, u.shape[1]))
+
+    def run(act, n):
+        ud, h = _gpu(u), p.md_momenta(lat, xi)
+        h0 = p.md.hamiltonian(act, ud, h)
+        p.md.omelyan(act, ud, h, 0.4, n)
+        return p.md.hamiltonian(act, ud, h) - h0, ud
+
+    d1, u1 = run(a32, 3)
+    d2, _ = run(a32, 6)
+    assert 3.2 < d1 / d2 < 4.8
+    d64, u64 = run(a64, 3)
+    assert float((u1 - u64).abs().max()) < 1e-5
+    assert d1 == pytest.approx(d64, rel=1e-4, abs=1e-5)

@@ -209,3 +209,32 @@ def test_48_force_finite_differences(p, big):
         an = float((grad[mu, s].conj() * du).real.sum())
         assert an == pytest.approx(fd, rel=1e-6, abs=1e-9)
         del lp, lm, up
+
+
+@pytest.mark.parametrize("dims,kind,seed,rho,nstep", CASES[:2])
+@pytest.mark.parametrize("out_kind", [1, 0])
+def test_fp32_smear_and_chain(p, dims, kind, seed, rho, nstep, out_kind):
+    """Single-precision variants (complex64 arrays, FP32 arithmetic) against the FP64 oracle at
+    FP32 tolerances: links 5e-6 absolute, pulled-back gradient 2e-5 relative."""
+    u = S.gauge_links(dims, kind, seed)
+    g = np.random.default_rng(seed + 200)
+    z = g.standard_normal(u.shape) + 1j * g.standard_normal(u.shape)
+    lat = p.Lattice(dims)
+    u32 = p.complex_convert(_gpu(u), torch.complex64)
+    levels = p.stout_smear(lat, u32, rho, nstep)
+    assert levels.dtype == torch.complex64
+    want = ost.stout(dims, u, rho, nstep)
+    for k in range(nstep):
+        assert np.abs(levels[k].cpu().numpy().astype(np.complex128) - want[k + 1]).max() < 5e-6
+    gw = ost.stout_backward(dims, want, rho, z)
+    if out_kind == 0:
+        gw = ost.lie_force(u, gw)
+    got = p.stout_force(lat, u32, levels, rho, p.complex_convert(_gpu(z), torch.complex64), kind=out_kind)
+    assert np.abs(got.cpu().numpy().astype(np.complex128) - gw).max() <= 2e-5 * np.abs(gw).max()
+
+
+def test_complex_convert_round_trip(p):
+    x = torch.randn(1000, dtype=torch.complex64, device="cuda")
+    y = p.complex_convert(x, torch.complex128)
+    assert torch.equal(y, x.to(torch.complex128))
+    assert torch.equal(p.complex_convert(y, torch.complex64), x)

@@ -344,30 +344,32 @@ def time_stout(torch, p):
     cfg = S.CONFIGS["force_48x48x48x48"]
     dims = cfg["dims"]
     lat = p.Lattice(dims)
-    ut = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
+    u64 = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
     rho, nstep = 0.15, 2
-    g = torch.Generator(device="cuda").manual_seed(3000 + cfg["k"])
-    z = torch.complex(torch.randn(ut.shape, dtype=torch.float64, device="cuda", generator=g),
-                      torch.randn(ut.shape, dtype=torch.float64, device="cuda", generator=g))
-    levels = p.stout_smear(lat, ut, rho, nstep)
-    f = p.stout_force(lat, ut, levels, rho, z, kind=1)
-    torch.cuda.synchronize()
-    e0, e1, e2 = events(torch) + (torch.cuda.Event(enable_timing=True),)
-    e0.record()
-    for _ in range(3):
+    out = {"lattice": "48^4", "steps": nstep, "rho": rho}
+    for tag, ut in (("fp64", u64), ("fp32", p.complex_convert(u64, torch.complex64))):
+        g = torch.Generator(device="cuda").manual_seed(3000 + cfg["k"])
+        z = torch.randn(ut.shape, dtype=ut.dtype, device="cuda", generator=g)
         levels = p.stout_smear(lat, ut, rho, nstep)
-    e1.record()
-    for _ in range(3):
         f = p.stout_force(lat, ut, levels, rho, z, kind=1)
-    e2.record()
-    torch.cuda.synchronize()
-    t_s, t_f = e0.elapsed_time(e1) / 3, e1.elapsed_time(e2) / 3
-    links = 4 * lat.V * nstep
-    del f, levels, z, ut
-    return {"lattice": "48^4", "steps": nstep, "rho": rho, "smear_ms": round(t_s, 3), "force_ms": round(t_f, 3),
-            "smear_fp64_tflops": round(links * STOUT_FWD_FLOPS / t_s / 1e9, 3),
-            "force_fp64_tflops": round(links * STOUT_BWD_FLOPS / t_f / 1e9, 3),
-            "note": "FP64, canonical link layout; flops algorithmic (216 per complex 3x3 product)"}
+        torch.cuda.synchronize()
+        e0, e1, e2 = events(torch) + (torch.cuda.Event(enable_timing=True),)
+        e0.record()
+        for _ in range(3):
+            levels = p.stout_smear(lat, ut, rho, nstep)
+        e1.record()
+        for _ in range(3):
+            f = p.stout_force(lat, ut, levels, rho, z, kind=1)
+        e2.record()
+        torch.cuda.synchronize()
+        t_s, t_f = e0.elapsed_time(e1) / 3, e1.elapsed_time(e2) / 3
+        links = 4 * lat.V * nstep
+        out[tag] = {"smear_ms": round(t_s, 3), "force_ms": round(t_f, 3),
+                    "smear_tflops": round(links * STOUT_FWD_FLOPS / t_s / 1e9, 3),
+                    "force_tflops": round(links * STOUT_BWD_FLOPS / t_f / 1e9, 3)}
+        del f, levels, z
+    out["note"] = "canonical link layout; fp32 = complex64 links (single-precision MD); flops algorithmic"
+    return out
 
 
 # Tree-level Symanzik gauge force: 6 plaquette + 18 rectangle staples per link = 84 complex 3x3
@@ -380,28 +382,35 @@ def time_gauge(torch, p):
     cfg = S.CONFIGS["force_48x48x48x48"]
     dims = cfg["dims"]
     lat = p.Lattice(dims)
-    ut = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
+    u64 = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
     beta = 5.6
-    f = p.gauge_force(lat, ut, beta, kind=0)
-    p.gauge_action(lat, ut, beta)
+    out = {"lattice": "48^4"}
+    for tag, ut in (("fp64", u64), ("fp32", p.complex_convert(u64, torch.complex64))):
+        f = p.gauge_force(lat, ut, beta, kind=0)
+        torch.cuda.synchronize()
+        e0, e1 = events(torch)
+        e0.record()
+        for _ in range(3):
+            f = p.gauge_force(lat, ut, beta, kind=0)
+        e1.record()
+        torch.cuda.synchronize()
+        t_f = e0.elapsed_time(e1) / 3
+        out[tag] = {"force_ms": round(t_f, 3), "force_tflops": round(4 * lat.V * GAUGE_FORCE_FLOPS / t_f / 1e9, 3)}
+        del f
+    p.gauge_action(lat, u64, beta)
+    res = torch.empty(3, dtype=torch.float64, device="cuda")
     torch.cuda.synchronize()
-    e0, e1, e2 = events(torch) + (torch.cuda.Event(enable_timing=True),)
+    e0, e1 = events(torch)
     e0.record()
     for _ in range(3):
-        f = p.gauge_force(lat, ut, beta, kind=0)
-    e1.record()
-    out = torch.empty(3, dtype=torch.float64, device="cuda")
-    for _ in range(3):
-        p.lib().stg_gauge_action(lat.handle, beta, ut.data_ptr(), out.data_ptr(),
+        p.lib().stg_gauge_action(lat.handle, beta, u64.data_ptr(), res.data_ptr(),
                                  torch.cuda.current_stream().cuda_stream)
-    e2.record()
+    e1.record()
     torch.cuda.synchronize()
-    t_f, t_a = e0.elapsed_time(e1) / 3, e1.elapsed_time(e2) / 3
-    del f, ut
-    return {"lattice": "48^4", "force_ms": round(t_f, 3), "action_ms": round(t_a, 3),
-            "force_fp64_tflops": round(4 * lat.V * GAUGE_FORCE_FLOPS / t_f / 1e9, 3),
-            "action_fp64_tflops": round(lat.V * GAUGE_ACTION_FLOPS / t_a / 1e9, 3),
-            "note": "tree-level Symanzik, FP64, canonical link layout; flops algorithmic"}
+    t_a = e0.elapsed_time(e1) / 3
+    out["fp64"].update({"action_ms": round(t_a, 3), "action_tflops": round(lat.V * GAUGE_ACTION_FLOPS / t_a / 1e9, 3)})
+    out["note"] = "tree-level Symanzik, canonical link layout; fp32 = complex64 links (single-precision MD)"
+    return out
 
 
 def run_gpu(args):

@@ -199,6 +199,23 @@ def dslash_eo(gauge: Gauge, psi_odd: torch.Tensor) -> torch.Tensor:
     return _canon_apply(gauge, psi_odd, lambda x: dslash_eo_(gauge, torch.empty_like(x), x))
 
 
+def dslash_host(gauge: Gauge, out_parity: int, fields: torch.Tensor, out: torch.Tensor | None = None,
+                stream=None) -> torch.Tensor:
+    """D_eo (out_parity 0) or D_oe (1) of a batch of canonical complex128 host fields [n, Vh, 3]
+    (pinned for overlap), streamed through the device by stg_dslash_host; returns host fields."""
+    if fields.is_cuda or fields.dtype != torch.complex128:
+        raise TypeError("dslash_host: fields must be complex128 host tensors")
+    src = fields.contiguous().reshape(-1, gauge.lattice.Vh, 3)
+    n = src.shape[0]
+    if out is None:
+        out = torch.empty(src.shape, dtype=src.dtype, pin_memory=src.is_pinned())
+    pi = (ctypes.c_void_p * n)(*[src[k].data_ptr() for k in range(n)])
+    po = (ctypes.c_void_p * n)(*[out[k].data_ptr() for k in range(n)])
+    check(lib().stg_dslash_host(gauge.handle, int(out_parity), n, ctypes.cast(pi, ctypes.POINTER(ctypes.c_void_p)),
+                                ctypes.cast(po, ctypes.POINTER(ctypes.c_void_p)), _stream(stream)), "stg_dslash_host")
+    return out
+
+
 def dslash_oe(gauge: Gauge, psi_even: torch.Tensor) -> torch.Tensor:
     """D_oe psi_even on canonical complex128 [Vh, 3] fields (host or device)."""
     return _canon_apply(gauge, psi_even, lambda x: dslash_oe_(gauge, torch.empty_like(x), x))

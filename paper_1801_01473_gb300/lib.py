@@ -24,7 +24,7 @@ EXPORTS = [
     "stg_lattice_create", "stg_lattice_destroy", "stg_lattice_sites",
     "stg_gauge_create", "stg_gauge_create_u1", "stg_gauge_destroy", "stg_gauge_bytes",
     "stg_field_bytes", "stg_field_pack", "stg_field_unpack",
-    "stg_dslash_eo", "stg_dslash_oe", "stg_dslash_multi", "stg_normal_op", "stg_normal_op_noalloc",
+    "stg_dslash_eo", "stg_dslash_oe", "stg_dslash_multi", "stg_dslash_host", "stg_normal_op", "stg_normal_op_noalloc",
     "stg_mscg_solve", "stg_mscg_solve_batched", "stg_fermion_force",
     "stg_stout_smear", "stg_stout_force", "stg_gauge_action", "stg_gauge_force",
     "stg_md_momenta", "stg_md_update_links", "stg_md_update_momenta", "stg_md_kinetic", "stg_complex_convert",
@@ -88,6 +88,7 @@ def lib() -> ctypes.CDLL:
     L.stg_dslash_eo.argtypes = [P, P, P, P]
     L.stg_dslash_oe.argtypes = [P, P, P, P]
     L.stg_dslash_multi.argtypes = [P, I32, I32, P, P, SZ, P]
+    L.stg_dslash_host.argtypes = [P, I32, I32, PP, PP, P]
     L.stg_normal_op.argtypes = [P, D, D, P, P, P, P, P]
     L.stg_normal_op_noalloc.argtypes = [P, D, D, P, P, P, P]
     L.stg_mscg_solve.argtypes = [P, P, ctypes.POINTER(MscgParams), P, PP, ctypes.POINTER(MscgStats), P]
@@ -107,7 +108,7 @@ def lib() -> ctypes.CDLL:
         f = getattr(L, name)
         if f.restype is ctypes.c_int or name in ("stg_lattice_create", "stg_gauge_create", "stg_field_pack",
                                                  "stg_field_unpack", "stg_dslash_eo", "stg_dslash_oe",
-                                                 "stg_dslash_multi", "stg_normal_op", "stg_normal_op_noalloc", "stg_mscg_solve",
+                                                 "stg_dslash_multi", "stg_dslash_host", "stg_normal_op", "stg_normal_op_noalloc", "stg_mscg_solve",
                                                  "stg_mscg_solve_batched", "stg_fermion_force",
                                                  "stg_stout_smear", "stg_stout_force", "stg_gauge_action",
                                                  "stg_gauge_force", "stg_gauge_create_u1", "stg_md_momenta", "stg_md_update_links",

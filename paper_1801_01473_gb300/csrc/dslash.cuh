@@ -174,6 +174,128 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
     }
 }
 
+// Shared-link variant for groups of several right-hand sides on FP32 / 16-bit links (R = float).
+// A block covers 64 output sites and every right-hand side of its group.  First all its threads
+// load the 8 links of the 64 sites (decoded, with the hop signs folded in: +u U forward, -u U
+// backward) into shared memory, together with the neighbours' half indices; after one barrier,
+// warps 2j and 2j+1 apply the operator to rhs j on the two 32-site halves from those links.  Every
+// link is read from memory once per block whatever the rhs count, and each thread holds the
+// registers of a one-rhs operator.  Sign folding is exact, so outputs and partial sums are bitwise
+// those of k_dslash.
+constexpr int kShSites = 64;
+constexpr size_t kShBytes = (size_t)8 * 18 * kShSites * sizeof(float) + (size_t)8 * kShSites * sizeof(int);
+
+template <typename LinkT, int MODE>
+__global__ void __launch_bounds__(512) k_dslash_sh(const __grid_constant__ DArgs a)
+{
+    using R = typename LinkT::R;
+    static_assert(sizeof(R) == sizeof(float), "shared-link operator is for FP32 arithmetic");
+    extern __shared__ float sh_links[];  // [8 hops][18 reals][64 sites], then int [8 hops][64 sites]
+    int *sh_nb = reinterpret_cast<int *>(sh_links + 8 * 18 * kShSites);
+    __shared__ double sh_part[16];
+    pdl_enter();
+    const DGroup &G = a.grp[blockIdx.y];
+    const int Vh = G.g.Vh;
+    const int h0 = blockIdx.x * kShSites;
+    if (h0 >= Vh) return;  // block-uniform
+    const int op = a.out_par;
+    // stage the links: hop k = 2 mu (forward) or 2 mu + 1 (backward) of site s
+    for (int t = threadIdx.x; t < 8 * kShSites; t += blockDim.x) {
+        const int k = t / kShSites, sl = t - k * kShSites, h = h0 + sl;
+        if (h >= Vh) continue;
+        const int mu = k >> 1;
+        const Hop hp = hop_of(G.g, site_of(G.g, op, h), mu);
+        cx<R> U[3][3];
+        R sign;
+        if ((k & 1) == 0) {
+            LinkT::load(link_block<LinkT>(G.links, Vh, mu, op), Vh, h, U);
+            sign = R(hp.sf);
+            sh_nb[k * kShSites + sl] = hp.hf;
+        } else {
+            LinkT::load(link_block<LinkT>(G.links, Vh, mu, 1 - op), Vh, hp.hb, U);
+            sign = R(-hp.sb);
+            sh_nb[k * kShSites + sl] = hp.hb;
+        }
+        float *dst = sh_links + (size_t)k * 18 * kShSites + sl;
+#pragma unroll
+        for (int e = 0; e < 9; ++e) {
+            dst[(2 * e) * kShSites] = sign * U[e / 3][e % 3].re;
+            dst[(2 * e + 1) * kShSites] = sign * U[e / 3][e % 3].im;
+        }
+    }
+    __syncthreads();
+    const int warp = threadIdx.x >> 5, j = warp >> 1;
+    const int sl = ((warp & 1) << 5) + (threadIdx.x & 31);
+    const int h = h0 + sl;
+    const bool act = j < G.nrhs && !(G.skip[j] != nullptr && *G.skip[j] != 0);  // warp-uniform
+    const bool live = act && h < Vh;
+    ProdSum<R> part;
+    if (live) {
+        cx<R> acc[3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) acc[c] = cx<R>{R(0), R(0)};
+#pragma unroll
+        for (int k = 0; k < 8; ++k) {
+            const float *src = sh_links + (size_t)k * 18 * kShSites + sl;
+            cx<R> U[3][3], v[3];
+#pragma unroll
+            for (int e = 0; e < 9; ++e) U[e / 3][e % 3] = cx<R>{src[(2 * e) * kShSites], src[(2 * e + 1) * kShSites]};
+            Field<R>::load(G.in[j], Vh, sh_nb[k * kShSites + sl], v);
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                cx<R> w = cx<R>{R(0), R(0)};
+                if ((k & 1) == 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) cmac(w, U[r][c], v[c]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) cmac_conj(w, U[c][r], v[c]);
+                }
+                acc[r].re = acc[r].re + w.re;
+                acc[r].im = acc[r].im + w.im;
+            }
+        }
+        cx<R> o[3];
+        if (MODE == 0) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) o[c] = cx<R>{R(0.5) * acc[c].re, R(0.5) * acc[c].im};
+        } else {
+            cx<R> pv[3];
+            Field<R>::load(G.epi_p[j], Vh, h, pv);
+            const R cj = (R)G.coef[j];
+#pragma unroll
+            for (int c = 0; c < 3; ++c)
+                o[c] = cx<R>{fma(cj, pv[c].re, R(-0.5) * acc[c].re), fma(cj, pv[c].im, R(-0.5) * acc[c].im)};
+            if (MODE == 1) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    part.add(pv[c].re, o[c].re);
+                    part.add(pv[c].im, o[c].im);
+                }
+            } else {
+                cx<R> b[3];
+                Field<R>::load(G.epi_b[j], Vh, h, b);
+#pragma unroll
+                for (int c = 0; c < 3; ++c) {
+                    o[c] = cx<R>{b[c].re - o[c].re, b[c].im - o[c].im};
+                    part.add(o[c].re, o[c].re);
+                    part.add(o[c].im, o[c].im);
+                }
+            }
+        }
+        Field<R>::store(G.out[j], Vh, h, o);
+    }
+    if (MODE != 0) {
+        const double pv = part.warp_total();
+        if ((threadIdx.x & 31) == 0) sh_part[warp] = pv;
+        __syncthreads();
+        const int jj = threadIdx.x;  // one thread per rhs writes its 64-site partial
+        if (jj < G.nrhs && 2 * jj + 1 < (int)(blockDim.x >> 5) && G.partial[jj] != nullptr &&
+            !(G.skip[jj] != nullptr && *G.skip[jj] != 0))
+            G.partial[jj][blockIdx.x] = sh_part[2 * jj] + sh_part[2 * jj + 1];
+    }
+}
+
 // Launches `kernel` with the programmatic-stream-serialization attribute (the kernel must start
 // with pdl_enter()); STG_PDL=0 in the environment launches without it.
 bool pdl_enabled();
@@ -185,6 +307,23 @@ cudaError_t launch_pdl(void (*kernel)(KArgs...), dim3 grid, dim3 block, cudaStre
     cfg.gridDim = grid;
     cfg.blockDim = block;
     cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+    attr[0].val.programmaticStreamSerializationAllowed = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = pdl_enabled() ? 1 : 0;
+    return cudaLaunchKernelEx(&cfg, kernel, static_cast<Args &&>(args)...);
+}
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl_smem(void (*kernel)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t st,
+                            Args &&...args)
+{
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = grid;
+    cfg.blockDim = block;
+    cfg.dynamicSmemBytes = smem;
     cfg.stream = st;
     cudaLaunchAttribute attr[1];
     attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
@@ -226,12 +365,27 @@ inline void dslash_extent(const DArgs &a, int &maxv, int &maxr)
 // NRHS template the launcher uses for a largest group of `maxr` right-hand sides.
 inline int dslash_nrhs_template(int maxr) { return maxr <= 1 ? 1 : maxr <= 2 ? 2 : maxr <= 4 ? 4 : 8; }
 
+// Launch shape code: a block size (64, 128, 256) for the rhs-in-registers kernel, or
+// kSharedLinks for k_dslash_sh (64 x nrhs threads per block; FP32 arithmetic only).
+constexpr int kSharedLinks = 1 << 16;
+
 template <typename LinkT>
 cudaError_t launch_dslash_t(const DArgs &a, int mode, int bs, cudaStream_t st)
 {
     int maxv, maxr;
     dslash_extent(a, maxv, maxr);
     if (a.ngroups <= 0 || maxv <= 0 || maxr <= 0) return cudaSuccess;
+    if (bs == kSharedLinks) {
+        if constexpr (sizeof(typename LinkT::R) == sizeof(float) && !LinkTraits<LinkT>::kU1) {
+            if (maxr > kMaxRhs) return cudaErrorInvalidValue;
+            const dim3 grid((maxv + kShSites - 1) / kShSites, a.ngroups), block(64 * maxr);
+            if (mode == 0) return launch_pdl_smem(k_dslash_sh<LinkT, 0>, grid, block, kShBytes, st, a);
+            if (mode == 1) return launch_pdl_smem(k_dslash_sh<LinkT, 1>, grid, block, kShBytes, st, a);
+            return launch_pdl_smem(k_dslash_sh<LinkT, 2>, grid, block, kShBytes, st, a);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
     switch (dslash_nrhs_template(maxr)) {
     case 1: return launch_dslash_n<LinkT, 1>(a, mode, maxv, bs, st);
     case 2: return launch_dslash_n<LinkT, 2>(a, mode, maxv, bs, st);

@@ -100,6 +100,47 @@ def test_multi_rhs_matches_single(variant, nrhs):
             assert torch.equal(one, out[j])
 
 
+@pytest.mark.parametrize("variant", [("f32", 12), ("f32", 18), ("f16", 12), ("bf16", 12)])
+@pytest.mark.parametrize("nrhs", [2, 3, 8])
+@pytest.mark.parametrize("shape", ["shared", "64", "256"])
+def test_multi_rhs_launch_shapes_bitwise(variant, nrhs, shape, monkeypatch):
+    """Every launch shape of the multi-rhs operator -- including the shared-link kernel, which
+    stages each block's links in shared memory once for all rhs -- gives bitwise the single-rhs
+    results, on a lattice whose last 64-site block is ragged (Vh = 1000)."""
+    p = stg()
+    prec, recon = variant
+    dims = (10, 10, 4, 10)
+    lat = p.Lattice(dims)
+    g = p.Gauge(lat, torch.from_numpy(links_for(dims)).cuda(), prec, recon)
+    inp = torch.stack([p.pack(lat, torch.from_numpy(S.gaussian_field(dims, 500 + j)).cuda(), g.vec_prec)
+                       for j in range(nrhs)])
+    monkeypatch.setenv("STG_DSLASH_SHAPE", "128")
+    ref = []
+    for out_par in (0, 1):
+        for j in range(nrhs):
+            one = torch.empty_like(inp[j])
+            (p.dslash_eo_ if out_par == 0 else p.dslash_oe_)(g, one, inp[j].contiguous())
+            ref.append(one)
+    monkeypatch.setenv("STG_DSLASH_SHAPE", shape)
+    k = 0
+    for out_par in (0, 1):
+        out = torch.empty_like(inp)
+        p.dslash_multi_(g, out_par, out, inp)
+        for j in range(nrhs):
+            assert torch.equal(ref[k], out[j]), (out_par, j)
+            k += 1
+    # the fused epilogue (normal operator, Re<p,q> partials) through the same shapes
+    for j in range(min(nrhs, 2)):
+        x = inp[j].contiguous()
+        monkeypatch.setenv("STG_DSLASH_SHAPE", "128")
+        a1, pq1 = torch.empty_like(x), torch.zeros(1, dtype=torch.float64, device="cuda")
+        p.normal_op_(g, 0.1, 0.01, a1, x, g.new_field(), pq1)
+        monkeypatch.setenv("STG_DSLASH_SHAPE", shape)
+        a2, pq2 = torch.empty_like(x), torch.zeros(1, dtype=torch.float64, device="cuda")
+        p.normal_op_(g, 0.1, 0.01, a2, x, g.new_field(), pq2)
+        assert torch.equal(a1, a2) and torch.equal(pq1, pq2)
+
+
 def test_pack_unpack_roundtrip():
     p = stg()
     dims = (6, 4, 2, 8)

@@ -138,15 +138,16 @@ stg_status stg_dslash_oe(const stg_gauge *g, void *out_odd_dev, const void *in_e
 stg_status stg_dslash_multi(const stg_gauge *g, int32_t out_parity, int32_t nrhs, void *out_dev, const void *in_dev,
                             size_t stride_bytes, void *stream);
 
-/* D_eo (out_parity 0) or D_oe (1) of nfield canonical complex128 [Vh][3] fields that live in HOST
- * memory: out_host[k] = D in_host[k].  A three-stage pipeline on internal streams overlaps the
+/* D_eo (out_parity 0) or D_oe (1) of nfield canonical [Vh][3] fields that live in HOST memory,
+ * complex128 (host_prec STG_F64) or complex64 (STG_F32: half the bytes over the host link, for
+ * gauges that compute in FP32 anyway): out_host[k] = D in_host[k].  A three-stage pipeline on internal streams overlaps the
  * host->device copy of field k+1, pack / D / unpack of field k (the gauge's precision) and the
  * device->host copy of field k-1, with two device staging slots per stage (4 canonical + 4 internal
  * fields of device memory, allocated and freed by the call).  Host buffers should be pinned for the
  * copies to overlap.  Ordered after the work queued on `stream`; returns when every output is in
  * host memory.  No in/out aliasing. */
-stg_status stg_dslash_host(const stg_gauge *g, int32_t out_parity, int32_t nfield, const void *const *in_host,
-                           void *const *out_host, void *stream);
+stg_status stg_dslash_host(const stg_gauge *g, int32_t out_parity, stg_prec host_prec, int32_t nfield,
+                           const void *const *in_host, void *const *out_host, void *stream);
 
 /* out_even = (m^2 + shift) in_even - D_eo D_oe in_even  (Eq. shift_eo), tmp_odd a caller buffer
  * of stg_field_bytes.  If pq_dev != NULL, *pq_dev (one device double) receives Re<in, out>,

@@ -201,17 +201,21 @@ def dslash_eo(gauge: Gauge, psi_odd: torch.Tensor) -> torch.Tensor:
 
 def dslash_host(gauge: Gauge, out_parity: int, fields: torch.Tensor, out: torch.Tensor | None = None,
                 stream=None) -> torch.Tensor:
-    """D_eo (out_parity 0) or D_oe (1) of a batch of canonical complex128 host fields [n, Vh, 3]
-    (pinned for overlap), streamed through the device by stg_dslash_host; returns host fields."""
-    if fields.is_cuda or fields.dtype != torch.complex128:
-        raise TypeError("dslash_host: fields must be complex128 host tensors")
+    """D_eo (out_parity 0) or D_oe (1) of a batch of canonical host fields [n, Vh, 3], complex128
+    or complex64 (pinned for overlap), streamed through the device by stg_dslash_host; returns
+    host fields of the same dtype."""
+    if fields.is_cuda or fields.dtype not in (torch.complex128, torch.complex64):
+        raise TypeError("dslash_host: fields must be complex128 or complex64 host tensors")
     src = fields.contiguous().reshape(-1, gauge.lattice.Vh, 3)
     n = src.shape[0]
     if out is None:
         out = torch.empty(src.shape, dtype=src.dtype, pin_memory=src.is_pinned())
+    if out.dtype != src.dtype:
+        raise TypeError("dslash_host: out must have the dtype of fields")
+    hp = PREC["f64"] if src.dtype == torch.complex128 else PREC["f32"]
     pi = (ctypes.c_void_p * n)(*[src[k].data_ptr() for k in range(n)])
     po = (ctypes.c_void_p * n)(*[out[k].data_ptr() for k in range(n)])
-    check(lib().stg_dslash_host(gauge.handle, int(out_parity), n, ctypes.cast(pi, ctypes.POINTER(ctypes.c_void_p)),
+    check(lib().stg_dslash_host(gauge.handle, int(out_parity), hp, n, ctypes.cast(pi, ctypes.POINTER(ctypes.c_void_p)),
                                 ctypes.cast(po, ctypes.POINTER(ctypes.c_void_p)), _stream(stream)), "stg_dslash_host")
     return out
 

@@ -65,9 +65,11 @@ struct Pipe {
 
 using namespace stg;
 
-extern "C" stg_status stg_dslash_host(const stg_gauge *g, int32_t out_parity, int32_t nfield,
+extern "C" stg_status stg_dslash_host(const stg_gauge *g, int32_t out_parity, stg_prec host_prec, int32_t nfield,
                                       const void *const *in_host, void *const *out_host, void *stream)
 {
+    if (host_prec != STG_F64 && host_prec != STG_F32)
+        return set_error(STG_ERR_ARG, "stg_dslash_host: host fields must be F64 (complex128) or F32 (complex64)");
     if (!g || (nfield > 0 && (!in_host || !out_host)))
         return set_error(STG_ERR_ARG, "stg_dslash_host: null pointer");
     if (out_parity != 0 && out_parity != 1) return set_error(STG_ERR_ARG, "stg_dslash_host: out_parity must be 0 or 1");
@@ -78,7 +80,8 @@ extern "C" stg_status stg_dslash_host(const stg_gauge *g, int32_t out_parity, in
     if (nfield == 0) return STG_OK;
 
     const int Vh = g->g.Vh;
-    const size_t canon = (size_t)Vh * 3 * sizeof(double2);                          // one canonical field
+    const bool c64 = host_prec == STG_F32;
+    const size_t canon = (size_t)Vh * 3 * (c64 ? sizeof(float2) : sizeof(double2));  // one canonical field
     const size_t inter = ((size_t)Vh * kind_vec_bytes(g->kind) + 255) & ~(size_t)255;  // one internal field
     const stg_prec vp = kind_is_f64(g->kind) ? STG_F64 : kind_is_ds(g->kind) ? STG_DS : STG_F32;
 
@@ -86,15 +89,17 @@ extern "C" stg_status stg_dslash_host(const stg_gauge *g, int32_t out_parity, in
     P.user = (cudaStream_t)stream;
     STG_CUDA_TRY(P.create());
     // staging: per slot a canonical input, an internal input, an internal output, a canonical output
-    STG_CUDA_TRY(cudaMalloc(&P.mem, kSlots * (2 * canon + 2 * inter)));
+    // (canonical slots rounded to 256 bytes so that every staging buffer stays aligned)
+    const size_t canon_al = (canon + 255) & ~(size_t)255;
+    STG_CUDA_TRY(cudaMalloc(&P.mem, kSlots * (2 * canon_al + 2 * inter)));
     char *base = static_cast<char *>(P.mem);
     char *c_in[kSlots], *i_in[kSlots], *i_out[kSlots], *c_out[kSlots];
     for (int k = 0; k < kSlots; ++k) {
-        char *b = base + (size_t)k * (2 * canon + 2 * inter);
+        char *b = base + (size_t)k * (2 * canon_al + 2 * inter);
         c_in[k] = b;
-        c_out[k] = b + canon;
-        i_in[k] = b + 2 * canon;
-        i_out[k] = b + 2 * canon + inter;
+        c_out[k] = b + canon_al;
+        i_in[k] = b + 2 * canon_al;
+        i_out[k] = b + 2 * canon_al + inter;
     }
     // order after the work already queued on the caller's stream
     STG_CUDA_TRY(cudaEventRecord(P.start, P.user));
@@ -116,15 +121,23 @@ extern "C" stg_status stg_dslash_host(const stg_gauge *g, int32_t out_parity, in
         STG_CUDA_TRY(cudaEventRecord(P.in_ready[s], P.s_in));
         // stage 2: pack, D, unpack, once the slot's previous output has left the device
         STG_CUDA_TRY(cudaStreamWaitEvent(P.s_cmp, P.in_ready[s], 0));
-        stg_status st = stg_field_pack(g->lat, vp, c_in[s], i_in[s], P.s_cmp);
-        if (st != STG_OK) return st;
+        if (c64) {
+            STG_CUDA_TRY(launch_field_pack_c64(vp, Vh, c_in[s], i_in[s], P.s_cmp));
+        } else {
+            const stg_status st = stg_field_pack(g->lat, vp, c_in[s], i_in[s], P.s_cmp);
+            if (st != STG_OK) return st;
+        }
         STG_CUDA_TRY(cudaEventRecord(P.in_free[s], P.s_cmp));
         if (k >= kSlots) STG_CUDA_TRY(cudaStreamWaitEvent(P.s_cmp, P.out_free[s], 0));
         a.grp[0].in[0] = i_in[s];
         a.grp[0].out[0] = i_out[s];
         STG_CUDA_TRY(launch_dslash(g->kind, a, 0, P.s_cmp));
-        st = stg_field_unpack(g->lat, vp, i_out[s], c_out[s], P.s_cmp);
-        if (st != STG_OK) return st;
+        if (c64) {
+            STG_CUDA_TRY(launch_field_unpack_c64(vp, Vh, i_out[s], c_out[s], P.s_cmp));
+        } else {
+            const stg_status st = stg_field_unpack(g->lat, vp, i_out[s], c_out[s], P.s_cmp);
+            if (st != STG_OK) return st;
+        }
         STG_CUDA_TRY(cudaEventRecord(P.out_ready[s], P.s_cmp));
         // stage 3: device -> host
         STG_CUDA_TRY(cudaStreamWaitEvent(P.s_out, P.out_ready[s], 0));

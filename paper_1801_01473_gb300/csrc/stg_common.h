@@ -46,6 +46,9 @@ cudaError_t launch_dslash_bs(int kind, const DArgs &a, int mode, int bs, cudaStr
 
 // Pack canonical complex128 links [4][V][3][3] into the internal layout of `kind`.
 cudaError_t launch_pack_links(int kind, const Geom &g, const void *canon, void *links, cudaStream_t st);
+// canonical complex64 field <-> internal layout of vec_prec (stg_core.cu)
+cudaError_t launch_field_pack_c64(stg_prec vec_prec, int Vh, const void *canon, void *internal, cudaStream_t st);
+cudaError_t launch_field_unpack_c64(stg_prec vec_prec, int Vh, const void *internal, void *canon, cudaStream_t st);
 
 // F32 12-real copy of an F64 gauge (created on first use, owned by the F64 gauge): the operator
 // of the refinement iterations when the multi-shift phase runs on 16-bit links.

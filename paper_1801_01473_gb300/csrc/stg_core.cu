@@ -433,27 +433,54 @@ stg_status f32_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge 
 }
 
 // canonical [Vh][3] complex128 <-> internal field
-template <typename R>
-__global__ void k_pack_field(int Vh, const double2 *__restrict__ canon, void *__restrict__ out)
+template <typename R, typename C = double2>
+__global__ void k_pack_field(int Vh, const C *__restrict__ canon, void *__restrict__ out)
 {
     int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= Vh) return;
     cx<R> v[3];
     for (int c = 0; c < 3; ++c) {
-        double2 d = canon[(size_t)h * 3 + c];
+        const C d = canon[(size_t)h * 3 + c];
         v[c] = cx<R>{(R)d.x, (R)d.y};
     }
     Field<R>::store(out, Vh, h, v);
 }
 
-template <typename R>
-__global__ void k_unpack_field(int Vh, const void *__restrict__ in, double2 *__restrict__ canon)
+template <typename R, typename C = double2>
+__global__ void k_unpack_field(int Vh, const void *__restrict__ in, C *__restrict__ canon)
 {
     int h = blockIdx.x * blockDim.x + threadIdx.x;
     if (h >= Vh) return;
     cx<R> v[3];
     Field<R>::load_rw(in, Vh, h, v);
-    for (int c = 0; c < 3; ++c) canon[(size_t)h * 3 + c] = make_double2((double)v[c].re, (double)v[c].im);
+    for (int c = 0; c < 3; ++c) {
+        C d;
+        d.x = (decltype(d.x))(double)v[c].re;
+        d.y = (decltype(d.y))(double)v[c].im;
+        canon[(size_t)h * 3 + c] = d;
+    }
+}
+
+// Pack / unpack between a canonical complex64 field and the internal layout of vec_prec (the
+// single-precision host fields of stg_dslash_host).
+cudaError_t launch_field_pack_c64(stg_prec vec_prec, int Vh, const void *canon, void *internal, cudaStream_t st)
+{
+    const int bs = 256;
+    const float2 *c = static_cast<const float2 *>(canon);
+    if (vec_prec == STG_F64) k_pack_field<double, float2><<<(Vh + bs - 1) / bs, bs, 0, st>>>(Vh, c, internal);
+    else if (vec_prec == STG_F32) k_pack_field<float, float2><<<(Vh + bs - 1) / bs, bs, 0, st>>>(Vh, c, internal);
+    else k_pack_field<dsf, float2><<<(Vh + bs - 1) / bs, bs, 0, st>>>(Vh, c, internal);
+    return cudaGetLastError();
+}
+
+cudaError_t launch_field_unpack_c64(stg_prec vec_prec, int Vh, const void *internal, void *canon, cudaStream_t st)
+{
+    const int bs = 256;
+    float2 *c = static_cast<float2 *>(canon);
+    if (vec_prec == STG_F64) k_unpack_field<double, float2><<<(Vh + bs - 1) / bs, bs, 0, st>>>(Vh, internal, c);
+    else if (vec_prec == STG_F32) k_unpack_field<float, float2><<<(Vh + bs - 1) / bs, bs, 0, st>>>(Vh, internal, c);
+    else k_unpack_field<dsf, float2><<<(Vh + bs - 1) / bs, bs, 0, st>>>(Vh, internal, c);
+    return cudaGetLastError();
 }
 
 // fixed-order sum of n partials into *out (one block)

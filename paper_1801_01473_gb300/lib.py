@@ -88,7 +88,7 @@ def lib() -> ctypes.CDLL:
     L.stg_dslash_eo.argtypes = [P, P, P, P]
     L.stg_dslash_oe.argtypes = [P, P, P, P]
     L.stg_dslash_multi.argtypes = [P, I32, I32, P, P, SZ, P]
-    L.stg_dslash_host.argtypes = [P, I32, I32, PP, PP, P]
+    L.stg_dslash_host.argtypes = [P, I32, ctypes.c_int, I32, PP, PP, P]
     L.stg_normal_op.argtypes = [P, D, D, P, P, P, P, P]
     L.stg_normal_op_noalloc.argtypes = [P, D, D, P, P, P, P]
     L.stg_mscg_solve.argtypes = [P, P, ctypes.POINTER(MscgParams), P, PP, ctypes.POINTER(MscgStats), P]

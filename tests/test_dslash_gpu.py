@@ -194,3 +194,11 @@ def test_dslash_host_pipeline(variant, out_par):
         assert rel(got[k].numpy(), oracle.dslash(dims, u, out_par, fields[k])) <= TOL[variant]
     empty = torch.empty((0, lat.Vh, 3), dtype=torch.complex128)
     assert p.dslash_host(g, out_par, empty).shape[0] == 0
+    if prec in ("f32", "bf16"):
+        # complex64 host fields: half the bytes over the host link, same FP32 arithmetic
+        h32 = host.to(torch.complex64).pin_memory()
+        got32 = p.dslash_host(g, out_par, h32)
+        assert got32.dtype == torch.complex64
+        for k in range(5):
+            dev = fn(g, h32[k].to(torch.complex128).cuda()).cpu().to(torch.complex64)
+            assert torch.equal(got32[k], dev), k

@@ -218,6 +218,18 @@ typedef struct {
 stg_status stg_mscg_solve(const stg_gauge *g_f64, const stg_gauge *g_inner, const stg_mscg_params *params,
                           const void *b_c128_dev, void *const *x_c128_dev, stg_mscg_stats *stats, void *stream);
 
+/* A rational function of the shifted normal operator applied to a field (Sec. 2: the RHMC's
+ * rational approximation of a fractional power, one pole per system of Eq. shift_eo):
+ *   out = alpha0 b + sum_i residues[i] (m^2 + sigma_i - D_eo D_oe)^-1 b,   sigma_i = params->shifts[i]
+ * the systems solved by stg_mscg_solve with params (and g_inner as there), the terms added in pole
+ * order in FP64.  The pseudofermion heatbath (power +1/8 per rooted staggered flavour) and the
+ * fermion action (power -1/4) are both of this form.  b, out: canonical complex128 even fields
+ * (device, may alias); stats as for stg_mscg_solve (may be NULL).  Allocates nshift FP64 fields
+ * from the stream-ordered allocator; synchronises like stg_mscg_solve. */
+stg_status stg_rational_apply(const stg_gauge *g_f64, const stg_gauge *g_inner, const stg_mscg_params *params,
+                              double alpha0, const double *residues, const void *b_c128_dev, void *out_c128_dev,
+                              stg_mscg_stats *stats, void *stream);
+
 /* One lattice of a batched solve: nrhs sources (pseudofermions) on the same gauge. */
 typedef struct {
     const stg_gauge *g_f64;

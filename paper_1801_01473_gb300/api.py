@@ -280,6 +280,22 @@ def mscg(g_f64: Gauge, b: torch.Tensor, shifts, mass: float, tol: float = 1e-10,
     return (_to_host(x) if host else x), stats
 
 
+def rational_apply(g_f64: Gauge, b: torch.Tensor, alpha0: float, residues, poles, mass: float, tol: float = 1e-10,
+                   g_inner: Gauge | None = None, max_iter: int = 20000, stream=None):
+    """alpha0 b + sum_i residues[i] (m^2 + poles[i] - D_eo D_oe)^-1 b on a canonical complex128 even
+    field (stg_rational_apply).  Returns (out [Vh, 3] complex128 on cuda, stats dict)."""
+    bd = _dev(b).reshape(g_f64.lattice.Vh, 3)
+    ns = len(poles)
+    out = torch.empty_like(bd)
+    p, _sh, _log = _params(poles, mass, tol, max_iter, 0.0, 0.0, 0)
+    res = (ctypes.c_double * ns)(*[float(r) for r in residues])
+    st, tr, si = _stats(ns)
+    check(lib().stg_rational_apply(g_f64.handle, g_inner.handle if g_inner is not None else None, ctypes.byref(p),
+                                   float(alpha0), ctypes.cast(res, ctypes.POINTER(ctypes.c_double)), _ptr(bd), _ptr(out),
+                                   ctypes.byref(st), _stream(stream)), "stg_rational_apply")
+    return out, _stats_dict(st, tr, si)
+
+
 def mscg_batched(instances, shifts, mass: float, tol: float = 1e-10, max_iter: int = 20000, inner_tol: float = 0.0,
                  reliable_delta: float = 0.0, stream=None):
     """instances: list of (g_f64, g_inner or None, [b_r canonical [Vh,3] cuda tensors]).

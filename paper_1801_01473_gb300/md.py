@@ -22,7 +22,7 @@ from typing import Sequence
 import torch
 
 from .api import (Gauge, Lattice, complex_convert, fermion_force, gauge_action, gauge_force, md_kinetic, md_momenta,
-                  md_update_links_, md_update_momenta_, mscg, stout_force, stout_smear)
+                  md_update_links_, md_update_momenta_, mscg, rational_apply, stout_force, stout_smear)
 
 # Omelyan's second-order minimum-norm parameter
 OMELYAN_LAMBDA = 0.1931833275037836
@@ -33,6 +33,7 @@ class Pseudofermion:
     b: torch.Tensor                 # even-site source [Vh, 3] complex128 (cuda)
     shifts: Sequence[float]
     residues: Sequence[float]
+    alpha0: float = 0.0             # constant term of the rational approximation (no force)
 
 
 @dataclass
@@ -67,6 +68,7 @@ class Action:
             for pf in self.pseudofermions:
                 x, _ = mscg(g64, pf.b, list(pf.shifts), self.mass, tol=self.tol, g_inner=gi)
                 bb = pf.b.reshape(-1)
+                s += float(pf.alpha0) * float(torch.vdot(bb, bb).real)
                 s += sum(float(r) * float(torch.vdot(bb, x[i].reshape(-1)).real) for i, r in enumerate(pf.residues))
         return s
 
@@ -94,6 +96,19 @@ class Action:
                     gk = complex_convert(gk, torch.complex64)
                 f = stout_force(self.lattice, u, levels, self.stout_rho, gk, kind=0)
             md_update_momenta_(self.lattice, eps, f, mom)
+
+
+def pseudofermion_heatbath(action: Action, links: torch.Tensor, eta: torch.Tensor, heat, act) -> Pseudofermion:
+    """Pseudofermion heatbath (Sec. 2: pseudofermions are drawn at the start of the trajectory):
+    phi = R_heat(A) eta on the (smeared) links, with eta complex Gaussian (density exp(-eta^dag eta),
+    drawn by the caller) and R_heat ~ A^(+1/8) per rooted staggered flavour, so that phi^dag R_act(A) phi
+    with R_act ~ A^(-1/4) has the distribution exp(-S_f).  heat, act: rational.RationalApprox (or any
+    object with alpha0, residues, poles).  Returns the pseudofermion carrying act's poles and residues."""
+    _, uk = action._smeared(links)
+    g64, gi = action._gauges(uk)
+    phi, _ = rational_apply(g64, eta, heat.alpha0, list(heat.residues), list(heat.poles), action.mass,
+                            tol=action.tol, g_inner=gi)
+    return Pseudofermion(phi, list(act.poles), list(act.residues), float(act.alpha0))
 
 
 def hamiltonian(action: Action, links: torch.Tensor, mom: torch.Tensor) -> float:

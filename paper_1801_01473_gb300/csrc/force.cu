@@ -10,10 +10,13 @@
 // kind 1: W^dag (dS/dRe U + i dS/dIm U).  With a U(1) phase field u carries exp(i theta) as well
 // (D uses u U and its adjoint), and U is the SU(3) link without the phase.
 //
-// Work split: y_i = D_oe x_i for all shifts by the multi-rhs D kernel on the double-single copy of
-// the links (link loads shared; 48-bit significand, ~3x the FP64 operator's speed on GB300); then
-// one thread per site z and direction mu gathers its rank-nshift sum of outer products in FP64
-// registers (no atomics: every link is owned by exactly one thread).
+// Work split: y_i = D_oe x_i for all shifts by the D kernel on the double-single copy of the links
+// (48-bit significand, ~3x the FP64 operator's speed on GB300); then one thread per site z and
+// direction mu gathers its rank-nshift sum of outer products (no atomics: every link is owned by
+// exactly one thread) -- in double-single on the FP32 pipes (k_force_ds, the default: GB300 issues
+// FP64 at 1/64 of FP32, and the FP64 gather was FP64-pipe bound at ~94 %), or in FP64 (k_force,
+// with STG_FORCE_FP64=1).  F = TA(U W) and W^dag are formed in FP64 from the double-single W.
+#include <cstdlib>
 #include <cstring>
 #include <vector>
 
@@ -95,6 +98,93 @@ __global__ void __launch_bounds__(kForceBlock) k_force(const __grid_constant__ F
                 Z[r][c] = z;
             }
         // TA(Z) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6: the trace of Z - Z^dag is 2i Im tr Z
+        const double im_tr = (Z[0][0].im + Z[1][1].im + Z[2][2].im) / 3.0;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                double re = 0.5 * (Z[r][c].re - Z[c][r].re);
+                double im = 0.5 * (Z[r][c].im + Z[c][r].im);
+                if (r == c) im -= im_tr;
+                o[r * 3 + c] = make_double2(re, im);
+            }
+    }
+}
+
+struct ForceArgsDS {
+    Geom g;
+    const void *links;          // double-single companion links (possibly with U(1) phases)
+    const void *x[kMaxShifts];  // even double-single fields
+    const void *y[kMaxShifts];  // odd double-single fields D_oe x_i
+    float2 res[kMaxShifts];     // residues as double-single (hi, lo), split on the host
+    int nshift;
+    int kind;
+    double2 *out;  // canonical [4][V][3][3]
+};
+
+template <typename LinkT>
+__global__ void __launch_bounds__(kForceBlock) k_force_ds(const __grid_constant__ ForceArgsDS a)
+{
+    const int par = blockIdx.y;
+    const int h = blockIdx.x * kForceBlock + threadIdx.x;
+    const int Vh = a.g.Vh;
+    if (h >= Vh) return;
+    const Site s = site_of(a.g, par, h);
+    const long long V = 2LL * Vh;
+    for (int mu = 0; mu < 4; ++mu) {
+        const Hop hp = hop_of(a.g, s, mu);
+        cx<dsf> W[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) W[r][c] = cx<dsf>{dsf(0.f, 0.f), dsf(0.f, 0.f)};
+        // W = sum_i r_i f_i g_i^dag  (f = y(z+mu), g = x(z) for even z; f = x(z+mu), g = y(z) for odd z)
+        for (int i = 0; i < a.nshift; ++i) {
+            cx<dsf> f[3], g[3];
+            if (par == 0) {
+                Field<dsf>::load(a.y[i], Vh, hp.hf, f);
+                Field<dsf>::load(a.x[i], Vh, h, g);
+            } else {
+                Field<dsf>::load(a.x[i], Vh, hp.hf, f);
+                Field<dsf>::load(a.y[i], Vh, h, g);
+            }
+            const dsf ri = dsf(a.res[i].x, a.res[i].y);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) f[c] = cx<dsf>{ri * f[c].re, ri * f[c].im};
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) cmac_conj(W[r][c], g[c], f[r]);  // W_rc += f_r conj(g_c)
+        }
+        // u = sign * exp(i theta) (theta = 0 without a phase field); sign = +u_mu(z) even, -u_mu(z) odd
+        const void *blk = link_block<LinkT>(a.links, Vh, mu, par);
+        cx<dsf> ph = LinkTraits<LinkT>::phase(blk, Vh, h);
+        if ((par == 0 ? hp.sf : -hp.sf) < 0.f) ph = cx<dsf>{-ph.re, -ph.im};
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) W[r][c] = cmul(ph, W[r][c]);
+        double2 *o = a.out + ((long long)mu * V + s.i) * 9;
+        if (a.kind == 1) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) o[r * 3 + c] = make_double2((double)W[c][r].re, -(double)W[c][r].im);
+            continue;
+        }
+        // Z = U W with the SU(3) link in double-single, then TA(Z) in FP64
+        cx<dsf> U[3][3];
+        LinkTraits<LinkT>::Base::load(blk, Vh, h, U);
+        cx<double> Z[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cx<dsf> z = cx<dsf>{dsf(0.f, 0.f), dsf(0.f, 0.f)};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) cmac(z, U[r][k], W[k][c]);
+                Z[r][c] = cx<double>{(double)z.re, (double)z.im};
+            }
         const double im_tr = (Z[0][0].im + Z[1][1].im + Z[2][2].im) / 3.0;
 #pragma unroll
         for (int r = 0; r < 3; ++r)
@@ -191,10 +281,13 @@ extern "C" stg_status stg_fermion_force(const stg_gauge *g, int32_t nshift, cons
         ptrs[kMaxShifts + i] = a.x[i];
         ptrs[2 * kMaxShifts + i] = ws + (size_t)(2 * nshift + i) * fb;  // x_i in double-single
     }
+    const char *fp64_env = getenv("STG_FORCE_FP64");
+    const bool fp64_gather = fp64_env && fp64_env[0] == '1';
     void **d_ptrs = reinterpret_cast<void **>(ws + 3 * nshift * fb);
     STG_CUDA_TRY(cudaMemcpyAsync(d_ptrs, ptrs.data(), ptr_bytes, cudaMemcpyHostToDevice, st));
-    k_pack_many<double><<<dim3((Vh + 255) / 256, nshift), 256, 0, st>>>(
-        Vh, reinterpret_cast<const double2 *const *>(d_ptrs), d_ptrs + kMaxShifts);
+    if (fp64_gather)  // FP64 copies of x_i only for the FP64 gather
+        k_pack_many<double><<<dim3((Vh + 255) / 256, nshift), 256, 0, st>>>(
+            Vh, reinterpret_cast<const double2 *const *>(d_ptrs), d_ptrs + kMaxShifts);
     k_pack_many<dsf><<<dim3((Vh + 255) / 256, nshift), 256, 0, st>>>(
         Vh, reinterpret_cast<const double2 *const *>(d_ptrs), d_ptrs + 2 * kMaxShifts);
     STG_CUDA_TRY(cudaGetLastError());
@@ -219,7 +312,31 @@ extern "C" stg_status stg_fermion_force(const stg_gauge *g, int32_t nshift, cons
         d.ngroups = ng;
         STG_CUDA_TRY(launch_dslash(gds->kind, d, 0, st));
     }
-    // r_i y_i: double-single -> FP64 in place (same 48-byte site layout)
+    if (!fp64_gather) {
+        ForceArgsDS b;
+        memset(&b, 0, sizeof(b));
+        b.g = g->g;
+        b.links = gds->links;
+        b.nshift = nshift;
+        b.kind = kind;
+        b.out = static_cast<double2 *>(out_c128_dev);
+        for (int i = 0; i < nshift; ++i) {
+            b.x[i] = ptrs[2 * kMaxShifts + i];
+            b.y[i] = a.y[i];
+            const float hi = (float)residues[i];
+            b.res[i] = make_float2(hi, (float)(residues[i] - (double)hi));
+        }
+        const dim3 grid_ds((Vh + kForceBlock - 1) / kForceBlock, 2);
+        switch (gds->kind) {
+        case kDSR18: k_force_ds<LinkDSR18><<<grid_ds, kForceBlock, 0, st>>>(b); break;
+        case kDSR12: k_force_ds<LinkDSR12><<<grid_ds, kForceBlock, 0, st>>>(b); break;
+        case kDSR18 | kU1: k_force_ds<LinkU1<LinkDSR18, double2>><<<grid_ds, kForceBlock, 0, st>>>(b); break;
+        default: k_force_ds<LinkU1<LinkDSR12, double2>><<<grid_ds, kForceBlock, 0, st>>>(b); break;
+        }
+        STG_CUDA_TRY(cudaGetLastError());
+        return STG_OK;
+    }
+    // FP64 gather: r_i y_i, double-single -> FP64 in place (same 48-byte site layout)
     Residues rs;
     for (int i = 0; i < kMaxShifts; ++i) rs.r[i] = i < nshift ? residues[i] : 0.0;
     k_ds_to_f64_scaled<<<dim3((Vh + 255) / 256, nshift), 256, 0, st>>>(Vh, a.y[0], fb, rs);

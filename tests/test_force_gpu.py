@@ -125,3 +125,22 @@ def test_force_48x48x48x48_finite_differences():
         assert err <= 1e-6, (trial, mu, z, fd, an)
         del gs
     print("48^4 force vs FD: worst relative error %.2e over 32 links" % worst)
+
+
+@pytest.mark.parametrize("recon", [18, 12])
+@pytest.mark.parametrize("kind", [0, 1])
+def test_double_single_gather_matches_fp64_gather(recon, kind, monkeypatch):
+    """The default double-single accumulation of W (FP32 pipes) against the FP64 accumulation
+    (STG_FORCE_FP64=1) on the same solutions: 1e-13 relative."""
+    import paper_1801_01473_gb300 as p
+    dims = (6, 4, 4, 8)
+    u = S.gauge_links(dims, "expih", 221)
+    lat = p.Lattice(dims)
+    g = p.Gauge(lat, torch.from_numpy(u).cuda(), "f64", recon)
+    gen = torch.Generator(device="cuda").manual_seed(222)
+    x = torch.randn((5, lat.Vh, 3), dtype=torch.complex128, device="cuda", generator=gen)
+    res = [0.9, 0.5, 0.3, 0.2, 0.1]
+    ds = p.fermion_force(g, res, x, kind=kind)
+    monkeypatch.setenv("STG_FORCE_FP64", "1")
+    f64 = p.fermion_force(g, res, x, kind=kind)
+    assert float((ds - f64).abs().max()) <= 1e-13 * float(f64.abs().max())

@@ -331,7 +331,7 @@ def time_force(torch, p):
     torch.cuda.synchronize()
     del f
     return {"lattice": "48^4", "shifts": 12, "ms": round(e0.elapsed_time(e1) / 3, 3),
-            "note": "D_oe on the 12 solutions + per-link gather, FP64"}
+            "note": "double-single D_oe on the 12 solutions + per-link gather of W in double-single, F in FP64"}
 
 
 # Algorithmic FP64 flops per link of one stout step (complex 3x3 product = 27 complex

@@ -51,10 +51,14 @@ def update_links(u, h, eps):
 
 
 class Action:
-    def __init__(self, dims, beta, mass=0.0, pseudofermions=(), stout_rho=0.0, stout_steps=0, tol=1e-13):
+    def __init__(self, dims, beta, mass=0.0, pseudofermions=(), stout_rho=0.0, stout_steps=0, tol=1e-13, theta=None):
         self.dims, self.beta, self.mass = dims, beta, mass
         self.pf = list(pseudofermions)  # (b, shifts, residues)
         self.rho, self.nstout, self.tol = stout_rho, stout_steps, tol
+        self.theta = theta  # U(1) phases of the fermion links [4][V] (None: none)
+
+    def _dirac_links(self, uk):
+        return uk if self.theta is None else oracle.u1_links(uk, self.theta)
 
     def _levels(self, u):
         return ost.stout(self.dims, u, self.rho, self.nstout)
@@ -62,7 +66,7 @@ class Action:
     def value(self, u) -> float:
         s = og.action(self.dims, u, self.beta) if self.beta != 0.0 else 0.0
         if self.pf:
-            uk = self._levels(u)[-1]
+            uk = self._dirac_links(self._levels(u)[-1])
             for b, shifts, res in self.pf:
                 x = oracle.mscg(self.dims, uk, self.mass, np.asarray(shifts), b, tol=self.tol)["x"]
                 s += oracle.action(np.asarray(res), b, x)
@@ -73,8 +77,12 @@ class Action:
         if self.pf:
             levels = self._levels(u)
             for b, shifts, res in self.pf:
-                x = oracle.mscg(self.dims, levels[-1], self.mass, np.asarray(shifts), b, tol=self.tol)["x"]
-                gk = oracle.force(self.dims, levels[-1], np.asarray(res), x, kind=1)
+                x = oracle.mscg(self.dims, self._dirac_links(levels[-1]), self.mass, np.asarray(shifts), b,
+                                tol=self.tol)["x"]
+                if self.theta is None:
+                    gk = oracle.force(self.dims, levels[-1], np.asarray(res), x, kind=1)
+                else:
+                    gk = oracle.force_u1(self.dims, levels[-1], self.theta, np.asarray(res), x, kind=1)
                 f = f + ost.lie_force(u, ost.stout_backward(self.dims, levels, self.rho, gk))
         return f
 

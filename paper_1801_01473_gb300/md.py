@@ -47,6 +47,7 @@ class Action:
     tol: float = 1e-12
     inner: str | None = None        # None: FP64 solve; "f32": mixed FP32-inner solve
     precision: str = "f64"          # forces in "f64" or "f32" (the Hamiltonian is always FP64)
+    theta: torch.Tensor | None = None  # U(1) phase field [4, V] on the fermion links (chemical potential, ...)
 
     def _smeared(self, links):
         if self.stout_steps > 0:
@@ -55,8 +56,8 @@ class Action:
         return None, links
 
     def _gauges(self, uk):
-        g64 = Gauge(self.lattice, uk, "f64", 18)
-        gi = Gauge(self.lattice, uk, "f32", 12) if self.inner == "f32" else None
+        g64 = Gauge(self.lattice, uk, "f64", 18, theta=self.theta)
+        gi = Gauge(self.lattice, uk, "f32", 12, theta=self.theta) if self.inner == "f32" else None
         return g64, gi
 
     def value(self, links: torch.Tensor) -> float:

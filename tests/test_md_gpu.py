@@ -158,3 +158,33 @@ def test_single_precision_forces(p):
     d64, u64 = run(a64, 3)
     assert float((u1 - u64).abs().max()) < 1e-5
     assert d1 == pytest.approx(d64, rel=1e-4, abs=1e-5)
+
+
+def test_trajectory_with_u1_phases_matches_oracle(p):
+    """Rows f1-f3 together: an Omelyan trajectory of gauge + stout-smeared pseudofermion with an
+    imaginary chemical potential (constant U(1) phase 0.2 on the time links) against the oracle's
+    trajectory (1e-9), and energy conservation at O(eps^2)."""
+    dims = (4, 4, 4, 4)
+    lat = p.Lattice(dims)
+    u = S.gauge_links(dims, "expih", 164)
+    b = S.gaussian_field(dims, 165)
+    theta = np.zeros((4, u.shape[1]))
+    theta[3] = 0.2
+    pf = ([0.05, 0.5], [0.4, 0.3])
+    a_gpu = p.md.Action(lat, beta=5.6, mass=0.2, pseudofermions=[p.md.Pseudofermion(_gpu(b), *pf)], tol=1e-13,
+                        stout_rho=0.15, stout_steps=1, theta=_gpu(theta))
+    a_ora = omd.Action(dims, beta=5.6, mass=0.2, pseudofermions=[(b, *pf)], tol=1e-13, stout_rho=0.15,
+                       stout_steps=1, theta=theta)
+    xi = _xi(166, u.shape[1])
+    ud, h = _gpu(u), p.md_momenta(lat, _gpu(xi))
+    h0 = p.md.hamiltonian(a_gpu, ud, h)
+    p.md.omelyan(a_gpu, ud, h, 0.4, 3)
+    dh3 = p.md.hamiltonian(a_gpu, ud, h) - h0
+    hw = omd.momenta(xi)
+    uw, hw = omd.omelyan(a_ora, u, hw, 0.4, 3)
+    assert np.abs(ud.cpu().numpy() - uw).max() < 1e-9
+    assert np.abs(h.cpu().numpy() - hw).max() < 1e-9
+    ud, h = _gpu(u), p.md_momenta(lat, _gpu(xi))
+    p.md.omelyan(a_gpu, ud, h, 0.4, 6)
+    dh6 = p.md.hamiltonian(a_gpu, ud, h) - h0
+    assert 3.2 < dh3 / dh6 < 4.8

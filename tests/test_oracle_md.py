@@ -59,3 +59,18 @@ def test_full_action_omelyan_energy_scaling():
     d2 = _dh(act, u, h, 0.4, 6, omd.omelyan)
     assert abs(d1) > 1e-7
     assert 3.2 < d1 / d2 < 4.8
+
+
+def test_full_action_with_u1_phases_energy_scaling():
+    """With an imaginary chemical potential on the time links the MD force must still be the
+    exact gradient of the action (phases enter D and the force, not the gauge part)."""
+    u = S.gauge_links(DIMS, "expih", 147)
+    b = S.gaussian_field(DIMS, 148)
+    h = omd.momenta(_xi(149, u.shape[1]))
+    theta = np.zeros((4, u.shape[1]))
+    theta[3] = 0.2
+    act = omd.Action(DIMS, beta=5.6, mass=0.2, pseudofermions=[(b, [0.05, 0.5], [0.4, 0.3])],
+                     stout_rho=0.15, stout_steps=1, theta=theta)
+    d1 = _dh(act, u, h, 0.4, 3, omd.omelyan)
+    d2 = _dh(act, u, h, 0.4, 6, omd.omelyan)
+    assert 3.2 < d1 / d2 < 4.8

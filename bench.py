@@ -415,6 +415,46 @@ def time_gauge(torch, p):
     return out
 
 
+def time_rhmc(torch, p):
+    """One RHMC trajectory on 32^4 (Sec. 2-3): pseudofermion heatbath, Omelyan MD (tau = 0.5, 8 steps,
+    17 force evaluations) with the gauge force, 2-step stout smearing and its chain rule and the
+    fermion force in single precision (mixed solves), then the FP64 Hamiltonian and the Metropolis
+    test; stored 10-pole Remez approximations of x^(1/8), x^(-1/4) for m = 0.3."""
+    from paper_1801_01473_gb300.rational import load_table
+    dims = (32, 32, 32, 32)
+    lat = p.Lattice(dims)
+    # smoothed synthetic start (10 stout steps of the random links), closer to an equilibrium
+    # configuration than the raw random links, whose large forces break the integrator
+    u = p.stout_smear(lat, torch.from_numpy(S.gauge_links(dims, "expih", 1002)).cuda(), 0.1, 10)[-1].contiguous()
+    tab = load_table()
+    act = p.md.Action(lat, beta=5.6, mass=0.3, tol=1e-10, inner="f32", precision="f32", stout_rho=0.15,
+                      stout_steps=2)
+    eta = torch.from_numpy(S.gaussian_field(dims, 2002)).cuda()
+    g = torch.Generator(device="cuda").manual_seed(4002)
+    xi = torch.randn((4, lat.V, 8), dtype=torch.float64, device="cuda", generator=g)
+
+    def timed(fn):
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        r = fn()
+        torch.cuda.synchronize()
+        return r, time.perf_counter() - t0
+
+    p.md.pseudofermion_heatbath(act, u, eta, tab["heatbath"], tab["action"])  # warm-up: tuned launch shapes
+    pf, t_hb = timed(lambda: p.md.pseudofermion_heatbath(act, u, eta, tab["heatbath"], tab["action"]))
+    act.pseudofermions = [pf]
+    mom = p.md_momenta(lat, xi)
+    _, t_h = timed(lambda: p.md.hamiltonian(act, u, mom))
+    _, t_f = timed(lambda: act.apply_force(u.clone(), mom.clone(), 0.01))
+    res, t_traj = timed(lambda: p.md.trajectory(act, u, xi, 0.5, 8, uniform=0.5))
+    return {"lattice": "32^4", "mass": 0.3, "stout": "2 x 0.15", "integrator": "omelyan, tau 0.5, 8 steps",
+            "start": "random exp(i 0.3 H) links after 10 stout steps of 0.1",
+            "forces": "fp32 (gauge, stout chain), mixed solves; FP64 Hamiltonian", "poles": len(pf.shifts),
+            "trajectory_s": round(t_traj, 3), "heatbath_ms": round(1e3 * t_hb, 1),
+            "force_eval_ms": round(1e3 * t_f, 1), "hamiltonian_ms": round(1e3 * t_h, 1),
+            "dH": round(res["dH"], 6), "accepted": bool(res["accepted"])}
+
+
 def run_gpu(args):
     import torch
     ws, rank, local = dist_env()
@@ -508,6 +548,7 @@ def run_gpu(args):
         line["force"] = time_force(torch, p)
         line["stout"] = time_stout(torch, p)
         line["gauge"] = time_gauge(torch, p)
+        line["rhmc"] = time_rhmc(torch, p)
         line["cpu_baseline"] = cpu_baseline()
     if ws > 1:
         torch.distributed.barrier()

@@ -173,3 +173,15 @@ def _remez(mp, power, n, lo, hi, max_iter, tol):
     return RationalApprox(power=float(power), lo=float(lo), hi=float(hi), alpha0=float(alpha0),
                           residues=[float(residues[k]) for k in order], poles=[float(poles[k]) for k in order],
                           max_rel_error=float(emax))
+
+
+def load_table(name: str = "rhmc_rational_m0.3.json") -> dict:
+    """Stored approximations written by data/make_rational.py (for hosts without mpmath):
+    {"heatbath": RationalApprox, "action": RationalApprox}."""
+    import json
+    import os
+    path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "data", name)
+    with open(path) as f:
+        raw = json.load(f)
+    return {k: RationalApprox(power=v["power"], lo=v["lo"], hi=v["hi"], alpha0=v["alpha0"], residues=list(v["residues"]),
+                              poles=list(v["poles"]), max_rel_error=v["max_rel_error"]) for k, v in raw.items()}

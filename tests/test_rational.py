@@ -91,7 +91,8 @@ def test_matrix_function_within_error_bound():
 def test_stored_rhmc_coefficients_are_remez_output():
     import json
     import os
-    stored = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "rhmc_rational.json")))
+    stored = json.load(open(os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_1801_01473_gb300", "data",
+                                         "rhmc_rational_m0.3.json")))
     for name, power in (("heatbath", 0.125), ("action", -0.25)):
         r = remez(power, 10, 0.05, 16.5)
         d = stored[name]

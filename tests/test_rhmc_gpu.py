@@ -1,6 +1,6 @@
 """RHMC pieces on the GPU: a rational function of the operator applied to a field, the
 pseudofermion heatbath, and a full trajectory (heatbath, Omelyan MD with gauge + stout-smeared
-fermion forces, Metropolis) with the Remez approximations of tests/golden/rhmc_rational.json.
+fermion forces, Metropolis) with the stored Remez approximations of paper_1801_01473_gb300/data.
 
 * stg_rational_apply vs the oracle's alpha0 b + sum_i r_i x_i (multi-shift solve at 1e-13): 1e-10;
 * heatbath identity: phi = R_{1/8}(A) eta gives phi^dag R_{-1/4}(A) phi = eta^dag eta up to the
@@ -20,7 +20,8 @@ import synthetic as S
 
 pytestmark = pytest.mark.gpu
 
-RAT = json.load(open(os.path.join(os.path.dirname(__file__), "golden", "rhmc_rational.json")))
+RAT = json.load(open(os.path.join(os.path.dirname(os.path.dirname(__file__)), "paper_1801_01473_gb300", "data",
+                               "rhmc_rational_m0.3.json")))
 MASS = 0.3
 
 

@@ -22,7 +22,7 @@ from typing import Sequence
 import torch
 
 from .api import (Gauge, Lattice, complex_convert, fermion_force, gauge_action, gauge_force, md_kinetic, md_momenta,
-                  md_update_links_, md_update_momenta_, mscg, rational_apply, stout_force, stout_smear)
+                  md_update_links_, md_update_momenta_, mscg, mscg_batched, rational_apply, stout_force, stout_smear)
 
 # Omelyan's second-order minimum-norm parameter
 OMELYAN_LAMBDA = 0.1931833275037836
@@ -44,7 +44,9 @@ class Action:
     pseudofermions: list = field(default_factory=list)
     stout_rho: float = 0.0
     stout_steps: int = 0
-    tol: float = 1e-12
+    tol: float = 1e-12              # stopping residual of the action (Metropolis) and heatbath solves
+    md_tol: float | None = None     # stopping residual of the MD force solves (None: tol); Sec. 2 uses
+                                    # different residuals in different parts of the RHMC
     inner: str | None = None        # None: FP64 solve; "f32": mixed FP32-inner solve
     precision: str = "f64"          # forces in "f64" or "f32" (the Hamiltonian is always FP64)
     theta: torch.Tensor | None = None  # U(1) phase field [4, V] on the fermion links (chemical potential, ...)
@@ -60,21 +62,39 @@ class Action:
         gi = Gauge(self.lattice, uk, "f32", 12, theta=self.theta) if self.inner == "f32" else None
         return g64, gi
 
+    def _solve_all(self, g64, gi, tol):
+        """x_i for every pseudofermion; pseudofermions sharing a pole set are solved together in one
+        batched multi-shift solve (their link loads shared, Sec. 2's multiple pseudofermions)."""
+        groups = {}
+        for k, pf in enumerate(self.pseudofermions):
+            groups.setdefault(tuple(float(v) for v in pf.shifts), []).append(k)
+        xs = [None] * len(self.pseudofermions)
+        for shifts, ks in groups.items():
+            if len(ks) == 1:
+                xs[ks[0]], _ = mscg(g64, self.pseudofermions[ks[0]].b, list(shifts), self.mass, tol=tol, g_inner=gi)
+            else:
+                (x, _), = mscg_batched([(g64, gi, [self.pseudofermions[k].b for k in ks])], list(shifts), self.mass,
+                                       tol=tol)
+                for j, k in enumerate(ks):
+                    xs[k] = x[j]
+        return xs
+
     def value(self, links: torch.Tensor) -> float:
         """S_g + S_f of the links."""
         s = gauge_action(self.lattice, links, self.beta)["action"] if self.beta != 0.0 else 0.0
         if self.pseudofermions:
             _, uk = self._smeared(links)
             g64, gi = self._gauges(uk)
-            for pf in self.pseudofermions:
-                x, _ = mscg(g64, pf.b, list(pf.shifts), self.mass, tol=self.tol, g_inner=gi)
+            for pf, x in zip(self.pseudofermions, self._solve_all(g64, gi, self.tol)):
                 bb = pf.b.reshape(-1)
                 s += float(pf.alpha0) * float(torch.vdot(bb, bb).real)
                 s += sum(float(r) * float(torch.vdot(bb, x[i].reshape(-1)).real) for i, r in enumerate(pf.residues))
         return s
 
     def apply_force(self, links: torch.Tensor, mom: torch.Tensor, eps: float) -> None:
-        """mom <- mom - eps i F(links), F the total Lie-algebra force."""
+        """mom <- mom - eps i F(links), F the total Lie-algebra force.  The fermion forces of all
+        pseudofermions are one force evaluation over the union of their (solution, residue) pairs
+        (up to 32 per launch)."""
         f32 = self.precision == "f32"
         u = complex_convert(links, torch.complex64) if f32 else links
         if self.beta != 0.0:
@@ -87,12 +107,15 @@ class Action:
         else:
             levels, uk = None, links
         g64, gi = self._gauges(uk)
-        for pf in self.pseudofermions:
-            x, _ = mscg(g64, pf.b, list(pf.shifts), self.mass, tol=self.tol, g_inner=gi)
+        xs = self._solve_all(g64, gi, self.md_tol if self.md_tol is not None else self.tol)
+        xall = torch.cat(xs) if len(xs) > 1 else xs[0]
+        rall = [float(r) for pf in self.pseudofermions for r in pf.residues]
+        for c0 in range(0, len(rall), 32):
+            x, r = xall[c0:c0 + 32], rall[c0:c0 + 32]
             if levels is None:
-                f = fermion_force(g64, list(pf.residues), x, kind=0)
+                f = fermion_force(g64, r, x, kind=0)
             else:
-                gk = fermion_force(g64, list(pf.residues), x, kind=1)
+                gk = fermion_force(g64, r, x, kind=1)
                 if f32:
                     gk = complex_convert(gk, torch.complex64)
                 f = stout_force(self.lattice, u, levels, self.stout_rho, gk, kind=0)

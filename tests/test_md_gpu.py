@@ -188,3 +188,24 @@ def test_trajectory_with_u1_phases_matches_oracle(p):
     p.md.omelyan(a_gpu, ud, h, 0.4, 6)
     dh6 = p.md.hamiltonian(a_gpu, ud, h) - h0
     assert 3.2 < dh3 / dh6 < 4.8
+
+
+def test_two_pseudofermions_batched_match_oracle(p):
+    """Two pseudofermions with one pole set: solved in one batched multi-shift solve and forced by
+    one force evaluation over both sets of solutions; the trajectory matches the oracle's (1e-9)."""
+    dims = (4, 4, 4, 4)
+    lat = p.Lattice(dims)
+    u = S.gauge_links(dims, "expih", 167)
+    b1, b2 = S.gaussian_field(dims, 168), S.gaussian_field(dims, 169)
+    pf = ([0.05, 0.5], [0.4, 0.3])
+    a_gpu = p.md.Action(lat, beta=5.6, mass=0.2, tol=1e-13, stout_rho=0.15, stout_steps=1,
+                        pseudofermions=[p.md.Pseudofermion(_gpu(b1), *pf), p.md.Pseudofermion(_gpu(b2), *pf)])
+    a_ora = omd.Action(dims, beta=5.6, mass=0.2, pseudofermions=[(b1, *pf), (b2, *pf)], tol=1e-13,
+                       stout_rho=0.15, stout_steps=1)
+    xi = _xi(170, u.shape[1])
+    ud, h = _gpu(u), p.md_momenta(lat, _gpu(xi))
+    p.md.omelyan(a_gpu, ud, h, 0.4, 3)
+    uw, hw = omd.omelyan(a_ora, u, omd.momenta(xi), 0.4, 3)
+    assert np.abs(ud.cpu().numpy() - uw).max() < 1e-9
+    assert np.abs(h.cpu().numpy() - hw).max() < 1e-9
+    assert p.md.hamiltonian(a_gpu, ud, h) == pytest.approx(omd.kinetic(hw) + a_ora.value(uw), rel=1e-10)

@@ -72,8 +72,11 @@ class Action:
                 s += oracle.action(np.asarray(res), b, x)
         return s
 
-    def force(self, u) -> np.ndarray:
-        f = og.force(self.dims, u, self.beta) if self.beta != 0.0 else np.zeros_like(u)
+    def gauge_force(self, u) -> np.ndarray:
+        return og.force(self.dims, u, self.beta) if self.beta != 0.0 else np.zeros_like(u)
+
+    def fermion_force(self, u) -> np.ndarray:
+        f = np.zeros_like(u)
         if self.pf:
             levels = self._levels(u)
             for b, shifts, res in self.pf:
@@ -85,6 +88,9 @@ class Action:
                     gk = oracle.force_u1(self.dims, levels[-1], self.theta, np.asarray(res), x, kind=1)
                 f = f + ost.lie_force(u, ost.stout_backward(self.dims, levels, self.rho, gk))
         return f
+
+    def force(self, u) -> np.ndarray:
+        return self.gauge_force(u) + self.fermion_force(u)
 
 
 def _kick(h, f, eps):
@@ -109,3 +115,30 @@ def omelyan(action: Action, u, h, tau, nsteps, lam=OMELYAN_LAMBDA):
         u = update_links(u, h, 0.5 * eps)
         h = _kick(h, action.force(u), (2.0 if k < nsteps - 1 else 1.0) * lam * eps)
     return u, h
+
+
+def omelyan_multiscale(action: Action, u, h, tau, nsteps, gauge_substeps, lam=OMELYAN_LAMBDA):
+    """Nested Omelyan: the fermion force on the outer level, each outer link update an Omelyan
+    integration under the gauge force with gauge_substeps steps."""
+    state = {"u": u, "h": h}
+
+    def omel(kick, drift, t, n):
+        eps = t / n
+        kick(lam * eps)
+        for k in range(n):
+            drift(0.5 * eps)
+            kick((1.0 - 2.0 * lam) * eps)
+            drift(0.5 * eps)
+            kick((2.0 if k < n - 1 else 1.0) * lam * eps)
+
+    def kick_g(e):
+        state["h"] = _kick(state["h"], action.gauge_force(state["u"]), e)
+
+    def kick_f(e):
+        state["h"] = _kick(state["h"], action.fermion_force(state["u"]), e)
+
+    def drift_u(e):
+        state["u"] = update_links(state["u"], state["h"], e)
+
+    omel(kick_f, lambda t: omel(kick_g, drift_u, t, gauge_substeps), tau, nsteps)
+    return state["u"], state["h"]

@@ -34,6 +34,13 @@ class Pseudofermion:
     shifts: Sequence[float]
     residues: Sequence[float]
     alpha0: float = 0.0             # constant term of the rational approximation (no force)
+    md_shifts: Sequence[float] | None = None    # optional cheaper approximation for the MD force
+    md_residues: Sequence[float] | None = None  # (Sec. 2: different orders in different parts)
+
+    def force_poles(self):
+        if self.md_shifts is not None:
+            return list(self.md_shifts), list(self.md_residues)
+        return list(self.shifts), list(self.residues)
 
 
 @dataclass
@@ -62,12 +69,14 @@ class Action:
         gi = Gauge(self.lattice, uk, "f32", 12, theta=self.theta) if self.inner == "f32" else None
         return g64, gi
 
-    def _solve_all(self, g64, gi, tol):
-        """x_i for every pseudofermion; pseudofermions sharing a pole set are solved together in one
-        batched multi-shift solve (their link loads shared, Sec. 2's multiple pseudofermions)."""
+    def _solve_all(self, g64, gi, tol, md=False):
+        """x_i for every pseudofermion (with its MD poles if md); pseudofermions sharing a pole set
+        are solved together in one batched multi-shift solve (their link loads shared, Sec. 2's
+        multiple pseudofermions)."""
         groups = {}
         for k, pf in enumerate(self.pseudofermions):
-            groups.setdefault(tuple(float(v) for v in pf.shifts), []).append(k)
+            shifts = pf.force_poles()[0] if md else pf.shifts
+            groups.setdefault(tuple(float(v) for v in shifts), []).append(k)
         xs = [None] * len(self.pseudofermions)
         for shifts, ks in groups.items():
             if len(ks) == 1:
@@ -95,21 +104,31 @@ class Action:
         """mom <- mom - eps i F(links), F the total Lie-algebra force.  The fermion forces of all
         pseudofermions are one force evaluation over the union of their (solution, residue) pairs
         (up to 32 per launch)."""
-        f32 = self.precision == "f32"
-        u = complex_convert(links, torch.complex64) if f32 else links
-        if self.beta != 0.0:
-            md_update_momenta_(self.lattice, eps, gauge_force(self.lattice, u, self.beta, kind=0), mom)
+        self.apply_gauge_force(links, mom, eps)
+        self.apply_fermion_force(links, mom, eps)
+
+    def apply_gauge_force(self, links: torch.Tensor, mom: torch.Tensor, eps: float) -> None:
+        """mom <- mom - eps i F_g(links), the gauge part alone (the inner time scale of multi-step MD)."""
+        if self.beta == 0.0:
+            return
+        u = complex_convert(links, torch.complex64) if self.precision == "f32" else links
+        md_update_momenta_(self.lattice, eps, gauge_force(self.lattice, u, self.beta, kind=0), mom)
+
+    def apply_fermion_force(self, links: torch.Tensor, mom: torch.Tensor, eps: float) -> None:
+        """mom <- mom - eps i F_f(links), the fermion part alone."""
         if not self.pseudofermions:
             return
+        f32 = self.precision == "f32"
+        u = complex_convert(links, torch.complex64) if f32 else links
         if self.stout_steps > 0:
             levels = stout_smear(self.lattice, u, self.stout_rho, self.stout_steps)
             uk = complex_convert(levels[-1], torch.complex128) if f32 else levels[-1].contiguous()
         else:
             levels, uk = None, links
         g64, gi = self._gauges(uk)
-        xs = self._solve_all(g64, gi, self.md_tol if self.md_tol is not None else self.tol)
+        xs = self._solve_all(g64, gi, self.md_tol if self.md_tol is not None else self.tol, md=True)
         xall = torch.cat(xs) if len(xs) > 1 else xs[0]
-        rall = [float(r) for pf in self.pseudofermions for r in pf.residues]
+        rall = [float(r) for pf in self.pseudofermions for r in pf.force_poles()[1]]
         for c0 in range(0, len(rall), 32):
             x, r = xall[c0:c0 + 32], rall[c0:c0 + 32]
             if levels is None:
@@ -163,15 +182,45 @@ def omelyan(action: Action, links: torch.Tensor, mom: torch.Tensor, tau: float, 
         action.apply_force(links, mom, (2.0 if k < nsteps - 1 else 1.0) * lam * eps)
 
 
+def _omelyan_steps(kick, drift, tau: float, nsteps: int, lam: float = OMELYAN_LAMBDA) -> None:
+    """Omelyan 2MN over tau in nsteps: kick(h) updates the momenta by a force step of size h,
+    drift(h) evolves the links (and, in a nested integrator, everything faster) over time h."""
+    eps = tau / nsteps
+    kick(lam * eps)
+    for k in range(nsteps):
+        drift(0.5 * eps)
+        kick((1.0 - 2.0 * lam) * eps)
+        drift(0.5 * eps)
+        kick((2.0 if k < nsteps - 1 else 1.0) * lam * eps)
+
+
+def omelyan_multiscale(action: Action, links: torch.Tensor, mom: torch.Tensor, tau: float, nsteps: int,
+                       gauge_substeps: int, lam: float = OMELYAN_LAMBDA) -> None:
+    """Multi-step (nested time-scale) Omelyan integrator, in place: the fermion force, the expensive
+    one, drives the outer level with nsteps steps; every outer link update is itself an Omelyan
+    integration of the links under the gauge force alone with gauge_substeps steps (Sec. 2 lists
+    multi-step integrators among the RHMC's improvements)."""
+    lat = action.lattice
+
+    def inner(h):
+        _omelyan_steps(lambda e: action.apply_gauge_force(links, mom, e),
+                       lambda e: md_update_links_(lat, e, mom, links), h, gauge_substeps, lam)
+
+    _omelyan_steps(lambda e: action.apply_fermion_force(links, mom, e), inner, tau, nsteps, lam)
+
+
 def trajectory(action: Action, links: torch.Tensor, xi: torch.Tensor, tau: float, nsteps: int,
-               uniform: float, integrator: str = "omelyan") -> dict:
+               uniform: float, integrator: str = "omelyan", gauge_substeps: int = 1) -> dict:
     """One RHMC trajectory from links (not modified): momentum heatbath from the standard normal
     numbers xi [4, V, 8], MD to tau, Metropolis test against the uniform number in [0, 1).
     Returns the new links (the old ones if rejected), dH and the decision."""
     mom = md_momenta(action.lattice, xi)
     h0 = hamiltonian(action, links, mom)
     u = links.clone()
-    (omelyan if integrator == "omelyan" else leapfrog)(action, u, mom, tau, nsteps)
+    if integrator == "omelyan" and gauge_substeps > 1:
+        omelyan_multiscale(action, u, mom, tau, nsteps, gauge_substeps)
+    else:
+        (omelyan if integrator == "omelyan" else leapfrog)(action, u, mom, tau, nsteps)
     h1 = hamiltonian(action, u, mom)
     dh = h1 - h0
     accept = uniform < math.exp(min(0.0, -dh))

@@ -209,3 +209,34 @@ def test_two_pseudofermions_batched_match_oracle(p):
     assert np.abs(ud.cpu().numpy() - uw).max() < 1e-9
     assert np.abs(h.cpu().numpy() - hw).max() < 1e-9
     assert p.md.hamiltonian(a_gpu, ud, h) == pytest.approx(omd.kinetic(hw) + a_ora.value(uw), rel=1e-10)
+
+
+def test_multiscale_integrator_matches_oracle(p):
+    """Nested Omelyan (fermion force outer, gauge force inner with 3 substeps): GPU vs oracle
+    trajectory (1e-9)."""
+    dims = (4, 4, 4, 4)
+    lat = p.Lattice(dims)
+    u, a_gpu, a_ora = _actions(p, dims, lat)
+    xi = _xi(171, u.shape[1])
+    ud, h = _gpu(u), p.md_momenta(lat, _gpu(xi))
+    p.md.omelyan_multiscale(a_gpu, ud, h, 0.4, 2, 3)
+    uw, hw = omd.omelyan_multiscale(a_ora, u, omd.momenta(xi), 0.4, 2, 3)
+    assert np.abs(ud.cpu().numpy() - uw).max() < 1e-9
+    assert np.abs(h.cpu().numpy() - hw).max() < 1e-9
+
+
+def test_md_force_uses_its_own_approximation(p):
+    """A pseudofermion with a separate (cheaper) MD approximation: the momentum update of
+    apply_fermion_force is the fermion force of the MD poles and residues, not of the action's."""
+    dims = (4, 4, 4, 4)
+    lat = p.Lattice(dims)
+    u = _gpu(S.gauge_links(dims, "expih", 172))
+    b = _gpu(S.gaussian_field(dims, 173))
+    pf = p.md.Pseudofermion(b, [0.05, 0.5, 3.0], [0.4, 0.3, 0.2], md_shifts=[0.1], md_residues=[0.7])
+    act = p.md.Action(lat, beta=0.0, mass=0.2, tol=1e-13, pseudofermions=[pf])
+    h = torch.zeros((4, lat.V, 3, 3), dtype=torch.complex128, device="cuda")
+    act.apply_fermion_force(u, h, 1.0)
+    g = p.Gauge(lat, u, "f64", 18)
+    x, _ = p.mscg(g, b, [0.1], 0.2, tol=1e-13)
+    f = p.fermion_force(g, [0.7], x, kind=0)
+    assert float((h + 1j * f).abs().max()) <= 1e-12 * float(f.abs().max())

@@ -74,3 +74,20 @@ def test_full_action_with_u1_phases_energy_scaling():
     d1 = _dh(act, u, h, 0.4, 3, omd.omelyan)
     d2 = _dh(act, u, h, 0.4, 6, omd.omelyan)
     assert 3.2 < d1 / d2 < 4.8
+
+
+def test_multiscale_integrator_energy_scaling():
+    """Nested Omelyan (fermion force outer, gauge force inner with 3 substeps): second order in the
+    outer step."""
+    u = S.gauge_links(DIMS, "expih", 150)
+    b = S.gaussian_field(DIMS, 151)
+    h = omd.momenta(_xi(152, u.shape[1]))
+    act = omd.Action(DIMS, beta=5.6, mass=0.2, pseudofermions=[(b, [0.05, 0.5], [0.4, 0.3])])
+
+    def dh(n):
+        h0 = omd.kinetic(h) + act.value(u)
+        u1, h1 = omd.omelyan_multiscale(act, u, h, 0.4, n, 3)
+        return omd.kinetic(h1) + act.value(u1) - h0
+
+    d1, d2 = dh(3), dh(6)
+    assert 3.2 < d1 / d2 < 4.8

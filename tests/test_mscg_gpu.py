@@ -263,3 +263,21 @@ def test_mixed_batch_bitwise_across_launch_shapes(monkeypatch):
             assert max(stats[r]["true_resid"]) <= 1e-10
     assert torch.equal(out["128"][0], out["shared"][0])
     assert out["128"][1] == out["shared"][1]
+
+
+@pytest.mark.parametrize("mass,tol", [(0.3, 1e-7), (0.05, 1e-6), (0.01, 1e-7)])
+def test_loose_tolerance_double_single_certified(mass, tol):
+    """At loose tolerances (MD force solves) the double-single residual certifies a shift without
+    the FP64 operator when tol is ten times its rounding-error bound; where the bound is too large
+    (m = 0.01, sigma = 0) the FP64 check still runs.  Either way the oracle's FP64 residual of every
+    shift is within tol and the reported residual matches it."""
+    p = stg()
+    dims = (4, 4, 6, 8)
+    u = S.gauge_links(dims, "expih", 1011)
+    b = S.gaussian_field(dims, 2011)
+    shifts = [0.0, 0.01, 0.5, 4.0]
+    _, g64, gi = gauges(p, dims, u, ("f32", 12))
+    x, st = p.mscg(g64, torch.from_numpy(b).cuda(), shifts, mass, tol=tol, g_inner=gi)
+    tr = oracle_true_resid(dims, u, mass, shifts, b, x.cpu().numpy())
+    assert np.all(tr <= tol), (tr, st)
+    np.testing.assert_allclose(st["true_resid"], tr, rtol=1e-3, atol=1e-14)

@@ -567,7 +567,8 @@ def run_case(name):
     FP32-inner solves of the 32^4 msCG workload; `force32` three double-single D_eo applications and
     one 4-shift fermion force at 32^4; `stout24` one stout step and its chain rule at 24^4;
     `gauge24` the gauge force and action at 24^4; `fp32links24` the single-precision gauge force,
-    stout step and chain rule at 24^4."""
+    stout step and chain rule at 24^4; `rhmc_force32` one MD force evaluation of the 32^4 RHMC
+    trajectory (inside the NVTX range "force_eval")."""
     import torch
     import paper_1801_01473_gb300 as p
     if name == "mscg":
@@ -608,6 +609,27 @@ def run_case(name):
         ut = torch.from_numpy(S.gauge_links(dims, "expih", 1005)).cuda()
         f = p.gauge_force(lat, ut, 5.6, kind=0)
         print("gauge24", p.gauge_action(lat, ut, 5.6)["action"], float(f.abs().max()))
+    elif name == "rhmc_force32":
+        # one MD force evaluation of the 32^4 trajectory workload (gauge force, 2-step stout
+        # smearing and chain rule, 10-pole mixed solve to 1e-7, fermion force) after one warm-up
+        # evaluation; the second one runs inside the NVTX range "force_eval"
+        from paper_1801_01473_gb300.rational import load_table
+        dims = (32, 32, 32, 32)
+        lat = p.Lattice(dims)
+        u = p.stout_smear(lat, torch.from_numpy(S.gauge_links(dims, "expih", 1002)).cuda(), 0.1, 10)[-1].contiguous()
+        ra = load_table()["action"]
+        b = torch.from_numpy(S.gaussian_field(dims, 2002)).cuda()
+        act = p.md.Action(lat, beta=5.6, mass=0.3, tol=1e-10, md_tol=1e-7, inner="f32", precision="f32",
+                          stout_rho=0.15, stout_steps=2,
+                          pseudofermions=[p.md.Pseudofermion(b, ra.poles, ra.residues, ra.alpha0)])
+        mom = torch.zeros((4, lat.V, 3, 3), dtype=torch.complex128, device="cuda")
+        act.apply_force(u, mom, 0.01)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_push("force_eval")
+        act.apply_force(u, mom, 0.01)
+        torch.cuda.synchronize()
+        torch.cuda.nvtx.range_pop()
+        print("rhmc_force32", float(mom.abs().max()))
     elif name == "fp32links24":
         dims = (24, 24, 24, 24)
         lat = p.Lattice(dims)
@@ -632,7 +654,7 @@ def main():
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--impl", default="stg", choices=["stg", "reference"])
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--case", default=None, choices=["mscg", "force32", "stout24", "gauge24", "fp32links24"],
+    ap.add_argument("--case", default=None, choices=["mscg", "force32", "stout24", "gauge24", "fp32links24", "rhmc_force32"],
                     help="run one small workload for a profiler instead of the benchmark")
     args = ap.parse_args()
     if args.case:

@@ -189,6 +189,13 @@ typedef struct {
     int32_t log_rows;        /* optional: rows of scalar_log to fill (0 = none)                    */
     double *scalar_log;      /* host [log_rows][2 + nshift]: alpha_k, beta_k, zeta_i^{k+1} of the
                                 first multi-shift iterations of system 0                         */
+    int32_t history;         /* mixed solves, multi-shift phase: residuals kept per window of the
+                                deferred solution update (x_i, p_i of every shift formed once per
+                                window from the stored FP32 residuals instead of every
+                                iteration); 0 -> automatic (up to 256 within 4 GiB of residual
+                                storage per solve), 1 -> per-iteration updates, >= 2 -> that many
+                                (rounded down to a multiple of 8, at least 8, at most 256);
+                                < 0 -> STG_ERR_ARG                                               */
 } stg_mscg_params;
 
 typedef struct {

@@ -233,12 +233,12 @@ def normal_op(gauge: Gauge, mass: float, shift: float, psi_even: torch.Tensor) -
 
 # ------------------------------------------------------------------ multi-shift CG
 
-def _params(shifts, mass, tol, max_iter, inner_tol, reliable_delta, log_rows):
+def _params(shifts, mass, tol, max_iter, inner_tol, reliable_delta, log_rows, history=0):
     sh = (ctypes.c_double * len(shifts))(*[float(s) for s in shifts])
     log = (ctypes.c_double * max(1, log_rows * (2 + len(shifts))))()
     p = MscgParams(len(shifts), ctypes.cast(sh, ctypes.POINTER(ctypes.c_double)), float(mass), float(tol),
                    int(max_iter), float(inner_tol), float(reliable_delta), int(log_rows),
-                   ctypes.cast(log, ctypes.POINTER(ctypes.c_double)) if log_rows > 0 else None)
+                   ctypes.cast(log, ctypes.POINTER(ctypes.c_double)) if log_rows > 0 else None, int(history))
     return p, sh, log
 
 
@@ -259,15 +259,16 @@ def _stats_dict(st, tr, extra):
 
 def mscg(g_f64: Gauge, b: torch.Tensor, shifts, mass: float, tol: float = 1e-10, g_inner: Gauge | None = None,
          max_iter: int = 20000, inner_tol: float = 0.0, reliable_delta: float = 0.0, log_rows: int = 0,
-         allow_noconv: bool = False, out: torch.Tensor | None = None, stream=None):
+         allow_noconv: bool = False, out: torch.Tensor | None = None, history: int = 0, stream=None):
     """Multi-shift CG: x_i = (m^2 + sigma_i - D_eo D_oe)^-1 b.  b canonical complex128 [Vh, 3].
-    Returns (x [nshift, Vh, 3] complex128, stats dict)."""
+    history: residuals per window of the deferred multi-shift update of mixed solves (0 automatic,
+    1 per-iteration updates).  Returns (x [nshift, Vh, 3] complex128, stats dict)."""
     host = not b.is_cuda
     bd = _dev(b).reshape(g_f64.lattice.Vh, 3)
     ns = len(shifts)
     x = out if out is not None else torch.empty((ns, g_f64.lattice.Vh, 3), dtype=torch.complex128, device="cuda")
     xp = (ctypes.c_void_p * ns)(*[x[i].data_ptr() for i in range(ns)])
-    p, _sh, log = _params(shifts, mass, tol, max_iter, inner_tol, reliable_delta, log_rows)
+    p, _sh, log = _params(shifts, mass, tol, max_iter, inner_tol, reliable_delta, log_rows, history)
     st, tr, si = _stats(ns)
     rc = lib().stg_mscg_solve(g_f64.handle, g_inner.handle if g_inner is not None else None, ctypes.byref(p), _ptr(bd),
                               ctypes.cast(xp, ctypes.POINTER(ctypes.c_void_p)), ctypes.byref(st), _stream(stream))
@@ -297,7 +298,7 @@ def rational_apply(g_f64: Gauge, b: torch.Tensor, alpha0: float, residues, poles
 
 
 def mscg_batched(instances, shifts, mass: float, tol: float = 1e-10, max_iter: int = 20000, inner_tol: float = 0.0,
-                 reliable_delta: float = 0.0, stream=None):
+                 reliable_delta: float = 0.0, history: int = 0, stream=None):
     """instances: list of (g_f64, g_inner or None, [b_r canonical [Vh,3] cuda tensors]).
     Returns list of (x [nrhs, nshift, Vh, 3], [stats per rhs])."""
     ns = len(shifts)
@@ -321,7 +322,7 @@ def mscg_batched(instances, shifts, mass: float, tol: float = 1e-10, max_iter: i
                           ctypes.cast(sts, ctypes.POINTER(MscgStats)))
         keep += [bs, bp, xp, sts, bufs]
         outs.append((x, sts, bufs))
-    p, _sh, _log = _params(shifts, mass, tol, max_iter, inner_tol, reliable_delta, 0)
+    p, _sh, _log = _params(shifts, mass, tol, max_iter, inner_tol, reliable_delta, 0, history)
     check(lib().stg_mscg_solve_batched(len(instances), arr, ctypes.byref(p), _stream(stream)), "stg_mscg_solve_batched")
     res = []
     for x, sts, bufs in outs:

@@ -59,6 +59,23 @@ struct SysScal {
     double cx[kMaxShifts], cr[kMaxShifts], cp[kMaxShifts];
     int upd_x[kMaxShifts], upd_p[kMaxShifts], active[kMaxShifts], shift_iters[kMaxShifts];
     int nshift, i0, running, iters, max_iter, nactive, phase2, stalls;
+    int win_start, hist_overflow;  // deferred update: iteration at the window start, entry overflow
+};
+
+struct HistEntry {
+    double ax, pr, pp;  // iteration of a window: x_i += ax p_i ; p_i = pr r + pp p_i
+};
+
+constexpr int kHistMax = 256;     // deferred update: residuals per window (a multiple of the chunk)
+constexpr int kFlushShifts = 8;   // shifts per thread block of the window flush
+
+// Coefficients of one window flush of one system (filled by k_flush_coef)
+struct FlushCoef {
+    float a[kHistMax][kMaxShifts];  // x_i += sum_t a[t][i] r^(t) + e[i] P0_i
+    float d[kHistMax][kMaxShifts];  // p_i  = sum_t d[t][i] r^(t) + f[i] P0_i
+    float e[kMaxShifts], f[kMaxShifts];
+    int xupd[kMaxShifts], pmat[kMaxShifts];
+    int n, first_slot;
 };
 
 struct SysVecs {
@@ -68,7 +85,20 @@ struct SysVecs {
     const double2 *bcanon;                   // canonical source (phase 1)
     double *part_d, *part_v, *part_v2;       // partial sums (64-site dslash chunks / 32-site warps)
     int Vh, nblk_d, nblk_v, npart_v;  // nblk_v: kVecBlock-site blocks; npart_v: partials (one per 32 sites)
+    // deferred update (phase 1 of mixed solves): r is a ring of nslot residual fields (slot k % nslot
+    // holds r^k), pstart the base direction at the window start, hist/coef the window's scalars
+    int nslot;
+    size_t slot_bytes;
+    void *pstart;
+    HistEntry *hist;  // [kHistMax][kMaxShifts]
+    FlushCoef *coef;
 };
+
+template <typename R>
+__device__ __forceinline__ void *ring_slot(const SysVecs &V, int k)
+{
+    return static_cast<char *>(V.r) + (size_t)(k % V.nslot) * V.slot_bytes;
+}
 
 // ------------------------------------------------------------------ vector kernels
 
@@ -108,6 +138,7 @@ __global__ void __launch_bounds__(kVecBlock) k_p1_init(const SysVecs *__restrict
             Field<R>::store(V.p[i], V.Vh, h, v);
             Field<H>::store(V.x[i], V.Vh, h, z);
         }
+        if (V.pstart) Field<R>::store(V.pstart, V.Vh, h, v);
         if (V.b64) {
             cx<H> w[3];
 #pragma unroll
@@ -156,12 +187,15 @@ __global__ void __launch_bounds__(kVecBlock) k_update_r(const SysScal *__restric
         ProdSum<R> pr;
         if (h < V.Vh) {
             const R a = (R)S.alpha;
+            // in a ring, r^(k+1) goes to the next slot and r^k stays for the window flush
+            void *rin = V.nslot ? ring_slot<R>(V, S.iters) : V.r;
+            void *rout = V.nslot ? ring_slot<R>(V, S.iters + 1) : V.r;
             cx<R> r[3], q[3];
-            Field<R>::load_rw(V.r, V.Vh, h, r);
+            Field<R>::load_rw(rin, V.Vh, h, r);
             Field<R>::load_rw(V.q, V.Vh, h, q);
 #pragma unroll
             for (int c = 0; c < 3; ++c) r[c] = cx<R>{fma(-a, q[c].re, r[c].re), fma(-a, q[c].im, r[c].im)};
-            Field<R>::store(V.r, V.Vh, h, r);
+            Field<R>::store(rout, V.Vh, h, r);
             norm2_site(pr, r);
         }
         warp_partial(pr, h, V.Vh, V.part_v);
@@ -222,6 +256,208 @@ __global__ void __launch_bounds__(kVecBlock) k_update_shifts(const SysScal *__re
                 for (int c = 0; c < 3; ++c)
                     p[c] = cx<R>{fma(zr, r[c].re, bb * p[c].re), fma(zr, r[c].im, bb * p[c].im)};
                 Field<R>::store(V.p[i], V.Vh, h, p);
+            }
+        }
+    }
+}
+
+// Deferred multi-shift update (phase 1 of mixed solves).  Instead of moving x_i and p_i of every
+// live shift each iteration, the residuals r^k of a window of n iterations stay in a ring and the
+// window's scalars in a history; per iteration only the base direction p (the input of D) is
+// updated.  Unrolling x_i += ax_t p_i ; p_i = pr_t r^(t) + pp_t p_i over the window t = 1..n gives
+//   x_i <- x_i + sum_t a_t r^(t) + e P0_i ,   p_i <- sum_t d_t r^(t) + f P0_i
+// with P0_i the p_i at the window start and, backwards from S_n = 0, P_n = 1,
+//   a_t = pr_t S_t ,  d_t = pr_t P_t ,  S_{t-1} = ax_t + pp_t S_t ,  P_{t-1} = pp_t P_t ,  e = S_0 ,  f = P_0 :
+// the same solutions in exact arithmetic, for 3 fields of traffic per iteration instead of 8 per
+// live shift.  The window is flushed when it is full (p_i materialised for the next window) and at
+// the end of the phase (x_i only).
+
+// p = pr r^k + pp p for the base direction (r^k the newest ring slot)
+template <typename R>
+__global__ void __launch_bounds__(kVecBlock) k_update_pbase(const SysScal *__restrict__ sc,
+                                                             const SysVecs *__restrict__ sv, const WorkList w)
+{
+    pdl_enter();
+    int s = 0;
+    for (int b = blockIdx.x; b < w.total; b += gridDim.x) {
+        s = advance_sys(w, s, b);
+        const SysScal &S = sc[s];
+        if (!S.running || !S.upd_p[S.i0]) continue;  // uniform over the block
+        const SysVecs &V = sv[s];
+        const int h = (b - w.start[s]) * kVecBlock + threadIdx.x;
+        if (h >= V.Vh) continue;
+        const R zr = (R)S.cr[S.i0], bb = (R)S.cp[S.i0];
+        cx<R> r[3], p[3];
+        Field<R>::load_rw(ring_slot<R>(V, S.iters), V.Vh, h, r);
+        Field<R>::load_rw(V.p[S.i0], V.Vh, h, p);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) p[c] = cx<R>{fma(zr, r[c].re, bb * p[c].re), fma(zr, r[c].im, bb * p[c].im)};
+        Field<R>::store(V.p[S.i0], V.Vh, h, p);
+    }
+}
+
+// coefficients of a window flush, one warp per system, one lane per shift (backward recursion in FP64)
+__global__ void k_flush_coef(SysScal *sc, const SysVecs *sv, int final_flush)
+{
+    SysScal &S = sc[blockIdx.x];
+    const SysVecs &V = sv[blockIdx.x];
+    FlushCoef &C = *V.coef;
+    const int n = min(S.iters - S.win_start, kHistMax);
+    const int i = threadIdx.x;
+    if (i < S.nshift) {
+        double sx = 0.0, pp = 1.0;
+        int any = 0;
+        for (int t = n - 1; t >= 0; --t) {
+            const HistEntry h = V.hist[t * kMaxShifts + i];
+            C.a[t][i] = (float)(h.pr * sx);
+            C.d[t][i] = (float)(h.pr * pp);
+            sx = h.ax + h.pp * sx;
+            pp = h.pp * pp;
+            any |= h.ax != 0.0;
+        }
+        C.e[i] = (float)sx;
+        C.f[i] = (float)pp;
+        C.xupd[i] = any;
+        C.pmat[i] = !final_flush && n > 0 && i != S.i0 && S.active[i];
+    }
+    __syncwarp();
+    if (threadIdx.x == 0) {
+        C.n = n;
+        C.first_slot = (S.win_start + 1) % V.nslot;
+        S.win_start = S.iters;
+    }
+}
+
+template <typename H>
+__device__ __forceinline__ void fold_acc(H &acc, float v);
+template <>
+__device__ __forceinline__ void fold_acc<dsf>(dsf &acc, float v)
+{
+    const dsf t = ds_two_sum(acc.hi, v);
+    acc = ds_fast_two_sum(t.hi, __fadd_rn(t.lo, acc.lo));
+}
+template <>
+__device__ __forceinline__ void fold_acc<double>(double &acc, float v)
+{
+    acc += (double)v;
+}
+
+// One window flush over the complex elements of the FP32 fields (element e of a field is its
+// float2 number e: colours 0, 1 of site e/2 for e < 2Vh, colour 2 of site e - 2Vh above), each thread
+// block covering kFlushShifts shifts.  Sums of 8 terms are formed in FP32 and folded into an
+// accumulator of the solution precision H.
+template <typename H, bool MATP>
+__global__ void __launch_bounds__(kVecBlock) k_flush(const SysScal *__restrict__ sc, const SysVecs *__restrict__ sv,
+                                                      int nchunk)
+{
+    __shared__ __align__(16) float s_a[kHistMax][kFlushShifts];
+    __shared__ __align__(16) float s_d[MATP ? kHistMax : 1][kFlushShifts];
+    __shared__ int s_any;
+    const SysScal &S = sc[blockIdx.y];
+    const SysVecs &V = sv[blockIdx.y];
+    const FlushCoef &C = *V.coef;
+    const int chunk = blockIdx.x % nchunk, eb = blockIdx.x / nchunk;
+    const int i0c = chunk * kFlushShifts, nsc = min(kFlushShifts, S.nshift - i0c);
+    const int nel = 3 * V.Vh;
+    if (nsc <= 0 || eb * kVecBlock >= nel) return;  // uniform over the block
+    const int n = C.n;
+    if (threadIdx.x == 0) {
+        int any = 0;
+        for (int j = 0; j < nsc; ++j) any |= C.xupd[i0c + j] | (MATP ? C.pmat[i0c + j] | (i0c + j == S.i0) : 0);
+        s_any = any;
+    }
+    for (int k = threadIdx.x; k < n * kFlushShifts; k += kVecBlock) {
+        const int t = k / kFlushShifts, j = k % kFlushShifts;
+        s_a[t][j] = j < nsc ? C.a[t][i0c + j] : 0.f;
+        if constexpr (MATP) s_d[t][j] = j < nsc ? C.d[t][i0c + j] : 0.f;
+    }
+    __syncthreads();
+    if (!s_any) return;
+    const int e = eb * kVecBlock + threadIdx.x;
+    if (e >= nel) return;
+
+    float2 bx[kFlushShifts], bp[kFlushShifts];
+    H ax[kFlushShifts], ay[kFlushShifts];
+#pragma unroll
+    for (int j = 0; j < kFlushShifts; ++j) {
+        bx[j] = make_float2(0.f, 0.f);
+        bp[j] = make_float2(0.f, 0.f);
+        ax[j] = H(0);
+        ay[j] = H(0);
+    }
+    int slot = C.first_slot;
+    const int nslot = V.nslot;
+    const char *ring = static_cast<const char *>(V.r);
+    for (int t0 = 0; t0 < n; t0 += 8) {
+        const int m = min(8, n - t0);
+        float2 rv[8];
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            if (u < m) {
+                rv[u] = reinterpret_cast<const float2 *>(ring + (size_t)slot * V.slot_bytes)[e];
+                slot = slot + 1 == nslot ? 0 : slot + 1;
+            } else {
+                rv[u] = make_float2(0.f, 0.f);
+            }
+        }
+#pragma unroll
+        for (int u = 0; u < 8; ++u) {
+            const int t = t0 + u < n ? t0 + u : n - 1;  // rv[u] is zero past the end
+            const float4 a0 = *reinterpret_cast<const float4 *>(&s_a[t][0]);
+            const float4 a1 = *reinterpret_cast<const float4 *>(&s_a[t][4]);
+            const float av[8] = {a0.x, a0.y, a0.z, a0.w, a1.x, a1.y, a1.z, a1.w};
+#pragma unroll
+            for (int j = 0; j < kFlushShifts; ++j) {
+                bx[j].x = fmaf(av[j], rv[u].x, bx[j].x);
+                bx[j].y = fmaf(av[j], rv[u].y, bx[j].y);
+            }
+            if constexpr (MATP) {
+                const float4 d0 = *reinterpret_cast<const float4 *>(&s_d[t][0]);
+                const float4 d1 = *reinterpret_cast<const float4 *>(&s_d[t][4]);
+                const float dv[8] = {d0.x, d0.y, d0.z, d0.w, d1.x, d1.y, d1.z, d1.w};
+#pragma unroll
+                for (int j = 0; j < kFlushShifts; ++j) {
+                    bp[j].x = fmaf(dv[j], rv[u].x, bp[j].x);
+                    bp[j].y = fmaf(dv[j], rv[u].y, bp[j].y);
+                }
+            }
+        }
+#pragma unroll
+        for (int j = 0; j < kFlushShifts; ++j) {
+            fold_acc<H>(ax[j], bx[j].x);
+            fold_acc<H>(ay[j], bx[j].y);
+            bx[j] = make_float2(0.f, 0.f);
+        }
+    }
+    // element e -> (site, colour) of the solution fields
+    const int h = e < 2 * V.Vh ? e >> 1 : e - 2 * V.Vh;
+    const int c = e < 2 * V.Vh ? e & 1 : 2;
+#pragma unroll
+    for (int j = 0; j < kFlushShifts; ++j) {
+        const int i = i0c + j;
+        if (j >= nsc) break;
+        const bool base = i == S.i0;
+        float2 *p0 = reinterpret_cast<float2 *>(base ? V.pstart : V.p[i]);
+        const float2 pv = p0[e];
+        if (C.xupd[i] || C.e[i] != 0.f) {
+            fold_acc<H>(ax[j], C.e[i] * pv.x);
+            fold_acc<H>(ay[j], C.e[i] * pv.y);
+            if constexpr (std::is_same<H, dsf>::value) {
+                float4 *xp = static_cast<float4 *>(V.x[i]) + (size_t)c * V.Vh + h;
+                const float4 xv = *xp;
+                const dsf re = dsf(xv.x, xv.y) + ax[j], im = dsf(xv.z, xv.w) + ay[j];
+                *xp = make_float4(re.hi, re.lo, im.hi, im.lo);
+            } else {
+                double2 *xp = static_cast<double2 *>(V.x[i]) + (size_t)c * V.Vh + h;
+                const double2 xv = *xp;
+                *xp = make_double2(xv.x + ax[j], xv.y + ay[j]);
+            }
+        }
+        if constexpr (MATP) {
+            if (base) {
+                p0[e] = reinterpret_cast<const float2 *>(V.p[i])[e];  // the explicit base direction
+            } else if (C.pmat[i]) {
+                p0[e] = make_float2(fmaf(C.f[i], pv.x, bp[j].x), fmaf(C.f[i], pv.y, bp[j].y));
             }
         }
     }
@@ -360,6 +596,7 @@ __global__ void __launch_bounds__(kScalBlock) k_beta(SysScal *sc, const SysVecs 
     }
     nact = warp_sum_int(nact);
     const bool cont = nact > 0 && S.iters + 1 < S.max_iter;
+    const int slot = S.iters - S.win_start;  // deferred update: this iteration's history entry
     for (int i = threadIdx.x; i < ns; i += 32) {
         if (!cont) {
             S.upd_p[i] = 0;
@@ -367,6 +604,13 @@ __global__ void __launch_bounds__(kScalBlock) k_beta(SysScal *sc, const SysVecs 
             S.upd_p[i] = 1;
             S.cr[i] = 1.0;
             S.cp[i] = beta;
+        }
+        if (V.hist != nullptr && slot < kHistMax) {
+            HistEntry h;
+            h.ax = S.upd_x[i] ? S.cx[i] : 0.0;
+            h.pr = S.upd_p[i] ? S.cr[i] : 0.0;
+            h.pp = S.upd_p[i] ? S.cp[i] : 1.0;
+            V.hist[slot * kMaxShifts + i] = h;
         }
         if (log != nullptr && blockIdx.x == 0 && S.iters < log_rows)
             log[(size_t)S.iters * (2 + ns) + 2 + i] = S.upd_x[i] ? S.zeta[i] : 0.0;
@@ -382,6 +626,7 @@ __global__ void __launch_bounds__(kScalBlock) k_beta(SysScal *sc, const SysVecs 
         S.rr = rr_new;
         S.iters += 1;
         S.nactive = nact;
+        if (V.hist != nullptr && slot >= V.nslot - 1) S.hist_overflow = 1;
         if (!cont) done[blockIdx.x] = 1;
         if (S.phase2 && (!cont || rr_new < S.delta2 * S.rr_last)) need_rel[blockIdx.x] = 1;
     }
@@ -691,6 +936,22 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     memset(v2.data(), 0, sizeof(SysVecs) * npair);
     memset(s1.data(), 0, sizeof(SysScal) * nsys);
     memset(s2.data(), 0, sizeof(SysScal) * npair);
+    // Deferred multi-shift update (FP32 phase 1): window length W (a multiple of the chunk), ring of
+    // W + 1 residuals per system; prm->history: 0 automatic (up to kHistMax within 4 GiB of rings),
+    // 1 per-iteration updates, >= 8 that many residuals per window
+    int hist_w = 0;
+    if (std::is_same<R, float>::value && prm->history != 1) {
+        size_t ring_field = 0;
+        for (int k = 0; k < ninst; ++k)
+            ring_field += (size_t)ii[k].nrhs * ii[k].g64->g.Vh * Field<R>::kBytesPerSite;
+        if (prm->history >= 2) {
+            hist_w = std::min(kHistMax, std::max(8, prm->history));
+        } else {
+            const size_t budget = (size_t)4 << 30;
+            hist_w = (int)std::min<size_t>(kHistMax, budget / std::max<size_t>(ring_field, 1) - 1);
+        }
+        hist_w = std::max(8, hist_w - hist_w % 8);
+    }
     int nblkv_max = 0;
     for (int k = 0; k < ninst; ++k) {
         const int Vh = ii[k].g64->g.Vh;
@@ -704,7 +965,16 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
             V.nblk_d = nbd;
             V.nblk_v = nbv;
             V.npart_v = npv;
-            V.r = mem.alloc(fb);
+            if (hist_w > 0) {
+                V.nslot = hist_w + 1;
+                V.slot_bytes = fb;
+                V.r = mem.alloc(fb * V.nslot);
+                V.pstart = mem.alloc(fb);
+                V.hist = static_cast<HistEntry *>(mem.alloc(sizeof(HistEntry) * kHistMax * kMaxShifts));
+                V.coef = static_cast<FlushCoef *>(mem.alloc(sizeof(FlushCoef)));
+            } else {
+                V.r = mem.alloc(fb);
+            }
             V.q = mem.alloc(fb);
             V.t = mem.alloc(fb);
             for (int i = 0; i < ns; ++i) {
@@ -888,6 +1158,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     };
     const dim3 g_r1 = wave((const void *)k_update_r<R>, wl1.total), g_r2 = wave((const void *)k_update_r<R>, wl2.total);
     const dim3 g_s1 = wave((const void *)k_update_shifts<R, H>, wl1.total);
+    const dim3 g_pb = wave((const void *)k_update_pbase<R>, wl1.total);
     const dim3 g_s2 = wave((const void *)k_update_shifts<R, R>, wl2.total);
     cudaGetLastError();
 
@@ -910,11 +1181,28 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         if ((e = launch_pdl(k_beta, dim3(n), dim3(kScalBlock), ws, dS, (const SysVecs *)dV, dn, nr, log, log_rows)) !=
             cudaSuccess)
             return e;
-        if (ph1)  // multi-shift phase: solutions in H
+        if (ph1 && hist_w > 0)  // deferred multi-shift update: the base direction only
+            e = launch_pdl(k_update_pbase<R>, g_pb, dim3(kVecBlock), ws, (const SysScal *)dS, (const SysVecs *)dV, wl);
+        else if (ph1)  // multi-shift phase: solutions in H
             e = launch_pdl(k_update_shifts<R, H>, g_s1, dim3(kVecBlock), ws, (const SysScal *)dS, (const SysVecs *)dV, wl);
         else      // refinement: the correction y in R
             e = launch_pdl(k_update_shifts<R, R>, g_s2, dim3(kVecBlock), ws, (const SysScal *)dS, (const SysVecs *)dV, wl);
         return e;
+    };
+
+    // window flush of the deferred update (every system of phase 1)
+    int nblke_max = 0;
+    for (int q = 0; q < nsys; ++q) nblke_max = std::max(nblke_max, (3 * v1[q].Vh + kVecBlock - 1) / kVecBlock);
+    const int nchunk = (ns + kFlushShifts - 1) / kFlushShifts;
+    auto flush = [&](bool final_flush) -> cudaError_t {
+        if (hist_w == 0) return cudaSuccess;
+        k_flush_coef<<<nsys, 32, 0, ws>>>(d_s1, d_v1, final_flush ? 1 : 0);
+        const dim3 g((unsigned)(nchunk * nblke_max), nsys);
+        if (final_flush)
+            k_flush<H, false><<<g, kVecBlock, 0, ws>>>(d_s1, d_v1, nchunk);
+        else
+            k_flush<H, true><<<g, kVecBlock, 0, ws>>>(d_s1, d_v1, nchunk);
+        return cudaGetLastError();
     };
 
     // Chunks of `kChunk` iterations are captured once per phase into a CUDA graph and replayed;
@@ -934,7 +1222,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     // system asks for a reliable update).
     auto run_until_done = [&](GraphCache &gc, int kind, const DPlan &pl, SysScal *dS, SysVecs *dV, int *dn, int *nr, int n,
                               dim3 vg, double *log, int log_rows, bool stop_on_need, std::vector<int> &h_done,
-                              std::vector<int> &h_need) -> stg_status {
+                              std::vector<int> &h_need, int flush_every = 0) -> stg_status {
         if (gc.state == 0) {
             // the D launches of one iteration, outside capture, settle the autotuned block sizes;
             // their outputs (t, q, partials) are recomputed by the first captured iteration
@@ -959,6 +1247,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
             cudaError_t e = gc.state == 1 ? cudaGraphLaunch(gc.exec, ws) : cudaSuccess;
             for (int k = 0; gc.state != 1 && k < kChunk && e == cudaSuccess; ++k)
                 e = iterate(kind, pl, dS, dV, dn, nr, n, vg, log, log_rows);
+            if (e == cudaSuccess && flush_every > 0 && (c + 1) % flush_every == 0) e = flush(false);
             if (e == cudaSuccess) e = cudaMemcpyAsync(h_done.data(), dn, sizeof(int) * n, cudaMemcpyDeviceToHost, ws);
             if (e == cudaSuccess && stop_on_need)
                 e = cudaMemcpyAsync(h_need.data(), nr, sizeof(int) * n, cudaMemcpyDeviceToHost, ws);
@@ -985,8 +1274,9 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     STG_CUDA_TRY(cudaGetLastError());
     std::vector<int> h_done1(nsys), h_need1(nsys);
     stg_status st = run_until_done(gc1, kind_i, p1, d_s1, d_v1, done1, need1, nsys, vgrid1, d_log, prm->log_rows, false,
-                                   h_done1, h_need1);
+                                   h_done1, h_need1, hist_w / kChunk);
     if (st != STG_OK) return st;
+    STG_CUDA_TRY(flush(true));
     stamp("phase 1 (multi-shift CG) done");
 
     // ---------------- phase 2: true residuals (precision H), refinement with reliable updates
@@ -995,6 +1285,8 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         std::vector<SysScal> tmp(nsys);
         STG_CUDA_TRY(cudaMemcpyAsync(tmp.data(), d_s1, sizeof(SysScal) * nsys, cudaMemcpyDeviceToHost, ws));
         STG_CUDA_TRY(cudaStreamSynchronize(ws));
+        for (int s = 0; s < nsys; ++s)
+            if (tmp[s].hist_overflow) return set_error(STG_ERR_CUDA, "stg_mscg_solve: internal error: residual history overflow");
         for (int s = 0; s < nsys; ++s) {
             s1[s] = tmp[s];
             for (int i = 0; i < ns; ++i) {
@@ -1177,6 +1469,7 @@ static stg_status validate(int ninst, const stg_instance *inst, const stg_mscg_p
             return set_error(STG_ERR_ARG, "stg_mscg_solve: shifts must be finite and >= 0");
     if (!std::isfinite(prm->mass) || !(prm->tol > 0.0) || prm->max_iter < 1)
         return set_error(STG_ERR_ARG, "stg_mscg_solve: need finite mass, tol > 0, max_iter > 0");
+    if (prm->history < 0) return set_error(STG_ERR_ARG, "stg_mscg_solve: history must be >= 0");
     if (prm->log_rows < 0 || (prm->log_rows > 0 && !prm->scalar_log))
         return set_error(STG_ERR_ARG, "stg_mscg_solve: scalar_log required when log_rows > 0");
     mixed = inst[0].g_inner != nullptr;

@@ -35,7 +35,8 @@ class MscgParams(ctypes.Structure):
     _fields_ = [("nshift", ctypes.c_int32), ("shifts", ctypes.POINTER(ctypes.c_double)),
                 ("mass", ctypes.c_double), ("tol", ctypes.c_double), ("max_iter", ctypes.c_int32),
                 ("inner_tol", ctypes.c_double), ("reliable_delta", ctypes.c_double),
-                ("log_rows", ctypes.c_int32), ("scalar_log", ctypes.POINTER(ctypes.c_double))]
+                ("log_rows", ctypes.c_int32), ("scalar_log", ctypes.POINTER(ctypes.c_double)),
+                ("history", ctypes.c_int32)]
 
 
 class MscgStats(ctypes.Structure):

@@ -143,6 +143,8 @@ def test_invalid_arguments_rejected():
     other = p.Gauge(p.Lattice((4, 4, 4, 6)), torch.from_numpy(S.gauge_links((4, 4, 4, 6), "haar", 4)).cuda(), "f32", 12)
     with pytest.raises(p.StgError):
         p.mscg(g64, b, [0.0], 0.1, g_inner=other)  # lattices differ
+    with pytest.raises(p.StgError):
+        p.mscg(g64, b, [0.0], 0.1, g_inner=gi, history=-1)  # negative history length
 
 
 @pytest.mark.parametrize("inner", [("f32", 12), ("bf16", 12)])
@@ -281,3 +283,47 @@ def test_loose_tolerance_double_single_certified(mass, tol):
     tr = oracle_true_resid(dims, u, mass, shifts, b, x.cpu().numpy())
     assert np.all(tr <= tol), (tr, st)
     np.testing.assert_allclose(st["true_resid"], tr, rtol=1e-3, atol=1e-14)
+
+
+@pytest.mark.parametrize("history", [0, 8, 24])
+def test_deferred_update_matches_per_iteration(small, history):
+    """The deferred multi-shift update (x_i, p_i formed once per window of stored FP32 residuals)
+    against per-iteration updates (history=1): the multi-shift recurrences do not depend on x_i, so
+    the scalar log and iteration counts agree bitwise; every shift meets tol in the oracle's FP64
+    residual and the two solutions agree to the solve's accuracy.  history=8 flushes (and
+    materialises p_i) every 8 iterations."""
+    cfg, dims, u, b = small
+    p = stg()
+    shifts = cfg["shifts"]()
+    _, g64, gi = gauges(p, dims, u, ("f32", 12))
+    bt = torch.from_numpy(b).cuda()
+    x1, st1 = p.mscg(g64, bt, shifts, cfg["mass"], tol=cfg["tol"], g_inner=gi, log_rows=40, history=1)
+    xh, sth = p.mscg(g64, bt, shifts, cfg["mass"], tol=cfg["tol"], g_inner=gi, log_rows=40, history=history)
+    assert st1["iters"] == sth["iters"] and st1["iters"] > 16
+    np.testing.assert_array_equal(st1["scalar_log"], sth["scalar_log"])
+    trh = oracle_true_resid(dims, u, cfg["mass"], shifts, b, xh.cpu().numpy())
+    assert np.all(trh <= cfg["tol"]), (trh, sth)
+    for i in range(len(shifts)):
+        d = (x1[i] - xh[i]).abs().max().item() / x1[i].abs().max().item()
+        assert d < 1e-8, (i, d)
+
+
+def test_deferred_update_batched_uneven_windows():
+    """Windows of 8 residuals over a batch of lattices of different sizes and several sources:
+    every system within tol (oracle), iteration counts equal to per-iteration updates."""
+    p = stg()
+    shifts = [0.0, 0.02, 0.3, 2.0, 9.0]
+    insts, data = [], []
+    for k, dims in enumerate([(4, 4, 4, 4), (4, 4, 6, 8), (6, 6, 6, 4)]):
+        u = S.gauge_links(dims, "expih", 1030 + k)
+        bs = [S.gaussian_field(dims, 2030 + 10 * k + r) for r in range(2)]
+        _, g64, gi = gauges(p, dims, u, ("f32", 12))
+        insts.append((g64, gi, [torch.from_numpy(b).cuda() for b in bs]))
+        data.append((dims, u, bs))
+    res8 = p.mscg_batched(insts, shifts, 0.1, tol=1e-10, history=8)
+    res1 = p.mscg_batched(insts, shifts, 0.1, tol=1e-10, history=1)
+    for (dims, u, bs), (x8, st8), (_, st1) in zip(data, res8, res1):
+        for r, b in enumerate(bs):
+            assert st8[r]["iters"] == st1[r]["iters"]
+            tr = oracle_true_resid(dims, u, 0.1, shifts, b, x8[r].cpu().numpy())
+            assert np.all(tr <= 1e-10), tr

@@ -91,21 +91,22 @@ __global__ void __launch_bounds__(kMdBlock) k_md_update_links(const __grid_const
     stl(a.U, l, mul<false, false>(poly3(e.f, q, q2), u));
 }
 
+// elementwise over the 9 nlink complex entries (coalesced); FP32 forces widened on the integer pipes
+__device__ __forceinline__ double widen(double v) { return v; }
+__device__ __forceinline__ double widen(float v) { return f32_to_f64(v); }
+
 template <typename C>
 __global__ void __launch_bounds__(kMdBlock) k_md_update_momenta(const __grid_constant__ MdArgs a)
 {
-    const long long l = (long long)blockIdx.x * kMdBlock + threadIdx.x;
-    if (l >= a.nlink) return;
-    const C *f = static_cast<const C *>(a.F) + l * 9;
-    double2 *h = a.H + l * 9;
-#pragma unroll
-    for (int k = 0; k < 9; ++k) {
+    const long long n = a.nlink * 9;
+    const C *f = static_cast<const C *>(a.F);
+    for (long long k = (long long)blockIdx.x * kMdBlock + threadIdx.x; k < n; k += (long long)gridDim.x * kMdBlock) {
         const C fv = f[k];
-        double2 hv = h[k];
+        double2 hv = a.H[k];
         // H - eps i F:  i (fr + i fi) = -fi + i fr
-        hv.x = fma(a.eps, (double)fv.y, hv.x);
-        hv.y = fma(-a.eps, (double)fv.x, hv.y);
-        h[k] = hv;
+        hv.x = fma(a.eps, widen(fv.y), hv.x);
+        hv.y = fma(-a.eps, widen(fv.x), hv.y);
+        a.H[k] = hv;
     }
 }
 
@@ -116,8 +117,16 @@ __global__ void k_convert(long long n, const S *__restrict__ src, D *__restrict_
     for (long long k = (long long)blockIdx.x * blockDim.x + threadIdx.x; k < n; k += (long long)gridDim.x * blockDim.x) {
         const S v = src[k];
         D w;
-        w.x = v.x;
-        w.y = v.y;
+        if constexpr (sizeof(v.x) == 8 && sizeof(w.x) == 4) {
+            w.x = f64_to_f32_rn(v.x);
+            w.y = f64_to_f32_rn(v.y);
+        } else if constexpr (sizeof(v.x) == 4 && sizeof(w.x) == 8) {
+            w.x = f32_to_f64(v.x);
+            w.y = f32_to_f64(v.y);
+        } else {
+            w.x = v.x;
+            w.y = v.y;
+        }
         dst[k] = w;
     }
 }

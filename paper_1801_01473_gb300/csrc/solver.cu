@@ -472,23 +472,24 @@ __device__ __forceinline__ double warp_sum_strided(const double *a, int n)
     return warp_sum(s);
 }
 
-constexpr int kScalBlock = 256;
-
-// Fixed-order sum of n partials by a whole block of kScalBlock threads (each thread a strided
-// slice, then a fixed tree), returned to every thread.  Many loads in flight: a one-warp sum of
-// the 8192 partials of a 32^4 lattice is latency-bound at tens of microseconds.
+// Fixed-order sum of n partials by a whole block of NT threads (each thread a strided slice with
+// eight independent accumulators, then a fixed tree), returned to every thread.  Many loads in
+// flight: a one-warp sum of the 16384 partials of a 32^4 lattice is latency-bound at tens of
+// microseconds.  NT = 256 by default (STG_SCALAR_BLOCK=1024 selects 1024-thread blocks, which
+// wait longer for a free SM behind the previous kernel).
+template <int kScalBlock>
 __device__ __forceinline__ double block_sum_strided(const double *a, int n, double *sh)
 {
-    double s0 = 0.0, s1 = 0.0, s2 = 0.0, s3 = 0.0;
+    double s[8] = {0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0, 0.0};
     int k = threadIdx.x;
-    for (; k + 3 * kScalBlock < n; k += 4 * kScalBlock) {
-        s0 += a[k];
-        s1 += a[k + kScalBlock];
-        s2 += a[k + 2 * kScalBlock];
-        s3 += a[k + 3 * kScalBlock];
+    for (; k + 7 * kScalBlock < n; k += 8 * kScalBlock) {
+#pragma unroll
+        for (int u = 0; u < 8; ++u) s[u] += a[k + u * kScalBlock];
     }
-    for (; k < n; k += kScalBlock) s0 += a[k];
-    double t = block_sum((s0 + s1) + (s2 + s3), sh);
+#pragma unroll
+    for (int u = 0; u < 7; ++u)
+        if (k + u * kScalBlock < n) s[u] += a[k + u * kScalBlock];
+    double t = block_sum(((s[0] + s[1]) + (s[2] + s[3])) + ((s[4] + s[5]) + (s[6] + s[7])), sh);
     if (threadIdx.x == 0) sh[32] = t;
     __syncthreads();
     t = sh[32];
@@ -531,6 +532,7 @@ __global__ void k_p1_init_scal(SysScal *sc, const SysVecs *sv, int *done, double
     }
 }
 
+template <int kScalBlock>
 __global__ void __launch_bounds__(kScalBlock) k_alpha(SysScal *sc, const SysVecs *sv, const int *done)
 {
     pdl_enter();
@@ -541,7 +543,7 @@ __global__ void __launch_bounds__(kScalBlock) k_alpha(SysScal *sc, const SysVecs
     }
     const SysVecs &V = sv[blockIdx.x];
     __shared__ double sh[33];
-    const double pq = block_sum_strided(V.part_d, V.nblk_d, sh);
+    const double pq = block_sum_strided<kScalBlock>(V.part_d, V.nblk_d, sh);
     if (threadIdx.x >= 32) return;  // the per-shift recurrences run in warp 0
     const double alpha = S.rr / pq;
     for (int i = threadIdx.x; i < S.nshift; i += 32) {
@@ -558,6 +560,7 @@ __global__ void __launch_bounds__(kScalBlock) k_alpha(SysScal *sc, const SysVecs
     }
 }
 
+template <int kScalBlock>
 __global__ void __launch_bounds__(kScalBlock) k_beta(SysScal *sc, const SysVecs *sv, int *done, int *need_rel,
                                                       double *log, int log_rows)
 {
@@ -566,7 +569,7 @@ __global__ void __launch_bounds__(kScalBlock) k_beta(SysScal *sc, const SysVecs 
     if (!S.running) return;
     const SysVecs &V = sv[blockIdx.x];
     __shared__ double sh[33];
-    const double rr_new = block_sum_strided(V.part_v, V.npart_v, sh);
+    const double rr_new = block_sum_strided<kScalBlock>(V.part_v, V.npart_v, sh);
     if (threadIdx.x >= 32) return;  // the per-shift recurrences run in warp 0
     const double beta = rr_new / S.rr;
     const int ns = S.nshift;
@@ -1162,6 +1165,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     const dim3 g_s2 = wave((const void *)k_update_shifts<R, R>, wl2.total);
     cudaGetLastError();
 
+    const bool scal_wide = getenv("STG_SCALAR_BLOCK") && atoi(getenv("STG_SCALAR_BLOCK")) == 1024;
     auto iterate = [&](int kind, const DPlan &pl, SysScal *dS, SysVecs *dV, int *dn, int *nr, int n, dim3 /*vg*/,
                        double *log, int log_rows) -> cudaError_t {
         cudaError_t e;
@@ -1171,16 +1175,16 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
             if ((e = launch_dslash(kind, a, 0, ws)) != cudaSuccess) return e;
         for (const DArgs &a : pl.eo)
             if ((e = launch_dslash(kind, a, 1, ws)) != cudaSuccess) return e;
-        if ((e = launch_pdl(k_alpha, dim3(n), dim3(kScalBlock), ws, dS, (const SysVecs *)dV, (const int *)dn)) !=
-            cudaSuccess)
-            return e;
+        e = scal_wide ? launch_pdl(k_alpha<1024>, dim3(n), dim3(1024), ws, dS, (const SysVecs *)dV, (const int *)dn)
+                      : launch_pdl(k_alpha<256>, dim3(n), dim3(256), ws, dS, (const SysVecs *)dV, (const int *)dn);
+        if (e != cudaSuccess) return e;
         if ((e = launch_pdl(k_update_r<R>, ph1 ? g_r1 : g_r2, dim3(kVecBlock), ws, (const SysScal *)dS,
                             (const SysVecs *)dV, wl)) !=
             cudaSuccess)
             return e;
-        if ((e = launch_pdl(k_beta, dim3(n), dim3(kScalBlock), ws, dS, (const SysVecs *)dV, dn, nr, log, log_rows)) !=
-            cudaSuccess)
-            return e;
+        e = scal_wide ? launch_pdl(k_beta<1024>, dim3(n), dim3(1024), ws, dS, (const SysVecs *)dV, dn, nr, log, log_rows)
+                      : launch_pdl(k_beta<256>, dim3(n), dim3(256), ws, dS, (const SysVecs *)dV, dn, nr, log, log_rows);
+        if (e != cudaSuccess) return e;
         if (ph1 && hist_w > 0)  // deferred multi-shift update: the base direction only
             e = launch_pdl(k_update_pbase<R>, g_pb, dim3(kVecBlock), ws, (const SysScal *)dS, (const SysVecs *)dV, wl);
         else if (ph1)  // multi-shift phase: solutions in H

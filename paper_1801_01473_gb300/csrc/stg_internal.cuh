@@ -74,6 +74,36 @@ __device__ __forceinline__ void reconstruct_row3(cx<R> U[3][3])
     U[2][2] = cx<R>{a.re - b.re, -(a.im - b.im)};
 }
 
+// ------------------------------------------------------------------ FP64 <-> FP32 on the integer pipes
+// GB300 executes FP64 <-> FP32 conversions on its narrow FP64 unit (~2 per clock per SM), which
+// makes plain conversion loops FP64-bound at a fraction of HBM bandwidth.  For normal numbers both
+// directions are bit manipulations of the IEEE 754 binary64 / binary32 formats (sign, biased
+// exponent 1023 / 127, 52 / 23 fraction bits); these do them on the integer pipes, rounding to
+// nearest even, and leave zeros, subnormals, infinities and NaNs (and results in those ranges) to
+// the hardware conversion.  Results are bit-identical to __double2float_rn and (double)f.
+__device__ __forceinline__ float f64_to_f32_rn(double d)
+{
+    const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+    const unsigned top = (unsigned)(b >> 32);
+    const int e = (int)((top >> 20) & 0x7ffu) - 896;  // binary32 biased exponent
+    if (e <= 0 || e >= 255) return __double2float_rn(d);
+    const unsigned long long m = b & 0xfffffffffffffull;
+    unsigned r = ((unsigned)e << 23) | (unsigned)(m >> 29);
+    const unsigned rem = (unsigned)(m & 0x1fffffffu);  // the 29 dropped fraction bits
+    r += (rem > 0x10000000u || (rem == 0x10000000u && (r & 1u))) ? 1u : 0u;  // carries into the exponent
+    return __uint_as_float(r | (top & 0x80000000u));
+}
+
+__device__ __forceinline__ double f32_to_f64(float f)
+{
+    const unsigned u = __float_as_uint(f);
+    const unsigned e = (u >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)f;
+    const unsigned long long b = ((unsigned long long)(u & 0x80000000u) << 32) |
+                                 ((unsigned long long)(e + 896u) << 52) | ((unsigned long long)(u & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)b);
+}
+
 // ------------------------------------------------------------------ double-single numbers
 // A value hi + lo held in two floats with |lo| <= ulp(hi)/2: a 48-bit significand (relative
 // rounding ~2^-47) computed on the FP32 pipes, which GB300 runs ~64x faster than FP64.
@@ -87,10 +117,28 @@ struct dsf {
     __device__ __forceinline__ constexpr dsf(float h, float l) : hi(h), lo(l) {}
     __device__ __forceinline__ dsf(int i) : hi((float)i), lo(0.f) {}
     __device__ __forceinline__ explicit dsf(float f) : hi(f), lo(0.f) {}
+    // hi = RN(d), lo = RN(d - hi): d - hi is the exact integer remainder of the 53-bit significand
+    // after rounding it to 24 bits, scaled by the last place of d (integer pipes; the hardware
+    // conversions for exponents outside the range where both parts are normal floats)
     __device__ __forceinline__ explicit dsf(double d)
     {
-        hi = __double2float_rn(d);
-        lo = __double2float_rn(d - (double)hi);
+        const unsigned long long b = (unsigned long long)__double_as_longlong(d);
+        const unsigned top = (unsigned)(b >> 32);
+        const int e = (int)((top >> 20) & 0x7ffu) - 896;
+        if (e < 53 || e >= 254) {
+            hi = __double2float_rn(d);
+            lo = __double2float_rn(d - (double)hi);
+            return;
+        }
+        const long long sig = (long long)((b & 0xfffffffffffffull) | 0x10000000000000ull);  // 53 bits
+        const unsigned rem = (unsigned)(sig & 0x1fffffff);
+        long long m24 = sig >> 29;
+        m24 += (rem > 0x10000000u || (rem == 0x10000000u && (m24 & 1))) ? 1 : 0;
+        const unsigned sign = top & 0x80000000u;
+        hi = __uint_as_float(((unsigned)(e << 23) + (unsigned)(m24 - (1ll << 23))) | sign);
+        const int low = (int)(sig - (m24 << 29));  // |low| <= 2^28
+        const float scale = __uint_as_float((unsigned)(e - 52) << 23);  // 2^(exponent of d's last place)
+        lo = __fmul_rn(__int2float_rn(sign ? -low : low), scale);
     }
     __device__ __forceinline__ explicit operator double() const { return (double)hi + (double)lo; }
     __device__ __forceinline__ explicit operator float() const { return __fadd_rn(hi, lo); }
@@ -411,9 +459,9 @@ struct LinkF32R18 {
         float4 *p = static_cast<float4 *>(blk);
         float2 *q = reinterpret_cast<float2 *>(p + 4 * (size_t)Vh);
         for (int k = 0; k < 4; ++k)
-            p[(size_t)k * Vh + h] = make_float4((float)m[2 * k].x, (float)m[2 * k].y, (float)m[2 * k + 1].x,
-                                                (float)m[2 * k + 1].y);
-        q[h] = make_float2((float)m[8].x, (float)m[8].y);
+            p[(size_t)k * Vh + h] = make_float4(f64_to_f32_rn(m[2 * k].x), f64_to_f32_rn(m[2 * k].y),
+                                                f64_to_f32_rn(m[2 * k + 1].x), f64_to_f32_rn(m[2 * k + 1].y));
+        q[h] = make_float2(f64_to_f32_rn(m[8].x), f64_to_f32_rn(m[8].y));
     }
 };
 
@@ -435,8 +483,8 @@ struct LinkF32R12 {
     {
         float4 *p = static_cast<float4 *>(blk);
         for (int k = 0; k < 3; ++k)
-            p[(size_t)k * Vh + h] = make_float4((float)m[2 * k].x, (float)m[2 * k].y, (float)m[2 * k + 1].x,
-                                                (float)m[2 * k + 1].y);
+            p[(size_t)k * Vh + h] = make_float4(f64_to_f32_rn(m[2 * k].x), f64_to_f32_rn(m[2 * k].y),
+                                                f64_to_f32_rn(m[2 * k + 1].x), f64_to_f32_rn(m[2 * k + 1].y));
     }
 };
 

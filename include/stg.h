@@ -110,6 +110,15 @@ stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, 
  * accepts such a gauge; the solvers need the inner gauge to carry the same phases. */
 stg_status stg_gauge_create_u1(const stg_lattice *lat, const void *links_c128_dev, const double *theta_dev,
                                stg_prec prec, stg_recon recon, void *stream, stg_gauge **out);
+/* Replaces the links of an existing gauge (same lattice, precision, compression) with new ones,
+ * without allocating: the MD evolution changes the links every step (Sec. 3), and a production
+ * loop keeps one gauge per precision and refreshes it.  theta_dev must be given (device, FP64,
+ * [4][V]) exactly when the gauge was created with stg_gauge_create_u1, NULL otherwise.  The
+ * double-single and FP32 companions that solves and forces created for an F64 gauge are refreshed
+ * too.  Stream-ordered: work already queued on `stream` sees the old links, later work the new;
+ * the gauge may not be in use on another stream meanwhile.  STG_ERR_ARG on null, misaligned or
+ * mismatched arguments. */
+stg_status stg_gauge_update(stg_gauge *g, const void *links_c128_dev, const double *theta_dev, void *stream);
 void stg_gauge_destroy(stg_gauge *g);
 /* Bytes of the internal link copy (4 V links). */
 size_t stg_gauge_bytes(const stg_gauge *g);
@@ -274,6 +283,13 @@ stg_status stg_mscg_solve_batched(int32_t ninst, const stg_instance *inst, const
  * out_c128_dev: canonical complex128 [4][V][3][3] (device).  g_f64 must be an F64 gauge. */
 stg_status stg_fermion_force(const stg_gauge *g_f64, int32_t nshift, const double *residues,
                              const void *const *x_c128_dev, void *out_c128_dev, int32_t kind, void *stream);
+/* stg_fermion_force at a chosen precision.  prec = STG_F64: exactly stg_fermion_force (out
+ * complex128).  prec = STG_F32 (single-precision MD forces, Sec. 5.3): x_i rounded to FP32, y_i from
+ * the FP32 12-real companion of the links (created on first use and kept, like the double-single
+ * one), W and the output in FP32 arithmetic; out_dev is canonical complex64 [4][V][3][3].  Relative
+ * accuracy ~1e-6 against the F64 force.  STG_ERR_ARG for any other prec. */
+stg_status stg_fermion_force_prec(const stg_gauge *g_f64, stg_prec prec, int32_t nshift, const double *residues,
+                                  const void *const *x_c128_dev, void *out_dev, int32_t kind, void *stream);
 
 /* ---- stout smearing ----------------------------------------------------------------------------- */
 

@@ -100,6 +100,16 @@ class Gauge:
     def handle(self):
         return self._h
 
+    def update(self, links: torch.Tensor, theta: torch.Tensor | None = None, stream=None) -> "Gauge":
+        """Replace the links (and, for a gauge created with theta, the phases) in place, without
+        allocating (stg_gauge_update)."""
+        links = _dev(links).reshape(4, self.lattice.V, 3, 3)
+        th = _dev(theta, torch.float64).reshape(4, self.lattice.V) if theta is not None else None
+        check(lib().stg_gauge_update(self._h, _ptr(links), _ptr(th) if th is not None else None, _stream(stream)),
+              "stg_gauge_update")
+        torch.cuda.current_stream().synchronize() if stream is None else stream.synchronize()
+        return self
+
     def new_field(self, n: int | None = None) -> torch.Tensor:
         """Uninitialised internal-layout field(s) at this gauge's vector precision."""
         dt, per = _FIELD[self.vec_prec]
@@ -332,16 +342,20 @@ def mscg_batched(instances, shifts, mass: float, tol: float = 1e-10, max_iter: i
 
 # ------------------------------------------------------------------ fermion force
 
-def fermion_force(g_f64: Gauge, residues, x: torch.Tensor, kind: int = 0, stream=None) -> torch.Tensor:
-    """Per-link force [4, V, 3, 3] complex128 from solutions x [nshift, Vh, 3]:
-    kind 0 -> TA(U W) (Lie-algebra force), kind 1 -> W^dag (gradient wrt link entries)."""
+def fermion_force(g_f64: Gauge, residues, x: torch.Tensor, kind: int = 0, prec: str = "f64",
+                  stream=None) -> torch.Tensor:
+    """Per-link force [4, V, 3, 3] from solutions x [nshift, Vh, 3]:
+    kind 0 -> TA(U W) (Lie-algebra force), kind 1 -> W^dag (gradient wrt link entries).
+    prec "f64": complex128 (double-single operator, FP64-class); "f32": complex64, FP32 operator
+    and gather (single-precision MD forces)."""
     ns = len(residues)
     xd = _dev(x).reshape(ns, g_f64.lattice.Vh, 3)
     res = (ctypes.c_double * ns)(*[float(r) for r in residues])
     xp = (ctypes.c_void_p * ns)(*[xd[i].data_ptr() for i in range(ns)])
-    out = torch.empty((4, g_f64.lattice.V, 3, 3), dtype=torch.complex128, device="cuda")
-    check(lib().stg_fermion_force(g_f64.handle, ns, res, ctypes.cast(xp, ctypes.POINTER(ctypes.c_void_p)), _ptr(out),
-                                  int(kind), _stream(stream)), "stg_fermion_force")
+    dt = torch.complex128 if prec == "f64" else torch.complex64
+    out = torch.empty((4, g_f64.lattice.V, 3, 3), dtype=dt, device="cuda")
+    check(lib().stg_fermion_force_prec(g_f64.handle, PREC[prec], ns, res, ctypes.cast(xp, ctypes.POINTER(ctypes.c_void_p)),
+                                       _ptr(out), int(kind), _stream(stream)), "stg_fermion_force_prec")
     return out
 
 

@@ -198,6 +198,96 @@ __global__ void __launch_bounds__(kForceBlock) k_force_ds(const __grid_constant_
     }
 }
 
+struct ForceArgsF32 {
+    Geom g;
+    const void *links;          // FP32 12-real companion links (possibly with U(1) phases)
+    const void *x[kMaxShifts];  // even FP32 fields
+    const void *y[kMaxShifts];  // odd FP32 fields D_oe x_i
+    float res[kMaxShifts];
+    int nshift;
+    int kind;
+    float2 *out;  // canonical complex64 [4][V][3][3]
+};
+
+// The gather of k_force_ds in FP32 arithmetic on FP32 fields (single-precision MD forces)
+template <typename LinkT>
+__global__ void __launch_bounds__(kForceBlock) k_force_f32(const __grid_constant__ ForceArgsF32 a)
+{
+    const int par = blockIdx.y;
+    const int h = blockIdx.x * kForceBlock + threadIdx.x;
+    const int Vh = a.g.Vh;
+    if (h >= Vh) return;
+    const Site s = site_of(a.g, par, h);
+    const long long V = 2LL * Vh;
+    for (int mu = 0; mu < 4; ++mu) {
+        const Hop hp = hop_of(a.g, s, mu);
+        cx<float> W[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) W[r][c] = cx<float>{0.f, 0.f};
+        for (int i = 0; i < a.nshift; ++i) {
+            cx<float> f[3], g[3];
+            if (par == 0) {
+                Field<float>::load(a.y[i], Vh, hp.hf, f);
+                Field<float>::load(a.x[i], Vh, h, g);
+            } else {
+                Field<float>::load(a.x[i], Vh, hp.hf, f);
+                Field<float>::load(a.y[i], Vh, h, g);
+            }
+            const float ri = a.res[i];
+#pragma unroll
+            for (int c = 0; c < 3; ++c) f[c] = cx<float>{ri * f[c].re, ri * f[c].im};
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) cmac_conj(W[r][c], g[c], f[r]);  // W_rc += f_r conj(g_c)
+        }
+        const void *blk = link_block<LinkT>(a.links, Vh, mu, par);
+        cx<float> ph = LinkTraits<LinkT>::phase(blk, Vh, h);
+        if ((par == 0 ? hp.sf : -hp.sf) < 0.f) ph = cx<float>{-ph.re, -ph.im};
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) W[r][c] = cmul(ph, W[r][c]);
+        float2 *o = a.out + ((long long)mu * V + s.i) * 9;
+        if (a.kind == 1) {
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) o[r * 3 + c] = make_float2(W[c][r].re, -W[c][r].im);
+            continue;
+        }
+        cx<float> U[3][3];
+        LinkTraits<LinkT>::Base::load(blk, Vh, h, U);
+        cx<float> Z[3][3];
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                cx<float> z = cx<float>{0.f, 0.f};
+#pragma unroll
+                for (int k = 0; k < 3; ++k) cmac(z, U[r][k], W[k][c]);
+                Z[r][c] = z;
+            }
+        const float im_tr = (Z[0][0].im + Z[1][1].im + Z[2][2].im) / 3.f;
+#pragma unroll
+        for (int r = 0; r < 3; ++r)
+#pragma unroll
+            for (int c = 0; c < 3; ++c) {
+                float re = 0.5f * (Z[r][c].re - Z[c][r].re);
+                float im = 0.5f * (Z[r][c].im + Z[c][r].im);
+                if (r == c) im -= im_tr;
+                o[r * 3 + c] = make_float2(re, im);
+            }
+    }
+}
+
+template <typename R>
+__device__ __forceinline__ R from_f64(double d) { return (R)d; }
+template <>
+__device__ __forceinline__ float from_f64<float>(double d) { return f64_to_f32_rn(d); }
+
 template <typename R>
 __global__ void k_pack_many(int Vh, const double2 *const *__restrict__ canon, void *const *__restrict__ out)
 {
@@ -207,7 +297,7 @@ __global__ void k_pack_many(int Vh, const double2 *const *__restrict__ canon, vo
     cx<R> v[3];
     for (int c = 0; c < 3; ++c) {
         double2 d = src[(size_t)h * 3 + c];
-        v[c] = cx<R>{(R)d.x, (R)d.y};
+        v[c] = cx<R>{from_f64<R>(d.x), from_f64<R>(d.y)};
     }
     Field<R>::store(out[blockIdx.y], Vh, h, v);
 }
@@ -233,6 +323,90 @@ __global__ void k_ds_to_f64_scaled(int Vh, const void *y0, size_t stride, const 
 }  // namespace stg
 
 using namespace stg;
+
+// single precision: y_i = D_oe x_i with the FP32 12-real companion, the gather in FP32, complex64 out
+static stg_status force_f32(const stg_gauge *g, int32_t nshift, const double *residues, const void *const *x_c128_dev,
+                            void *out_c64_dev, int32_t kind, cudaStream_t st)
+{
+    const int Vh = g->g.Vh;
+    const size_t fb = (size_t)Vh * 24;
+    const stg_gauge *g32 = nullptr;
+    {
+        stg_status s = f32_companion(g, st, &g32);
+        if (s != STG_OK) return s;
+    }
+    char *ws = nullptr;
+    const size_t ptr_bytes = 2 * kMaxShifts * sizeof(void *);
+    STG_CUDA_TRY(cudaMallocAsync((void **)&ws, 2 * nshift * fb + ptr_bytes, st));
+    struct Free {
+        void *p;
+        cudaStream_t s;
+        ~Free() { cudaFreeAsync(p, s); }
+    } fr{ws, st};
+    std::vector<const void *> ptrs(2 * kMaxShifts, nullptr);
+    ForceArgsF32 b;
+    memset(&b, 0, sizeof(b));
+    b.g = g->g;
+    b.links = g32->links;
+    b.nshift = nshift;
+    b.kind = kind;
+    b.out = static_cast<float2 *>(out_c64_dev);
+    for (int i = 0; i < nshift; ++i) {
+        b.x[i] = ws + (size_t)i * fb;
+        b.y[i] = ws + (size_t)(nshift + i) * fb;
+        b.res[i] = (float)residues[i];
+        ptrs[i] = x_c128_dev[i];
+        ptrs[kMaxShifts + i] = b.x[i];
+    }
+    void **d_ptrs = reinterpret_cast<void **>(ws + 2 * nshift * fb);
+    STG_CUDA_TRY(cudaMemcpyAsync(d_ptrs, ptrs.data(), ptr_bytes, cudaMemcpyHostToDevice, st));
+    k_pack_many<float><<<dim3((Vh + 255) / 256, nshift), 256, 0, st>>>(
+        Vh, reinterpret_cast<const double2 *const *>(d_ptrs), d_ptrs + kMaxShifts);
+    STG_CUDA_TRY(cudaGetLastError());
+    for (int base = 0; base < nshift;) {
+        DArgs d;
+        memset(&d, 0, sizeof(d));
+        d.out_par = 1;
+        int ng = 0;
+        while (ng < kMaxGroups && base < nshift) {
+            DGroup &G = d.grp[ng++];
+            G.g = g32->g;
+            G.links = g32->links;
+            G.nrhs = (nshift - base) < kMaxRhs ? (nshift - base) : kMaxRhs;
+            for (int j = 0; j < G.nrhs; ++j) {
+                G.in[j] = b.x[base + j];
+                G.out[j] = const_cast<void *>(b.y[base + j]);
+            }
+            base += G.nrhs;
+        }
+        d.ngroups = ng;
+        STG_CUDA_TRY(launch_dslash(g32->kind, d, 0, st));
+    }
+    const dim3 grid((Vh + kForceBlock - 1) / kForceBlock, 2);
+    if (kind_has_u1(g32->kind))
+        k_force_f32<LinkU1<LinkF32R12, float>><<<grid, kForceBlock, 0, st>>>(b);
+    else
+        k_force_f32<LinkF32R12><<<grid, kForceBlock, 0, st>>>(b);
+    STG_CUDA_TRY(cudaGetLastError());
+    return STG_OK;
+}
+
+extern "C" stg_status stg_fermion_force_prec(const stg_gauge *g, stg_prec prec, int32_t nshift, const double *residues,
+                                             const void *const *x_c128_dev, void *out_dev, int32_t kind, void *stream)
+{
+    if (prec == STG_F64) return stg_fermion_force(g, nshift, residues, x_c128_dev, out_dev, kind, stream);
+    if (prec != STG_F32) return set_error(STG_ERR_ARG, "stg_fermion_force_prec: prec must be F64 or F32");
+    if (!g || !residues || !x_c128_dev || !out_dev) return set_error(STG_ERR_ARG, "stg_fermion_force_prec: null pointer");
+    if (!kind_is_f64(g->kind)) return set_error(STG_ERR_ARG, "stg_fermion_force_prec: needs an F64 gauge");
+    if (nshift < 1 || nshift > kMaxShifts) return set_error(STG_ERR_ARG, "stg_fermion_force_prec: nshift must be in 1..32");
+    if (kind != 0 && kind != 1) return set_error(STG_ERR_ARG, "stg_fermion_force_prec: kind must be 0 or 1");
+    for (int i = 0; i < nshift; ++i)
+        if (!x_c128_dev[i] || (reinterpret_cast<uintptr_t>(x_c128_dev[i]) & 15))
+            return set_error(STG_ERR_ARG, "stg_fermion_force_prec: x must be non-null and 16-byte aligned");
+    if (reinterpret_cast<uintptr_t>(out_dev) & 15)
+        return set_error(STG_ERR_ARG, "stg_fermion_force_prec: out must be 16-byte aligned");
+    return force_f32(g, nshift, residues, x_c128_dev, out_dev, kind, (cudaStream_t)stream);
+}
 
 extern "C" stg_status stg_fermion_force(const stg_gauge *g, int32_t nshift, const double *residues,
                                         const void *const *x_c128_dev, void *out_c128_dev, int32_t kind, void *stream)

@@ -341,6 +341,42 @@ __global__ void k_links_to_ds(Geom g, const void *__restrict__ src, void *__rest
     copy_theta<SrcT, DstT>(sblk, dblk, Vh, h);
 }
 
+// (re)fill the companions of an F64 gauge from its links
+static cudaError_t fill_ds_companion(const stg_gauge *g64, stg_gauge *g, cudaStream_t st)
+{
+    const long long n = 8LL * g->g.Vh;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    switch (g64->kind) {
+    case kF64R18: k_links_to_ds<LinkF64R18, LinkDSR18><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
+    case kF64R12: k_links_to_ds<LinkF64R12, LinkDSR12><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
+    case kF64R18 | kU1:
+        k_links_to_ds<LinkU1<LinkF64R18, double2>, LinkU1<LinkDSR18, double2>><<<nb, 256, 0, st>>>(g->g, g64->links, g->links);
+        break;
+    default:
+        k_links_to_ds<LinkU1<LinkF64R12, double2>, LinkU1<LinkDSR12, double2>><<<nb, 256, 0, st>>>(g->g, g64->links, g->links);
+        break;
+    }
+    return cudaGetLastError();
+}
+
+static cudaError_t fill_f32_companion(const stg_gauge *g64, stg_gauge *g, cudaStream_t st)
+{
+    const long long n = 8LL * g->g.Vh;
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    using F32U = LinkU1<LinkF32R12, float>;
+    switch (g64->kind) {
+    case kF64R18: k_links_to_f32r12<LinkF64R18, LinkF32R12><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
+    case kF64R12: k_links_to_f32r12<LinkF64R12, LinkF32R12><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
+    case kF64R18 | kU1:
+        k_links_to_f32r12<LinkU1<LinkF64R18, double2>, F32U><<<nb, 256, 0, st>>>(g->g, g64->links, g->links);
+        break;
+    default:
+        k_links_to_f32r12<LinkU1<LinkF64R12, double2>, F32U><<<nb, 256, 0, st>>>(g->g, g64->links, g->links);
+        break;
+    }
+    return cudaGetLastError();
+}
+
 static std::mutex g_companion_mu;
 
 stg_status ds_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge **out)
@@ -358,23 +394,7 @@ stg_status ds_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge *
         g->ds_copy = nullptr;
         cudaError_t e = cudaMalloc(&g->links, g->bytes);
         if (e == cudaSuccess) e = cudaMalloc(&g->scratch, g->scratch_count * sizeof(double));
-        if (e == cudaSuccess) {
-            long long n = 8LL * g->g.Vh;
-            const unsigned nb = (unsigned)((n + 255) / 256);
-            switch (g64->kind) {
-            case kF64R18: k_links_to_ds<LinkF64R18, LinkDSR18><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
-            case kF64R12: k_links_to_ds<LinkF64R12, LinkDSR12><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
-            case kF64R18 | kU1:
-                k_links_to_ds<LinkU1<LinkF64R18, double2>, LinkU1<LinkDSR18, double2>><<<nb, 256, 0, st>>>(g->g, g64->links,
-                                                                                                      g->links);
-                break;
-            default:
-                k_links_to_ds<LinkU1<LinkF64R12, double2>, LinkU1<LinkDSR12, double2>><<<nb, 256, 0, st>>>(g->g, g64->links,
-                                                                                                      g->links);
-                break;
-            }
-            e = cudaGetLastError();
-        }
+        if (e == cudaSuccess) e = fill_ds_companion(g64, g, st);
         if (e != cudaSuccess) {
             cudaFree(g->links);
             cudaFree(g->scratch);
@@ -404,22 +424,7 @@ stg_status f32_companion(const stg_gauge *g64, cudaStream_t st, const stg_gauge 
         g->ds_copy = nullptr;
         cudaError_t e = cudaMalloc(&g->links, g->bytes);
         if (e == cudaSuccess) e = cudaMalloc(&g->scratch, g->scratch_count * sizeof(double));
-        if (e == cudaSuccess) {
-            long long n = 8LL * g->g.Vh;
-            const unsigned nb = (unsigned)((n + 255) / 256);
-            using F32U = LinkU1<LinkF32R12, float>;
-            switch (g64->kind) {
-            case kF64R18: k_links_to_f32r12<LinkF64R18, LinkF32R12><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
-            case kF64R12: k_links_to_f32r12<LinkF64R12, LinkF32R12><<<nb, 256, 0, st>>>(g->g, g64->links, g->links); break;
-            case kF64R18 | kU1:
-                k_links_to_f32r12<LinkU1<LinkF64R18, double2>, F32U><<<nb, 256, 0, st>>>(g->g, g64->links, g->links);
-                break;
-            default:
-                k_links_to_f32r12<LinkU1<LinkF64R12, double2>, F32U><<<nb, 256, 0, st>>>(g->g, g64->links, g->links);
-                break;
-            }
-            e = cudaGetLastError();
-        }
+        if (e == cudaSuccess) e = fill_f32_companion(g64, g, st);
         if (e != cudaSuccess) {
             cudaFree(g->links);
             cudaFree(g->scratch);
@@ -604,6 +609,24 @@ stg_status stg_gauge_create(const stg_lattice *lat, const void *links_c128_dev, 
                             void *stream, stg_gauge **out)
 {
     return gauge_create(lat, links_c128_dev, nullptr, prec, recon, stream, out);
+}
+
+stg_status stg_gauge_update(stg_gauge *g, const void *links_c128_dev, const double *theta_dev, void *stream)
+{
+    if (!g || !links_c128_dev) return set_error(STG_ERR_ARG, "stg_gauge_update: null pointer");
+    if (!aligned16(links_c128_dev)) return set_error(STG_ERR_ARG, "stg_gauge_update: links not 16-byte aligned");
+    const bool u1 = kind_has_u1(g->kind);
+    if (u1 != (theta_dev != nullptr))
+        return set_error(STG_ERR_ARG, "stg_gauge_update: theta must be given exactly when the gauge carries phases");
+    if (theta_dev && (reinterpret_cast<uintptr_t>(theta_dev) & 7))
+        return set_error(STG_ERR_ARG, "stg_gauge_update: theta not 8-byte aligned");
+    cudaStream_t st = (cudaStream_t)stream;
+    STG_CUDA_TRY(u1 ? launch_pack_links_u1(g->kind, g->g, links_c128_dev, theta_dev, g->links, st)
+                    : launch_pack_links(g->kind, g->g, links_c128_dev, g->links, st));
+    std::lock_guard<std::mutex> lk(g_companion_mu);
+    if (g->ds_copy) STG_CUDA_TRY(fill_ds_companion(g, g->ds_copy, st));
+    if (g->f32_copy) STG_CUDA_TRY(fill_f32_companion(g, g->f32_copy, st));
+    return STG_OK;
 }
 
 stg_status stg_gauge_create_u1(const stg_lattice *lat, const void *links_c128_dev, const double *theta_dev, stg_prec prec,

@@ -65,9 +65,21 @@ class Action:
         return None, links
 
     def _gauges(self, uk):
-        g64 = Gauge(self.lattice, uk, "f64", 18, theta=self.theta)
-        gi = Gauge(self.lattice, uk, "f32", 12, theta=self.theta) if self.inner == "f32" else None
-        return g64, gi
+        """The action's F64 (and FP32 inner) gauges holding uk: created once, then refreshed in place
+        (no allocation per force evaluation)."""
+        cache = self.__dict__.setdefault("_gauge_cache", {})
+        key = (self.theta is None, self.inner)
+        if cache.get("key") != key:
+            cache.clear()
+            cache["key"] = key
+        if "g64" not in cache:
+            cache["g64"] = Gauge(self.lattice, uk, "f64", 18, theta=self.theta)
+            cache["gi"] = Gauge(self.lattice, uk, "f32", 12, theta=self.theta) if self.inner == "f32" else None
+        else:
+            cache["g64"].update(uk, self.theta)
+            if cache["gi"] is not None:
+                cache["gi"].update(uk, self.theta)
+        return cache["g64"], cache["gi"]
 
     def _solve_all(self, g64, gi, tol, md=False):
         """x_i for every pseudofermion (with its MD poles if md); pseudofermions sharing a pole set
@@ -129,14 +141,13 @@ class Action:
         xs = self._solve_all(g64, gi, self.md_tol if self.md_tol is not None else self.tol, md=True)
         xall = torch.cat(xs) if len(xs) > 1 else xs[0]
         rall = [float(r) for pf in self.pseudofermions for r in pf.force_poles()[1]]
+        fprec = "f32" if f32 else "f64"
         for c0 in range(0, len(rall), 32):
             x, r = xall[c0:c0 + 32], rall[c0:c0 + 32]
             if levels is None:
-                f = fermion_force(g64, r, x, kind=0)
+                f = fermion_force(g64, r, x, kind=0, prec=fprec)
             else:
-                gk = fermion_force(g64, r, x, kind=1)
-                if f32:
-                    gk = complex_convert(gk, torch.complex64)
+                gk = fermion_force(g64, r, x, kind=1, prec=fprec)
                 f = stout_force(self.lattice, u, levels, self.stout_rho, gk, kind=0)
             md_update_momenta_(self.lattice, eps, f, mom)
 

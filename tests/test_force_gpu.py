@@ -144,3 +144,30 @@ def test_double_single_gather_matches_fp64_gather(recon, kind, monkeypatch):
     monkeypatch.setenv("STG_FORCE_FP64", "1")
     f64 = p.fermion_force(g, res, x, kind=kind)
     assert float((ds - f64).abs().max()) <= 1e-13 * float(f64.abs().max())
+
+
+@pytest.mark.parametrize("dims", [(4, 4, 4, 4), (6, 4, 2, 8), (8, 8, 4, 6)])
+@pytest.mark.parametrize("kind", [0, 1])
+@pytest.mark.parametrize("phases", [False, True])
+def test_single_precision_force_matches_oracle(dims, kind, phases):
+    """prec="f32" (FP32 12-real links, FP32 fields and gather, complex64 out) against the oracle's
+    FP64 force on the same solutions: 5e-6 relative (FP32 rounding of links, fields and sums)."""
+    p = stg()
+    u = S.gauge_links(dims, "haar", 63)
+    b = S.gaussian_field(dims, 64)
+    shifts = [1e-3, 0.02, 0.3, 1.5]
+    res = [0.7, 0.4, 0.25, 0.1]
+    lat = p.Lattice(dims)
+    theta = np.random.default_rng(65).uniform(-np.pi, np.pi, (4, lat.V)) if phases else None
+    if phases:
+        sol = oracle.mscg(dims, oracle.u1_links(u, theta), 0.1, shifts, b, tol=1e-12)
+        ref = oracle.force_u1(dims, u, theta, res, sol["x"], kind=kind)
+    else:
+        sol = oracle.mscg(dims, u, 0.1, shifts, b, tol=1e-12)
+        ref = oracle.force(dims, u, res, sol["x"], kind=kind)
+    g = p.Gauge(lat, torch.from_numpy(u).cuda(), "f64", 18,
+                theta=torch.from_numpy(theta).cuda() if phases else None)
+    got = p.fermion_force(g, res, torch.from_numpy(sol["x"]).cuda(), kind=kind, prec="f32")
+    assert got.dtype == torch.complex64
+    got = got.cpu().numpy()
+    assert np.abs(got - ref).max() <= 5e-6 * np.abs(ref).max()

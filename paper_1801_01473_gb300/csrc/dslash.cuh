@@ -15,6 +15,8 @@
 // reduced values do not depend on the block size the autotuner picks.
 #pragma once
 
+#include <type_traits>
+
 #include "stg_internal.cuh"
 
 namespace stg {
@@ -47,6 +49,27 @@ struct DArgs {
     int out_par;  // parity of the output sites: 0 -> D_eo, 1 -> D_oe
 };
 
+// hi + lo += a * b for double-single a, b (see the kLazyDS path of k_dslash)
+__device__ __forceinline__ void lazy_mac(float &hi, float &lo, const dsf &a, const dsf &b)
+{
+    const float p = __fmul_rn(a.hi, b.hi);
+    float e = __fmaf_rn(a.hi, b.hi, -p);
+    e = __fmaf_rn(a.hi, b.lo, e);
+    e = __fmaf_rn(a.lo, b.hi, e);
+    const float t = __fadd_rn(hi, p);
+    const float bb = __fsub_rn(t, hi);
+    const float err = __fadd_rn(__fsub_rn(hi, __fsub_rn(t, bb)), __fsub_rn(p, bb));
+    hi = t;
+    lo = __fadd_rn(lo, __fadd_rn(err, e));
+}
+
+template <typename R>
+__device__ __forceinline__ void neg3(cx<R> v[3])
+{
+#pragma unroll
+    for (int c = 0; c < 3; ++c) v[c] = cx<R>{-v[c].re, -v[c].im};
+}
+
 template <typename LinkT, int NRHS, int MODE, int BS>
 __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
 {
@@ -75,7 +98,67 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
 #pragma unroll
         for (int c = 0; c < 3; ++c) acc[j][c] = cx<R>{R(0), R(0)};
 
-    if (live) {
+    // Double-single links without phases: every real output is a signed sum of 48 products of
+    // double-single numbers; each product is formed to ~2^-48 (FMA TwoProduct of the high parts plus
+    // the two cross terms) and added with TwoSum to a running FP32 head, all rounding errors
+    // collecting in an FP32 tail that is folded in once at the end (Ogita-Rump-Oishi style
+    // compensated dot product): ~12 FP32 operations per product instead of ~28 for double-single
+    // multiply-adds renormalised at every step.
+    constexpr bool kLazyDS = std::is_same<R, dsf>::value && !LinkTraits<LinkT>::kU1;
+    if constexpr (kLazyDS) {
+        if (live) {
+            float ahi[NRHS][3][2], alo[NRHS][3][2];
+#pragma unroll
+            for (int j = 0; j < NRHS; ++j)
+#pragma unroll
+                for (int r = 0; r < 3; ++r) ahi[j][r][0] = ahi[j][r][1] = alo[j][r][0] = alo[j][r][1] = 0.f;
+            const Site s = site_of(G.g, op, h);
+#pragma unroll
+            for (int mu = 0; mu < 4; ++mu) {
+                const Hop hp = hop_of(G.g, s, mu);
+                cx<R> U[3][3];
+                LinkT::load(link_block<LinkT>(G.links, Vh, mu, op), Vh, h, U);
+#pragma unroll
+                for (int j = 0; j < NRHS; ++j) {
+                    if (!act[j]) continue;
+                    cx<R> v[3];
+                    Field<R>::load(G.in[j], Vh, hp.hf, v);
+                    if (hp.sf < 0.f) neg3(v);
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {  // U[r][c] v[c]
+                            lazy_mac(ahi[j][r][0], alo[j][r][0], U[r][c].re, v[c].re);
+                            lazy_mac(ahi[j][r][0], alo[j][r][0], -U[r][c].im, v[c].im);
+                            lazy_mac(ahi[j][r][1], alo[j][r][1], U[r][c].re, v[c].im);
+                            lazy_mac(ahi[j][r][1], alo[j][r][1], U[r][c].im, v[c].re);
+                        }
+                }
+                LinkT::load(link_block<LinkT>(G.links, Vh, mu, 1 - op), Vh, hp.hb, U);
+#pragma unroll
+                for (int j = 0; j < NRHS; ++j) {
+                    if (!act[j]) continue;
+                    cx<R> v[3];
+                    Field<R>::load(G.in[j], Vh, hp.hb, v);
+                    if (hp.sb > 0.f) neg3(v);  // the backward hop enters with -u_mu(x - mu)
+#pragma unroll
+                    for (int r = 0; r < 3; ++r)
+#pragma unroll
+                        for (int c = 0; c < 3; ++c) {  // conj(U[c][r]) v[c]
+                            lazy_mac(ahi[j][r][0], alo[j][r][0], U[c][r].re, v[c].re);
+                            lazy_mac(ahi[j][r][0], alo[j][r][0], U[c][r].im, v[c].im);
+                            lazy_mac(ahi[j][r][1], alo[j][r][1], U[c][r].re, v[c].im);
+                            lazy_mac(ahi[j][r][1], alo[j][r][1], -U[c][r].im, v[c].re);
+                        }
+                }
+            }
+#pragma unroll
+            for (int j = 0; j < NRHS; ++j)
+#pragma unroll
+                for (int r = 0; r < 3; ++r)
+                    acc[j][r] = cx<R>{ds_two_sum(ahi[j][r][0], alo[j][r][0]), ds_two_sum(ahi[j][r][1], alo[j][r][1])};
+        }
+    } else if (live) {
         const Site s = site_of(G.g, op, h);
 #pragma unroll
         for (int mu = 0; mu < 4; ++mu) {

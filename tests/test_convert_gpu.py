@@ -58,8 +58,8 @@ def test_double_single_split_bitwise():
     ds = p.pack(lat, torch.from_numpy(canon).cuda(), "ds").cpu().numpy().reshape(3, lat.Vh, 4)
     for part, col in (("re", (0, 1)), ("im", (2, 3))):
         x = (canon.real if part == "re" else canon.imag).T  # [3, Vh]
-        hi = x.astype(np.float32)
         with np.errstate(over="ignore", invalid="ignore"):
+            hi = x.astype(np.float32)
             lo = (x - hi.astype(np.float64)).astype(np.float32)
         fin = np.isfinite(hi)
         np.testing.assert_array_equal(ds[..., col[0]][fin].view(np.uint32), hi[fin].view(np.uint32))

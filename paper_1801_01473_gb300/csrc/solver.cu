@@ -950,8 +950,11 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         if (prm->history >= 2) {
             hist_w = std::min(kHistMax, std::max(8, prm->history));
         } else {
+            // slots that fit the budget, less the one holding the current residual (at least the
+            // minimum window when even that does not fit)
             const size_t budget = (size_t)4 << 30;
-            hist_w = (int)std::min<size_t>(kHistMax, budget / std::max<size_t>(ring_field, 1) - 1);
+            const size_t fit = budget / std::max<size_t>(ring_field, 1);
+            hist_w = fit > 1 ? (int)std::min<size_t>(kHistMax, fit - 1) : 8;
         }
         hist_w = std::max(8, hist_w - hist_w % 8);
     }
@@ -1322,7 +1325,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     stamp("FP64 residuals of the multi-shift solutions done");
     std::vector<double> trr0(npair);
     STG_CUDA_TRY(cudaMemcpy(trr0.data(), d_true_rr, sizeof(double) * npair, cudaMemcpyDeviceToHost));
-    int rounds = 0, chunks_before = 0;
+    int rounds = 0;
     const long long rel_cap = 4LL * prm->max_iter + 64;
     for (long long round = 0; round < rel_cap; ++round) {
         bool all = true;
@@ -1351,7 +1354,6 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         snprintf(buf, sizeof buf, "phase 2 (refinement) done: %d reliable-update rounds", rounds);
         stamp(buf);
     }
-    (void)chunks_before;
 
     // ---------------- FP64 verification of double-single results
     if (kDS) {

@@ -230,6 +230,14 @@ def dslash_host(gauge: Gauge, out_parity: int, fields: torch.Tensor, out: torch.
     return out
 
 
+def dslash(gauge: Gauge, out_parity: int, psi: torch.Tensor) -> torch.Tensor:
+    """D_eo psi (out_parity 0: odd input, even output) or D_oe psi (out_parity 1: even input, odd
+    output) on canonical complex128 [Vh, 3] fields (host or device)."""
+    if out_parity not in (0, 1):
+        raise ValueError("dslash: out_parity must be 0 (D_eo) or 1 (D_oe)")
+    return dslash_eo(gauge, psi) if out_parity == 0 else dslash_oe(gauge, psi)
+
+
 def dslash_oe(gauge: Gauge, psi_even: torch.Tensor) -> torch.Tensor:
     """D_oe psi_even on canonical complex128 [Vh, 3] fields (host or device)."""
     return _canon_apply(gauge, psi_even, lambda x: dslash_oe_(gauge, torch.empty_like(x), x))

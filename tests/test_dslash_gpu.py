@@ -202,3 +202,14 @@ def test_dslash_host_pipeline(variant, out_par):
         for k in range(5):
             dev = fn(g, h32[k].to(torch.complex128).cuda()).cpu().to(torch.complex64)
             assert torch.equal(got32[k], dev), k
+
+
+def test_generic_dslash_dispatch():
+    """stg.dslash(gauge, out_parity, psi) is D_eo for parity 0 and D_oe for parity 1, bitwise."""
+    p = stg()
+    dims = (4, 4, 4, 6)
+    lat = p.Lattice(dims)
+    g = p.Gauge(lat, torch.from_numpy(links_for(dims)).cuda(), "f64", 18)
+    psi = torch.from_numpy(S.gaussian_field(dims, 205)).cuda()
+    assert torch.equal(p.dslash(g, 0, psi), p.dslash_eo(g, psi))
+    assert torch.equal(p.dslash(g, 1, psi), p.dslash_oe(g, psi))

@@ -141,6 +141,9 @@ stg_status stg_field_unpack(const stg_lattice *lat, stg_prec vec_prec, const voi
 stg_status stg_dslash_eo(const stg_gauge *g, void *out_even_dev, const void *in_odd_dev, void *stream);
 /* out_odd = D_oe in_even. */
 stg_status stg_dslash_oe(const stg_gauge *g, void *out_odd_dev, const void *in_even_dev, void *stream);
+/* out_parity 0: out = D_eo in (as stg_dslash_eo); 1: out = D_oe in (as stg_dslash_oe).
+ * STG_ERR_ARG for any other out_parity. */
+stg_status stg_dslash(const stg_gauge *g, int32_t out_parity, void *out_dev, const void *in_dev, void *stream);
 /* nrhs applications of one block sharing each link load: out_parity 0 -> D_eo, 1 -> D_oe;
  * field j at in_dev + j*stride_bytes (same for out).  1 <= nrhs <= 64; stride a multiple of
  * 16 bytes and >= stg_field_bytes. */

@@ -748,6 +748,12 @@ stg_status stg_dslash_oe(const stg_gauge *g, void *out_odd_dev, const void *in_e
     return stg_dslash_multi(g, 1, 1, out_odd_dev, in_even_dev, 0, stream);
 }
 
+stg_status stg_dslash(const stg_gauge *g, int32_t out_parity, void *out_dev, const void *in_dev, void *stream)
+{
+    if (out_parity != 0 && out_parity != 1) return set_error(STG_ERR_ARG, "stg_dslash: out_parity must be 0 or 1");
+    return stg_dslash_multi(g, out_parity, 1, out_dev, in_dev, 0, stream);
+}
+
 stg_status stg_normal_op(const stg_gauge *g, double mass, double shift, void *out_even_dev, const void *in_even_dev,
                          void *tmp_odd_dev, double *pq_dev, void *stream)
 {

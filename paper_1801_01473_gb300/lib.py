@@ -24,7 +24,7 @@ EXPORTS = [
     "stg_lattice_create", "stg_lattice_destroy", "stg_lattice_sites",
     "stg_gauge_create", "stg_gauge_create_u1", "stg_gauge_update", "stg_gauge_destroy", "stg_gauge_bytes",
     "stg_field_bytes", "stg_field_pack", "stg_field_unpack",
-    "stg_dslash_eo", "stg_dslash_oe", "stg_dslash_multi", "stg_dslash_host", "stg_normal_op", "stg_normal_op_noalloc",
+    "stg_dslash", "stg_dslash_eo", "stg_dslash_oe", "stg_dslash_multi", "stg_dslash_host", "stg_normal_op", "stg_normal_op_noalloc",
     "stg_mscg_solve", "stg_mscg_solve_batched", "stg_rational_apply", "stg_fermion_force", "stg_fermion_force_prec",
     "stg_stout_smear", "stg_stout_force", "stg_gauge_action", "stg_gauge_force",
     "stg_md_momenta", "stg_md_update_links", "stg_md_update_momenta", "stg_md_kinetic", "stg_complex_convert",
@@ -102,6 +102,7 @@ def lib() -> ctypes.CDLL:
     L.stg_gauge_action.argtypes = [P, D, P, P, P]
     L.stg_gauge_create_u1.argtypes = [P, P, P, ctypes.c_int, ctypes.c_int, P, ctypes.POINTER(P)]
     L.stg_gauge_update.argtypes = [P, P, P, P]
+    L.stg_dslash.argtypes = [P, I32, P, P, P]
     L.stg_fermion_force_prec.argtypes = [P, ctypes.c_int, I32, ctypes.POINTER(D), PP, P, I32, P]
     L.stg_gauge_force.argtypes = [P, ctypes.c_int, D, P, P, I32, P]
     L.stg_md_momenta.argtypes = [P, P, P, P]
@@ -116,7 +117,7 @@ def lib() -> ctypes.CDLL:
                                                  "stg_dslash_multi", "stg_dslash_host", "stg_normal_op", "stg_normal_op_noalloc", "stg_mscg_solve",
                                                  "stg_mscg_solve_batched", "stg_rational_apply", "stg_fermion_force",
                                                  "stg_stout_smear", "stg_stout_force", "stg_gauge_action",
-                                                 "stg_gauge_force", "stg_gauge_create_u1", "stg_gauge_update", "stg_fermion_force_prec", "stg_md_momenta", "stg_md_update_links",
+                                                 "stg_gauge_force", "stg_gauge_create_u1", "stg_gauge_update", "stg_fermion_force_prec", "stg_dslash", "stg_md_momenta", "stg_md_update_links",
                                                  "stg_md_update_momenta", "stg_md_kinetic", "stg_complex_convert"):
             f.restype = ctypes.c_int
     _lib = L

@@ -126,5 +126,7 @@ def test_gauge_and_md_arguments_rejected_before_launch(L):
     assert L.stg_complex_convert(10, 3, a, 1, b, None) == -1
     assert L.stg_md_kinetic(h, a, None, None) == -1
     assert L.stg_gauge_update(None, a, None, None) == -1
+    assert L.stg_dslash(None, 0, a, b, None) == -1
+    assert L.stg_dslash(None, 2, a, b, None) == -1 and b"out_parity" in L.stg_last_error()
     assert L.stg_fermion_force_prec(None, 3, 1, None, None, None, 0, None) == -1
     L.stg_lattice_destroy(h)

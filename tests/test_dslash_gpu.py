@@ -213,3 +213,12 @@ def test_generic_dslash_dispatch():
     psi = torch.from_numpy(S.gaussian_field(dims, 205)).cuda()
     assert torch.equal(p.dslash(g, 0, psi), p.dslash_eo(g, psi))
     assert torch.equal(p.dslash(g, 1, psi), p.dslash_oe(g, psi))
+    # the C entry stg_dslash on internal-layout fields
+    x = p.pack(lat, psi, "f64")
+    for par, fn in ((0, p.dslash_eo_), (1, p.dslash_oe_)):
+        want = fn(g, torch.empty_like(x), x)
+        got = torch.empty_like(x)
+        assert p.lib().stg_dslash(g.handle, par, got.data_ptr(), x.data_ptr(),
+                                  torch.cuda.current_stream().cuda_stream) == 0
+        torch.cuda.synchronize()
+        assert torch.equal(got, want)

@@ -100,3 +100,74 @@ def test_ragged_lattices(dims):
     shifts = np.array([0.0, 0.05, 0.5])
     res = oracle.mscg(dims, u, 0.1, shifts, b, tol=1e-11)
     assert np.all(res["true_resid"] <= 1e-11)
+
+
+# ---------------------------------------------------------------------------- the true residual
+# oracle.true_residual is the pass/fail gate of every mixed-precision GPU solve, so it is pinned
+# here against quantities fixed by the algebra alone: the relative residual |b - A_sigma x| / |b|
+# (Sec. 2, per shift) of x = 0, of a multiple of the exact solution, and of an arbitrary x against
+# the dense matrix.
+
+
+def _dense_solution(small, i):
+    a, b = small["a"], small["b"].reshape(-1)
+    return np.linalg.solve(a + small["shifts"][i] * np.eye(a.shape[0]), b)
+
+
+def test_true_residual_of_zero_guess_is_one(small):
+    """x = 0 leaves r = b, so the relative residual is exactly 1 for every shift."""
+    x0 = np.zeros_like(small["b"])
+    for s in small["shifts"]:
+        assert oracle.true_residual(small["dims"], small["u"], small["mass"], s, small["b"], x0) == 1.0
+
+
+@pytest.mark.parametrize("t", [0.5, 1.25, -1.0, 3.0])
+def test_true_residual_of_scaled_solution(small, t):
+    """x = t x* with A x* = b gives r = (1 - t) b: the residual is |1 - t| (a square, a missing
+    sqrt, a division by |b|^2 or a sign flip b + A x would each give another number)."""
+    for i in (0, 4, 7):
+        xs = _dense_solution(small, i).reshape(small["b"].shape)
+        got = oracle.true_residual(small["dims"], small["u"], small["mass"], small["shifts"][i], small["b"], t * xs)
+        assert abs(got - abs(1.0 - t)) <= 1e-12, (i, t, got)
+
+
+def test_true_residual_of_dense_solution_vanishes(small):
+    for i in range(len(small["shifts"])):
+        xs = _dense_solution(small, i).reshape(small["b"].shape)
+        got = oracle.true_residual(small["dims"], small["u"], small["mass"], small["shifts"][i], small["b"], xs)
+        assert got <= 1e-13, (i, got)
+
+
+def test_true_residual_of_perturbed_solution_matches_dense(small):
+    """Any x: the oracle's value equals |b - (A + sigma) x| / |b| from the dense 4^4 matrix."""
+    rng = np.random.default_rng(99)
+    a, b = small["a"], small["b"].reshape(-1)
+    n = a.shape[0]
+    for i, eps in ((0, 1e-6), (3, 1e-3), (7, 0.3)):
+        s = small["shifts"][i]
+        xs = _dense_solution(small, i)
+        x = xs + eps * np.linalg.norm(xs) / np.sqrt(n) * (rng.standard_normal(n) + 1j * rng.standard_normal(n))
+        want = np.linalg.norm(b - (a + s * np.eye(n)) @ x) / np.linalg.norm(b)
+        got = oracle.true_residual(small["dims"], small["u"], small["mass"], s, small["b"], x.reshape(small["b"].shape))
+        assert abs(got - want) <= 1e-12 * want + 1e-15, (i, got, want)
+
+
+def test_refinement_branch_finishes_capped_shifts(small):
+    """With the multi-shift phase capped at 150 iterations the five smallest shifts stop above tol;
+    the oracle then finishes each with plain CG from its x_i.  Every shift must end at or below
+    tol by the dense residual, and within kappa_i tol of the dense solution."""
+    dims, u, b, mass, tol = small["dims"], small["u"], small["b"], small["mass"], small["tol"]
+    res = oracle.mscg(dims, u, mass, small["shifts"], b, tol=tol, max_iter=150)
+    assert res["iters"] == 150 and res["refine_iters"] > 0
+    assert np.sum(res["shift_iters"] == 150) >= 3
+    a, bb = small["a"], b.reshape(-1)
+    n = a.shape[0]
+    ev = np.linalg.eigvalsh(a)
+    for i, s in enumerate(small["shifts"]):
+        x = res["x"][i].reshape(-1)
+        dense_r = np.linalg.norm(bb - (a + s * np.eye(n)) @ x) / np.linalg.norm(bb)
+        assert dense_r <= tol, (i, dense_r)
+        assert abs(res["true_resid"][i] - dense_r) <= 1e-13
+        xd = _dense_solution(small, i)
+        kappa = (ev.max() + s) / (ev.min() + s)
+        assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= kappa * tol, i

@@ -70,6 +70,63 @@ __device__ __forceinline__ void neg3(cx<R> v[3])
     for (int c = 0; c < 3; ++c) v[c] = cx<R>{-v[c].re, -v[c].im};
 }
 
+// Epilogue of the D kernels: scale (MODE 0) or fuse the shifted normal operator and its FP64
+// partial sums (MODE 1, 2), store, and write one partial per 64 output sites.  `sh` holds >= 32
+// doubles of shared memory; `act` is uniform over the block.
+template <typename R, int NRHS, int MODE, int BS>
+__device__ __forceinline__ void dslash_epilogue(const DGroup &G, const bool act[NRHS], bool live, int h,
+                                                const cx<R> acc[NRHS][3], double *sh)
+{
+    const int Vh = G.g.Vh;
+#pragma unroll
+    for (int j = 0; j < NRHS; ++j) {
+        if (!act[j]) continue;  // uniform over the block
+        ProdSum<R> part;
+        if (live) {
+            cx<R> o[3];
+            if (MODE == 0) {
+#pragma unroll
+                for (int c = 0; c < 3; ++c) o[c] = cx<R>{R(0.5) * acc[j][c].re, R(0.5) * acc[j][c].im};
+            } else {
+                cx<R> p[3];
+                Field<R>::load(G.epi_p[j], Vh, h, p);
+                const R cj = (R)G.coef[j];
+#pragma unroll
+                for (int c = 0; c < 3; ++c)
+                    o[c] = cx<R>{fma(cj, p[c].re, R(-0.5) * acc[j][c].re), fma(cj, p[c].im, R(-0.5) * acc[j][c].im)};
+                if (MODE == 1) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        part.add(p[c].re, o[c].re);
+                        part.add(p[c].im, o[c].im);
+                    }
+                } else {
+                    cx<R> b[3];
+                    Field<R>::load(G.epi_b[j], Vh, h, b);
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) {
+                        o[c] = cx<R>{b[c].re - o[c].re, b[c].im - o[c].im};
+                        part.add(o[c].re, o[c].re);
+                        part.add(o[c].im, o[c].im);
+                    }
+                }
+            }
+            Field<R>::store(G.out[j], Vh, h, o);
+        }
+        if (MODE != 0 && G.partial[j] != nullptr) {
+            // two warps per 64-site chunk: warp sums, then pairs of warps
+            const double pv = part.warp_total();
+            __syncthreads();
+            if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = pv;
+            __syncthreads();
+            constexpr int kChunks = BS / kPartialSites;
+            const int c = blockIdx.x * kChunks + threadIdx.x;
+            if (threadIdx.x < kChunks && c < dslash_partials(Vh))
+                G.partial[j][c] = sh[2 * threadIdx.x] + sh[2 * threadIdx.x + 1];
+        }
+    }
+}
+
 template <typename LinkT, int NRHS, int MODE, int BS>
 __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
 {
@@ -208,53 +265,7 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
     }
 
     __shared__ double sh[32];
-#pragma unroll
-    for (int j = 0; j < NRHS; ++j) {
-        if (!act[j]) continue;  // uniform over the block
-        ProdSum<R> part;
-        if (live) {
-            cx<R> o[3];
-            if (MODE == 0) {
-#pragma unroll
-                for (int c = 0; c < 3; ++c) o[c] = cx<R>{R(0.5) * acc[j][c].re, R(0.5) * acc[j][c].im};
-            } else {
-                cx<R> p[3];
-                Field<R>::load(G.epi_p[j], Vh, h, p);
-                const R cj = (R)G.coef[j];
-#pragma unroll
-                for (int c = 0; c < 3; ++c)
-                    o[c] = cx<R>{fma(cj, p[c].re, R(-0.5) * acc[j][c].re), fma(cj, p[c].im, R(-0.5) * acc[j][c].im)};
-                if (MODE == 1) {
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        part.add(p[c].re, o[c].re);
-                        part.add(p[c].im, o[c].im);
-                    }
-                } else {
-                    cx<R> b[3];
-                    Field<R>::load(G.epi_b[j], Vh, h, b);
-#pragma unroll
-                    for (int c = 0; c < 3; ++c) {
-                        o[c] = cx<R>{b[c].re - o[c].re, b[c].im - o[c].im};
-                        part.add(o[c].re, o[c].re);
-                        part.add(o[c].im, o[c].im);
-                    }
-                }
-            }
-            Field<R>::store(G.out[j], Vh, h, o);
-        }
-        if (MODE != 0 && G.partial[j] != nullptr) {
-            // two warps per 64-site chunk: warp sums, then pairs of warps
-            const double pv = part.warp_total();
-            __syncthreads();
-            if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = pv;
-            __syncthreads();
-            constexpr int kChunks = BS / kPartialSites;
-            const int c = blockIdx.x * kChunks + threadIdx.x;
-            if (threadIdx.x < kChunks && c < dslash_partials(Vh))
-                G.partial[j][c] = sh[2 * threadIdx.x] + sh[2 * threadIdx.x + 1];
-        }
-    }
+    dslash_epilogue<R, NRHS, MODE, BS>(G, act, live, h, acc, sh);
 }
 
 // Shared-link variant for groups of several right-hand sides on FP32 / 16-bit links (R = float).
@@ -451,7 +462,6 @@ inline int dslash_nrhs_template(int maxr) { return maxr <= 1 ? 1 : maxr <= 2 ? 2
 // Launch shape code: a block size (64, 128, 256) for the rhs-in-registers kernel, or
 // kSharedLinks for k_dslash_sh (64 x nrhs threads per block; FP32 arithmetic only).
 constexpr int kSharedLinks = 1 << 16;
-
 template <typename LinkT>
 cudaError_t launch_dslash_t(const DArgs &a, int mode, int bs, cudaStream_t st)
 {

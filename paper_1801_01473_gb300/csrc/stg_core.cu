@@ -542,6 +542,7 @@ stg_status stg_lattice_create(const int32_t dims[4], int32_t t_antiperiodic, stg
     for (int k = 0; k < 4; ++k) l->g.L[k] = dims[k];
     l->g.Vh = (int)(V / 2);
     l->g.antiperiodic = t_antiperiodic ? 1 : 0;
+    geom_init(l->g);
     l->V = V;
     *out = l;
     return STG_OK;

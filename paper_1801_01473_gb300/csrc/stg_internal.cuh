@@ -62,16 +62,22 @@ __device__ __forceinline__ cx<R> cmul(const cx<R> &a, const cx<R> &b)
 template <typename R>
 __device__ __forceinline__ cx<R> cconj(const cx<R> &a) { return cx<R>{a.re, -a.im}; }
 
+// conj(a b - c d) as one chain of a product and three multiply-adds per real part
+template <typename R>
+__device__ __forceinline__ cx<R> conj_cross(const cx<R> &a, const cx<R> &b, const cx<R> &c, const cx<R> &d)
+{
+    const R re = fma(a.re, b.re, fma(-a.im, b.im, fma(-c.re, d.re, c.im * d.im)));
+    const R im = fma(-a.re, b.im, fma(-a.im, b.re, fma(c.re, d.im, c.im * d.re)));
+    return cx<R>{re, im};
+}
+
 // third row of an SU(3) matrix from the first two: r3 = (r1 x r2)^*
 template <typename R>
 __device__ __forceinline__ void reconstruct_row3(cx<R> U[3][3])
 {
-    cx<R> a = cmul(U[0][1], U[1][2]), b = cmul(U[0][2], U[1][1]);
-    U[2][0] = cx<R>{a.re - b.re, -(a.im - b.im)};
-    a = cmul(U[0][2], U[1][0]); b = cmul(U[0][0], U[1][2]);
-    U[2][1] = cx<R>{a.re - b.re, -(a.im - b.im)};
-    a = cmul(U[0][0], U[1][1]); b = cmul(U[0][1], U[1][0]);
-    U[2][2] = cx<R>{a.re - b.re, -(a.im - b.im)};
+    U[2][0] = conj_cross(U[0][1], U[1][2], U[0][2], U[1][1]);
+    U[2][1] = conj_cross(U[0][2], U[1][0], U[0][0], U[1][2]);
+    U[2][2] = conj_cross(U[0][0], U[1][1], U[0][1], U[1][0]);
 }
 
 // ------------------------------------------------------------------ FP64 <-> FP32 on the integer pipes
@@ -238,11 +244,43 @@ struct ProdSum<dsf> {
 
 // ------------------------------------------------------------------ geometry
 
+// Quotient n / d for 0 <= n < 2^31 by one multiply-high, one add and one shift, with (m, s)
+// precomputed on the host for the invariant divisor d (Granlund and Montgomery, "Division by
+// invariant integers using multiplication", PLDI 1994, Sec. 4): s = ceil(log2 d),
+// m = floor(2^32 (2^s - d) / d) + 1 and n / d = (umulhi(m, n) + n) >> s; the sum stays below
+// 2^32 because umulhi(m, n) < n < 2^31.  A runtime integer division costs ~20 instructions.
+struct FastDiv {
+    unsigned m;
+    int s;
+};
+
+inline FastDiv make_fast_div(unsigned d)
+{
+    int s = 0;
+    while ((1ull << s) < d) ++s;
+    const unsigned long long m = ((1ull << 32) * ((1ull << s) - d)) / d + 1;
+    return FastDiv{(unsigned)m, s};
+}
+
+__device__ __forceinline__ int fast_div(int n, const FastDiv &f)
+{
+    return (int)((__umulhi(f.m, (unsigned)n) + (unsigned)n) >> f.s);
+}
+
 struct Geom {
     int L[4];       // Lx Ly Lz Lt
     int Vh;         // sites per parity
     int antiperiodic;
+    FastDiv div[3];  // by Lx / 2, Ly and Lz (geom_init)
 };
+
+// Fills the derived members of a Geom whose extents are set.
+inline void geom_init(Geom &g)
+{
+    g.div[0] = make_fast_div((unsigned)(g.L[0] >> 1));
+    g.div[1] = make_fast_div((unsigned)g.L[1]);
+    g.div[2] = make_fast_div((unsigned)g.L[2]);
+}
 
 // Coordinates and lexicographic index of the site with half index h on parity par.
 struct Site {
@@ -253,13 +291,13 @@ struct Site {
 __device__ __forceinline__ Site site_of(const Geom &g, int par, int h)
 {
     Site s;
-    int lxh = g.L[0] >> 1;
-    int r = h / lxh;
-    int xh = h - r * lxh;
-    s.y = r % g.L[1];
-    int r2 = r / g.L[1];
-    s.z = r2 % g.L[2];
-    s.t = r2 / g.L[2];
+    const int lxh = g.L[0] >> 1;
+    const int r = fast_div(h, g.div[0]);
+    const int xh = h - r * lxh;
+    const int r2 = fast_div(r, g.div[1]);
+    s.y = r - r2 * g.L[1];
+    s.t = fast_div(r2, g.div[2]);
+    s.z = r2 - s.t * g.L[2];
     int odd = (par + s.y + s.z + s.t) & 1;
     s.x = 2 * xh + odd;
     s.i = 2 * h + odd;

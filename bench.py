@@ -16,14 +16,18 @@ The same JSON line carries (measured in the same run, outside the timed steps):
              the workload computes in FP32 -- pack, D_eo, unpack, device -> host, pipelined on
              three streams; the complex128 figure beside it);
   roofline   D_eo FP32-12 against the measured HBM copy bandwidth;
-  sweep      16^4 and 32^4 D_eo for every link storage, L2 flushed, median of 50;
+  sweep      16^4 and 32^4 D_eo for every link storage: single launches after an L2 flush that
+             leaves clean lines (median of 50), and back-to-back launches over distinct sources
+             alternating two link copies; GB/s and fraction of the measured HBM bandwidth;
   mscg       32^4 msCG (16 poles 1e-5..10, m = 0.01, true residual 1e-10): mixed
              (FP32, FP16, BF16 inner; double-single reliable updates, FP64-verified) vs pure
-             FP64, s/solve;
+             FP64, s/solve, and the effective bandwidth of the algorithmic bytes;
   batched    the uneven batch (16^4, 24^3x8, 32^3x8, 24^4, 4 sources x 16 shifts) in one
-             solve vs the sum of separate solves;
-  force      48^4 fermion-force time (12 shifts, FP64);
-  cpu_baseline  the FP64 oracle's D_eo on the host cores, bounded sample.
+             solve vs the sum of separate solves, with per-instance iteration counts;
+  force      48^4 fermion force (12 shifts): whole call, its double-single D_oe part and the
+             per-link gather, with fractions of the measured HBM bandwidth;
+  cpu_baseline  the FP64 oracle on the host cores: D_eo at 16^4 and 32^4 and capped msCG
+             iterations at 32^4, on one thread and on all of them.
 --impl reference times that oracle as the reference arm (the paper ships no code).
 Multi-GPU: replicas only (independent copies of the workload on every rank).
 """
@@ -49,6 +53,17 @@ UNIT = "GB/s"
 WORKLOAD = "32^4 D_eo, exp(i0.3H) links FP32 12-real, complex64 vectors, batch of distinct sources"
 LINK_BYTES = {("f64", 18): 144, ("f64", 12): 96, ("ds", 18): 144, ("ds", 12): 96, ("f32", 18): 72,
               ("f32", 12): 48, ("bf16", 12): 24, ("f16", 12): 24}
+
+
+_LINKS = {}
+
+
+def links_cached(dims, kind, seed):
+    """Seeded synthetic links, generated once per (dims, kind, seed) in this process."""
+    key = (tuple(dims), kind, seed)
+    if key not in _LINKS:
+        _LINKS[key] = S.gauge_links(dims, kind, seed)
+    return _LINKS[key]
 
 
 def workload_config(batch, ws=1):
@@ -160,7 +175,7 @@ def run_reference(args):
     import oracle
     oracle.build()
     dims = S.CONFIGS["bandwidth_32x32x32x32"]["dims"]
-    u = S.gauge_links(dims, "expih", 1000 + 2)
+    u = links_cached(dims, "expih", 1000 + 2)
     psi = S.gaussian_field(dims, 2000 + 2)
     vh = S.volume(dims) // 2
     alg = bytes_per_site("f32", 12) * vh
@@ -186,23 +201,53 @@ def run_reference(args):
     return 0
 
 
-def cpu_baseline(budget_s=12.0):
+def cpu_baseline(d_budget_s=2.0, mscg_iters=(12, 4)):
+    """The FP64 oracle on the host cores: D_eo at 16^4 and 32^4, and the 32^4 msCG workload's
+    multi-shift iterations (capped, reported per iteration), each on one thread and on all of them.
+    `value` (the line's unit) is D_eo at 32^4 on all threads, bytes counted as the FP32-12
+    workload.  About 15 s of CPU work in all."""
     import oracle
     oracle.build()
-    dims = S.CONFIGS["bandwidth_32x32x32x32"]["dims"]
-    u = S.gauge_links(dims, "expih", 1000 + 2)
-    psi = S.gaussian_field(dims, 2000 + 2)
-    vh = S.volume(dims) // 2
-    oracle.dslash_eo(dims, u, psi)
-    n, t = 0, 0.0
-    while t < budget_s and n < 50:
+    nall = os.cpu_count() or 1
+    cases = []
+    value = None
+    for key in ("bandwidth_16x16x16x16", "bandwidth_32x32x32x32"):
+        cfg = S.CONFIGS[key]
+        dims = cfg["dims"]
+        u = links_cached(dims, cfg["links"], 1000 + cfg["k"])
+        psi = S.gaussian_field(dims, 2000 + cfg["k"])
+        vh = S.volume(dims) // 2
+        for nthr in (1, nall):
+            oracle.set_num_threads(nthr)
+            oracle.dslash_eo(dims, u, psi)
+            n, t = 0, 0.0
+            while (t < d_budget_s and n < 50) or n < 2:
+                t0 = time.perf_counter()
+                oracle.dslash_eo(dims, u, psi)
+                t += time.perf_counter() - t0
+                n += 1
+            gbs = bytes_per_site("f32", 12) * vh * n / t / 1e9
+            cases.append({"case": f"D_eo {'x'.join(map(str, dims))}", "threads": nthr, "calls": n,
+                          "ms_per_call": round(1e3 * t / n, 2), "GBs_f32r12_equiv": round(gbs, 3)})
+            if key == "bandwidth_32x32x32x32" and nthr == nall:
+                value = gbs
+    cfg = S.CONFIGS["mscg_32x32x32x32"]
+    dims = cfg["dims"]
+    u = links_cached(dims, cfg["links"], 1000 + cfg["k"])
+    b = S.gaussian_field(dims, 2000 + cfg["k"])
+    for nthr, cap in ((nall, mscg_iters[0]), (1, mscg_iters[1])):
+        oracle.set_num_threads(nthr)
         t0 = time.perf_counter()
-        oracle.dslash_eo(dims, u, psi)
-        t += time.perf_counter() - t0
-        n += 1
-    return {"value": bytes_per_site("f32", 12) * vh * n / t / 1e9, "unit": UNIT, "cores": oracle.num_threads(),
-            "kind": "oracle",
-            "sample": f"{n} FP64 oracle D_eo applications at 32^4 ({t:.1f} s), bytes counted as the FP32-12 workload"}
+        r = oracle.mscg(dims, u, cfg["mass"], cfg["shifts"](), b, tol=cfg["tol"], max_iter=cap, finish=False)
+        t = time.perf_counter() - t0
+        cases.append({"case": "msCG 32x32x32x32, 16 shifts, multi-shift iterations", "threads": nthr,
+                      "iters": r["iters"], "ms_per_iter": round(1e3 * t / r["iters"], 1),
+                      "note": f"capped at {cap} iterations; the GPU solve needs ~210 plus refinement"})
+    oracle.set_num_threads(nall)
+    return {"value": value, "unit": UNIT, "cores": nall, "kind": "oracle",
+            "sample": "FP64 oracle D_eo at 32^4 on all host threads (bytes counted as the FP32-12 workload); "
+                      "cases: D_eo at 16^4 and 32^4 and capped msCG iterations at 32^4, on 1 and all threads",
+            "cases": cases}
 
 
 # ---------------------------------------------------------------------------- GPU arm
@@ -212,51 +257,102 @@ def events(torch):
     return torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
 
 
-def time_deo_sweep(torch, p, dims, reps=50):
-    """D_eo per storage kind, L2 flushed before every call, median of reps."""
-    cfg_links = S.gauge_links(dims, "expih", 1000 + 2)
+class L2Flush:
+    """Evicts L2 between timed launches and leaves it holding clean lines: writes one 256 MB
+    buffer (> the 129 MB L2), then reads another.  A write alone leaves up to an L2 of dirty lines
+    that the next kernel must write back to HBM, which would be charged to that kernel."""
+
+    def __init__(self, torch):
+        self.w = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        self.r = torch.ones(64 * 1024 * 1024, dtype=torch.float32, device="cuda")
+        self.sink = torch.zeros((), dtype=torch.float32, device="cuda")
+        self.k = 0
+
+    def __call__(self):
+        self.k += 1
+        self.w.fill_(float(self.k))
+        self.sink.copy_(self.r.sum())
+
+
+def time_deo_sweep(torch, p, dims, peak, reps=50, b2b_batch=32):
+    """D_eo per storage kind at `dims`: single launches after an L2 flush (median of reps), and
+    back-to-back launches over distinct sources alternating two copies of the links (inputs larger
+    than L2, the configuration of the headline number)."""
+    cfg_links = links_cached(dims, "expih", 1000 + 2)
     ut = torch.from_numpy(cfg_links).cuda()
     lat = p.Lattice(dims)
     psi = torch.from_numpy(S.gaussian_field(dims, 2000 + 2)).cuda()
-    flush = torch.empty(64 * 1024 * 1024, dtype=torch.float32, device="cuda")  # 256 MB > L2
+    flush = L2Flush(torch)
     out = []
     theta = torch.from_numpy(np.random.default_rng(4000 + 2).uniform(-np.pi, np.pi, (4, lat.V))).cuda()
     for prec, recon, u1 in [("f64", 18, False), ("f64", 12, False), ("ds", 18, False), ("ds", 12, False),
                             ("f32", 18, False), ("f32", 12, False), ("f16", 12, False), ("bf16", 12, False),
                             ("f64", 18, True), ("ds", 18, True), ("f32", 12, True), ("f16", 12, True)]:
-        g = p.Gauge(lat, ut, prec, recon, theta=theta if u1 else None)
-        x = p.pack(lat, psi, g.vec_prec)
+        gs = [p.Gauge(lat, ut, prec, recon, theta=theta if u1 else None) for _ in range(2)]
+        x = p.pack(lat, psi, gs[0].vec_prec)
+        src = x.unsqueeze(0).repeat(b2b_batch, 1)
+        dst = torch.empty_like(src)
         y = torch.empty_like(x)
         for _ in range(5):
-            p.dslash_eo_(g, y, x)
+            p.dslash_eo_(gs[0], y, x)
         ts = []
         for _ in range(reps):
-            flush.zero_()
+            flush()
             e0, e1 = events(torch)
             e0.record()
-            p.dslash_eo_(g, y, x)
+            p.dslash_eo_(gs[0], y, x)
             e1.record()
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1) * 1e-3)
         t = float(np.median(ts))
+        e0, e1 = events(torch)
+        for j in range(b2b_batch):
+            p.dslash_eo_(gs[j & 1], dst[j], src[j])
+        e0.record()
+        for _ in range(3):
+            for j in range(b2b_batch):
+                p.dslash_eo_(gs[j & 1], dst[j], src[j])
+        e1.record()
+        torch.cuda.synchronize()
+        tb = e0.elapsed_time(e1) * 1e-3 / (3 * b2b_batch)
         # a U(1) phase field adds one stored phase per link ((cos, sin) doubles for f64/ds, a float angle otherwise)
         byt = (bytes_per_site(prec, recon) + (8 * (16 if prec in ("f64", "ds") else 4) if u1 else 0)) * lat.Vh
         out.append({"lattice": "x".join(map(str, dims)), "links": f"{prec}-{recon}" + ("+u1" if u1 else ""),
-                    "us": round(t * 1e6, 2), "GBs": round(byt / t / 1e9, 1)})
-        del g
+                    "us": round(t * 1e6, 2), "GBs": round(byt / t / 1e9, 1), "frac": round(byt / t / 1e9 / peak, 3),
+                    "b2b_us": round(tb * 1e6, 2), "b2b_GBs": round(byt / tb / 1e9, 1),
+                    "b2b_frac": round(byt / tb / 1e9 / peak, 3)})
+        del gs, src, dst
     return out
 
 
-def time_mscg(torch, p, reps=3):
+def mscg_alg_bytes(vh, st, inner):
+    """Algorithmic bytes of one msCG solve on one system, from its statistics.
+    Multi-shift phase, per iteration and even site (the standard count): 2 (8 links + 2 v) for
+    D_oe and D_eo, 5 v for r, p, q, and 4 v for x_i, p_i of each active shift -- summed with the
+    real number of active shifts of every iteration (sum over shifts of the iteration each stopped).
+    Refinement, per CG iteration of a shift: 2 (8 links + 2 v) + 7 v (x, r, p updates) on the FP32
+    12-real operator; per reliable update the double-single residual, 2 (8 x 144 + 2 x 48) + 4 x 48.
+    inner: (link bytes, vector bytes) of the multi-shift phase."""
+    lb, v = inner
+    p1 = st["iters"] * (2 * (8 * lb + 2 * v) + 5 * v) + 4 * v * sum(st["shift_iters"])
+    if lb >= 144:  # pure FP64 solve: no refinement
+        return vh * p1
+    ref = sum(st["refine_shift_iters"]) * (2 * (8 * 48 + 2 * 24) + 7 * 24)
+    rel = sum(st["shift_reliable_updates"]) * (2 * (8 * 144 + 2 * 48) + 4 * 48)
+    return vh * (p1 + ref + rel)
+
+
+def time_mscg(torch, p, peak, reps=3):
     cfg = S.CONFIGS["mscg_32x32x32x32"]
     dims = cfg["dims"]
-    ut = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
+    ut = torch.from_numpy(links_cached(dims, cfg["links"], 1000 + cfg["k"])).cuda()
     b = torch.from_numpy(S.gaussian_field(dims, 2000 + cfg["k"])).cuda()
     lat = p.Lattice(dims)
     g64 = p.Gauge(lat, ut, "f64", 18)
     shifts = cfg["shifts"]()
     res = {}
-    for name, inner in [("fp32", ("f32", 12)), ("fp16", ("f16", 12)), ("bf16", ("bf16", 12)), ("fp64", None)]:
+    for name, inner, ib in [("fp32", ("f32", 12), (48, 24)), ("fp16", ("f16", 12), (24, 24)),
+                            ("bf16", ("bf16", 12), (24, 24)), ("fp64", None, (144, 48))]:
         gi = p.Gauge(lat, ut, inner[0], inner[1]) if inner else None
         p.mscg(g64, b, shifts, cfg["mass"], tol=cfg["tol"], g_inner=gi, allow_noconv=True)  # autotune, untimed
         ts = []
@@ -267,21 +363,28 @@ def time_mscg(torch, p, reps=3):
             _, st = p.mscg(g64, b, shifts, cfg["mass"], tol=cfg["tol"], g_inner=gi, allow_noconv=True)
             torch.cuda.synchronize()
             ts.append(time.perf_counter() - t0)
-        res[name] = {"s_per_solve": round(float(np.median(ts)), 5), "iters": st["iters"],
+        t = float(np.median(ts))
+        alg = mscg_alg_bytes(lat.Vh, st, ib)
+        res[name] = {"s_per_solve": round(t, 5), "iters": st["iters"],
                      "refine_iters": st["refine_iters"], "reliable_updates": st["reliable_updates"],
-                     "max_true_resid": float(max(st["true_resid"])), "converged": st["status"] == 0}
+                     "max_true_resid": float(max(st["true_resid"])), "converged": st["status"] == 0,
+                     "alg_GB": round(alg / 1e9, 2), "eff_GBs": round(alg / t / 1e9, 1),
+                     "frac": round(alg / t / 1e9 / peak, 3)}
         del gi
     res["mixed_speedup_vs_fp64"] = round(res["fp64"]["s_per_solve"] / min(
         res[k]["s_per_solve"] for k in ("fp32", "fp16", "bf16") if res[k]["converged"]), 3)
+    res["note"] = ("eff_GBs = algorithmic bytes (multi-shift phase with the real active-shift count per iteration, "
+                   "refinement and reliable updates) / solve time; the deferred solution update moves fewer bytes "
+                   "than the count, the FP64 verification is not counted")
     return res
 
 
-def time_batched(torch, p, reps=2):
+def time_batched(torch, p, peak, reps=2):
     cfg = S.CONFIGS["batched_uneven"]
     shifts = cfg["shifts"]()
     insts = []
     for li, dims in enumerate(cfg["dims_list"]):
-        ut = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + 10 * cfg["k"] + li)).cuda()
+        ut = torch.from_numpy(links_cached(dims, cfg["links"], 1000 + 10 * cfg["k"] + li)).cuda()
         lat = p.Lattice(dims)
         bs = [torch.from_numpy(S.gaussian_field(dims, 2000 + 10 * cfg["k"] + 4 * li + r)).cuda()
               for r in range(cfg["nrhs"])]
@@ -298,6 +401,9 @@ def time_batched(torch, p, reps=2):
         torch.cuda.synchronize()
         tb.append(time.perf_counter() - t0)
     worst = max(max(s["true_resid"]) for _, sts in out for s in sts)
+    alg = sum(mscg_alg_bytes(g64.lattice.Vh, s, (48, 24)) for (g64, _, _), (_, sts) in zip(insts, out) for s in sts)
+    per_inst = [{"lattice": "x".join(map(str, g64.lattice.dims)), "iters": [s["iters"] for s in sts],
+                 "refine_iters": [s["refine_iters"] for s in sts]} for (g64, _, _), (_, sts) in zip(insts, out)]
     ts = 0.0
     for g64, gi, bs in insts:
         for b in bs:
@@ -306,17 +412,28 @@ def time_batched(torch, p, reps=2):
             p.mscg(g64, b, shifts, cfg["mass"], tol=cfg["tol"], g_inner=gi)
             torch.cuda.synchronize()
             ts += time.perf_counter() - t0
-    return {"s_per_batch": round(float(np.median(tb)), 5), "sum_of_separate_s": round(ts, 5),
-            "speedup": round(ts / float(np.median(tb)), 3), "systems": 16, "shifts": 16,
-            "max_true_resid": worst}
+    t = float(np.median(tb))
+    return {"s_per_batch": round(t, 5), "sum_of_separate_s": round(ts, 5),
+            "speedup": round(ts / t, 3), "systems": 16, "shifts": 16,
+            "max_true_resid": worst, "alg_GB": round(alg / 1e9, 2), "eff_GBs": round(alg / t / 1e9, 1),
+            "frac": round(alg / t / 1e9 / peak, 3), "separate_eff_GBs": round(alg / ts / 1e9, 1),
+            "per_instance": per_inst}
 
 
-def time_force(torch, p):
+# Fermion force per link (48^4, 12 shifts): the link (144 B), the output (144 B) and, with every
+# vector read once per site, 12 x 48 B of x_i or y_i per site over its 4 links = 144 B.
+FORCE_BYTES_PER_LINK = 3 * 144
+
+
+def time_force(torch, p, peak):
+    """48^4 fermion force: the whole call, and apart from it the 12 double-single D_oe
+    applications y_i = D_oe x_i it contains (the rest is the per-link gather of W and F)."""
     cfg = S.CONFIGS["force_48x48x48x48"]
     dims = cfg["dims"]
     lat = p.Lattice(dims)
-    ut = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
+    ut = torch.from_numpy(links_cached(dims, cfg["links"], 1000 + cfg["k"])).cuda()
     g64 = p.Gauge(lat, ut, "f64", 18)
+    gds = p.Gauge(lat, ut, "ds", 18)
     del ut
     res = S.positive_residues(3000 + cfg["k"], 12)
     g = torch.Generator(device="cuda").manual_seed(2000 + cfg["k"])
@@ -329,9 +446,28 @@ def time_force(torch, p):
         f = p.fermion_force(g64, res, x)
     e1.record()
     torch.cuda.synchronize()
+    t = e0.elapsed_time(e1) * 1e-3 / 3
     del f
-    return {"lattice": "48^4", "shifts": 12, "ms": round(e0.elapsed_time(e1) / 3, 3),
-            "note": "double-single D_oe on the 12 solutions + per-link gather of W in double-single, F in FP64"}
+    xd = p.pack(lat, x[0], "ds")
+    yd = torch.empty_like(xd)
+    p.dslash_oe_(gds, yd, xd)
+    e0, e1 = events(torch)
+    e0.record()
+    for _ in range(12):
+        p.dslash_oe_(gds, yd, xd)
+    e1.record()
+    torch.cuda.synchronize()
+    t_d = e0.elapsed_time(e1) * 1e-3
+    links = 4 * lat.V
+    t_g = max(t - t_d, 1e-9)
+    d_bytes = 12 * bytes_per_site("ds", 18) * lat.Vh
+    return {"lattice": "48^4", "shifts": 12, "ms": round(t * 1e3, 3),
+            "doe_ms": round(t_d * 1e3, 3), "doe_GBs": round(d_bytes / t_d / 1e9, 1),
+            "doe_frac": round(d_bytes / t_d / 1e9 / peak, 3),
+            "gather_ms": round(t_g * 1e3, 3), "gather_GBs": round(FORCE_BYTES_PER_LINK * links / t_g / 1e9, 1),
+            "gather_frac": round(FORCE_BYTES_PER_LINK * links / t_g / 1e9 / peak, 3),
+            "note": "double-single D_oe on the 12 solutions (FP32-pipe bound) + per-link gather of W in "
+                    "double-single and F in FP64 (FP32/FP64-pipe bound); fractions are of measured HBM bandwidth"}
 
 
 # Algorithmic FP64 flops per link of one stout step (complex 3x3 product = 27 complex
@@ -346,7 +482,7 @@ def time_stout(torch, p):
     cfg = S.CONFIGS["force_48x48x48x48"]
     dims = cfg["dims"]
     lat = p.Lattice(dims)
-    u64 = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
+    u64 = torch.from_numpy(links_cached(dims, cfg["links"], 1000 + cfg["k"])).cuda()
     rho, nstep = 0.15, 2
     out = {"lattice": "48^4", "steps": nstep, "rho": rho}
     for tag, ut in (("fp64", u64), ("fp32", p.complex_convert(u64, torch.complex64))):
@@ -384,7 +520,7 @@ def time_gauge(torch, p):
     cfg = S.CONFIGS["force_48x48x48x48"]
     dims = cfg["dims"]
     lat = p.Lattice(dims)
-    u64 = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
+    u64 = torch.from_numpy(links_cached(dims, cfg["links"], 1000 + cfg["k"])).cuda()
     beta = 5.6
     out = {"lattice": "48^4"}
     for tag, ut in (("fp64", u64), ("fp32", p.complex_convert(u64, torch.complex64))):
@@ -425,7 +561,7 @@ def time_rhmc(torch, p):
     lat = p.Lattice(dims)
     # smoothed synthetic start (10 stout steps of the random links), closer to an equilibrium
     # configuration than the raw random links, whose large forces break the integrator
-    u = p.stout_smear(lat, torch.from_numpy(S.gauge_links(dims, "expih", 1002)).cuda(), 0.1, 10)[-1].contiguous()
+    u = p.stout_smear(lat, torch.from_numpy(links_cached(dims, "expih", 1002)).cuda(), 0.1, 10)[-1].contiguous()
     tab = load_table()
     act = p.md.Action(lat, beta=5.6, mass=0.3, tol=1e-10, md_tol=1e-7, inner="f32", precision="f32",
                       stout_rho=0.15, stout_steps=2)
@@ -471,7 +607,7 @@ def run_gpu(args):
     cfg = S.CONFIGS["bandwidth_32x32x32x32"]
     dims = cfg["dims"]
     lat = p.Lattice(dims)
-    u = S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])
+    u = links_cached(dims, cfg["links"], 1000 + cfg["k"])
     ut = torch.from_numpy(u).cuda()
     gauges = [p.Gauge(lat, ut, "f32", 12), p.Gauge(lat, ut, "f32", 12)]
     del ut
@@ -528,10 +664,13 @@ def run_gpu(args):
         e2e_rates[dt] = (time.perf_counter() - t0) / (2 * n_e2e)
         del host_in, host_out
     e2e_t = e2e_rates[torch.complex64]
+    # one e2e step = one dslash_host call on n_e2e complex64 fields: every field is copied host ->
+    # device and its result device -> host inside the timed region
     e2e = {"value": round(ws * alg / e2e_t / 1e9, 2), "unit": UNIT,
-           "h2d_bytes_per_step": int(one.numel() * 8 * B), "d2h_bytes_per_step": int(one.numel() * 8 * B),
-           "note": f"2 calls of dslash_host, {n_e2e} pinned host complex64 fields each (copy in, pack, D_eo, "
-                   "unpack, copy out; three-stage pipeline)",
+           "h2d_bytes_per_step": int(one.numel() * 8 * n_e2e), "d2h_bytes_per_step": int(one.numel() * 8 * n_e2e),
+           "steps": 2, "fields_per_step": n_e2e,
+           "note": f"2 steps, each one call of dslash_host on {n_e2e} pinned host complex64 fields (copy in, pack, "
+                   "D_eo, unpack, copy out; three-stage pipeline)",
            "complex128_host_fields": round(ws * alg / e2e_rates[torch.complex128] / 1e9, 2)}
     del gauges, src, dst
 
@@ -546,10 +685,10 @@ def run_gpu(args):
                          "kernel": "k_dslash<LinkF32R12,1,0>"},
             "gpu_launches": launches, "clocks": clocks, "e2e": e2e}
     if rank == 0 and not args.no_extras:
-        line["sweep"] = time_deo_sweep(torch, p, (16, 16, 16, 16)) + time_deo_sweep(torch, p, (32, 32, 32, 32))
-        line["mscg"] = time_mscg(torch, p)
-        line["batched"] = time_batched(torch, p)
-        line["force"] = time_force(torch, p)
+        line["sweep"] = time_deo_sweep(torch, p, (16, 16, 16, 16), peak) + time_deo_sweep(torch, p, (32, 32, 32, 32), peak)
+        line["mscg"] = time_mscg(torch, p, peak)
+        line["batched"] = time_batched(torch, p, peak)
+        line["force"] = time_force(torch, p, peak)
         line["stout"] = time_stout(torch, p)
         line["gauge"] = time_gauge(torch, p)
         line["rhmc"] = time_rhmc(torch, p)
@@ -575,7 +714,7 @@ def run_case(name):
         cfg = S.CONFIGS["mscg_32x32x32x32"]
         dims = cfg["dims"]
         lat = p.Lattice(dims)
-        ut = torch.from_numpy(S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])).cuda()
+        ut = torch.from_numpy(links_cached(dims, cfg["links"], 1000 + cfg["k"])).cuda()
         b = torch.from_numpy(S.gaussian_field(dims, 2000 + cfg["k"])).cuda()
         g64, gi = p.Gauge(lat, ut, "f64", 18), p.Gauge(lat, ut, "f32", 12)
         for _ in range(2):
@@ -584,7 +723,7 @@ def run_case(name):
     elif name == "force32":
         dims = (32, 32, 32, 32)
         lat = p.Lattice(dims)
-        ut = torch.from_numpy(S.gauge_links(dims, "expih", 1002)).cuda()
+        ut = torch.from_numpy(links_cached(dims, "expih", 1002)).cuda()
         g64, gds = p.Gauge(lat, ut, "f64", 18), p.Gauge(lat, ut, "ds", 18)
         x = p.pack(lat, torch.from_numpy(S.gaussian_field(dims, 2002)).cuda(), "ds")
         y = torch.empty_like(x)
@@ -597,7 +736,7 @@ def run_case(name):
     elif name == "stout24":
         dims = (24, 24, 24, 24)
         lat = p.Lattice(dims)
-        ut = torch.from_numpy(S.gauge_links(dims, "expih", 1005)).cuda()
+        ut = torch.from_numpy(links_cached(dims, "expih", 1005)).cuda()
         levels = p.stout_smear(lat, ut, 0.15, 1)
         gen = torch.Generator(device="cuda").manual_seed(3005)
         z = torch.randn(ut.shape, dtype=torch.complex128, device="cuda", generator=gen)
@@ -606,7 +745,7 @@ def run_case(name):
     elif name == "gauge24":
         dims = (24, 24, 24, 24)
         lat = p.Lattice(dims)
-        ut = torch.from_numpy(S.gauge_links(dims, "expih", 1005)).cuda()
+        ut = torch.from_numpy(links_cached(dims, "expih", 1005)).cuda()
         f = p.gauge_force(lat, ut, 5.6, kind=0)
         print("gauge24", p.gauge_action(lat, ut, 5.6)["action"], float(f.abs().max()))
     elif name == "rhmc_force32":
@@ -616,7 +755,7 @@ def run_case(name):
         from paper_1801_01473_gb300.rational import load_table
         dims = (32, 32, 32, 32)
         lat = p.Lattice(dims)
-        u = p.stout_smear(lat, torch.from_numpy(S.gauge_links(dims, "expih", 1002)).cuda(), 0.1, 10)[-1].contiguous()
+        u = p.stout_smear(lat, torch.from_numpy(links_cached(dims, "expih", 1002)).cuda(), 0.1, 10)[-1].contiguous()
         ra = load_table()["action"]
         b = torch.from_numpy(S.gaussian_field(dims, 2002)).cuda()
         act = p.md.Action(lat, beta=5.6, mass=0.3, tol=1e-10, md_tol=1e-7, inner="f32", precision="f32",
@@ -633,7 +772,7 @@ def run_case(name):
     elif name == "fp32links24":
         dims = (24, 24, 24, 24)
         lat = p.Lattice(dims)
-        u32 = p.complex_convert(torch.from_numpy(S.gauge_links(dims, "expih", 1005)).cuda(), torch.complex64)
+        u32 = p.complex_convert(torch.from_numpy(links_cached(dims, "expih", 1005)).cuda(), torch.complex64)
         f = p.gauge_force(lat, u32, 5.6, kind=0)
         levels = p.stout_smear(lat, u32, 0.15, 1)
         gen = torch.Generator(device="cuda").manual_seed(3005)

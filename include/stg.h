@@ -224,6 +224,10 @@ typedef struct {
     double *inner_resid;      /* host [nshift] (may be NULL): true residual of each shift right
                                  after the multi-shift phase, before refinement                   */
     int32_t fp64_fallback;    /* 1 if a mixed solve was repeated with FP64 reliable updates       */
+    int32_t *refine_shift_iters;  /* host [nshift] (may be NULL): refinement CG iterations of each
+                                     shift (0 for shifts the multi-shift phase finished)          */
+    int32_t *shift_reliable_updates; /* host [nshift] (may be NULL): reliable updates of each shift's
+                                     refinement                                                   */
 } stg_mscg_stats;
 
 /* Solves A_{sigma_i} x_i = b for every shift.

@@ -46,7 +46,8 @@ def _load():
         lib.oracle_true_residual.argtypes = [P, I, P, D, D, P, P]
         lib.oracle_true_residual.restype = D
         lib.oracle_cg.argtypes = [P, I, P, D, D, D, I, P, P]
-        lib.oracle_mscg.argtypes = [P, I, P, D, I, P, D, I, P, P, P, P, P, P, I]
+        lib.oracle_mscg.argtypes = [P, I, P, D, I, P, D, I, P, P, P, P, P, P, I, I]
+        lib.oracle_set_num_threads.argtypes = [I]
         lib.oracle_force.argtypes = [P, I, P, I, P, P, P, I]
         lib.oracle_num_threads.restype = I
         _lib = lib
@@ -78,6 +79,11 @@ def volume(dims) -> int:
 
 def num_threads() -> int:
     return int(_load().oracle_num_threads())
+
+
+def set_num_threads(n: int) -> None:
+    """OpenMP threads of the following oracle calls."""
+    _load().oracle_set_num_threads(int(n))
 
 
 def dslash_full(dims, links, psi, antiperiodic: bool = True) -> np.ndarray:
@@ -149,9 +155,11 @@ def cg(dims, links, mass, sigma, b, x0=None, tol=1e-10, max_iter=10000, antiperi
     return x, int(it)
 
 
-def mscg(dims, links, mass, shifts, b, tol=1e-10, max_iter=20000, log_rows: int = 0, antiperiodic: bool = True):
+def mscg(dims, links, mass, shifts, b, tol=1e-10, max_iter=20000, log_rows: int = 0, antiperiodic: bool = True,
+         finish: bool = True):
     """Multi-shift CG.  Returns dict(x [nshift][Vh][3], true_resid, shift_iters,
-    iters, refine_iters, scalar_log [log_rows][2+nshift] or None)."""
+    iters, refine_iters, scalar_log [log_rows][2+nshift] or None).  finish=False stops after the
+    multi-shift iterations (no true residuals, which are then -1, and no refinement)."""
     d = _dims(dims)
     v = volume(d)
     u = _c128(links, (4, v, 3, 3))
@@ -165,7 +173,7 @@ def mscg(dims, links, mass, shifts, b, tol=1e-10, max_iter=20000, log_rows: int 
     log = np.zeros((max(log_rows, 1), 2 + ns), np.float64)
     it = _load().oracle_mscg(_ptr(d), int(antiperiodic), _ptr(u), float(mass), ns, _ptr(sig), float(tol),
                              int(max_iter), _ptr(bb), _ptr(x), _ptr(tr), _ptr(si), _ptr(ri),
-                             _ptr(log) if log_rows > 0 else None, int(log_rows))
+                             _ptr(log) if log_rows > 0 else None, int(log_rows), int(bool(finish)))
     if it < 0:
         raise MemoryError("oracle_mscg")
     return dict(x=x, true_resid=tr, shift_iters=si, iters=int(it), refine_iters=int(ri[0]),

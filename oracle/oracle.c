@@ -242,12 +242,13 @@ int oracle_cg(const int L[4], int antiperiodic, const cplx *U, double mass, doub
  * x: [nshift][Vh][3] output.  true_resid[nshift], shift_iters[nshift] outputs.
  * scalar_log (optional, may be NULL): row k = (alpha_k, beta_k, zeta_0^{k+1}, ...,
  * zeta_{n-1}^{k+1}) for the first log_rows iterations.
+ * finish == 0 skips the true residuals and the refinement (true_resid = -1).
  * Returns the number of multi-shift iterations, or -1 on allocation failure.
  */
 int oracle_mscg(const int L[4], int antiperiodic, const cplx *U, double mass,
                 int nshift, const double *sigma, double tol, int max_iter,
                 const cplx *b, cplx *x, double *true_resid, int *shift_iters,
-                int *refine_iters, double *scalar_log, int log_rows)
+                int *refine_iters, double *scalar_log, int log_rows, int finish)
 {
     long n = volume_of(L) / 2 * 3;
     double sigma0 = sigma[0];
@@ -331,9 +332,11 @@ int oracle_mscg(const int L[4], int antiperiodic, const cplx *U, double mass,
     }
     for (int i = 0; i < nshift; ++i) if (active[i]) shift_iters[i] = it;
 
-    /* true residuals; finish any shift above tol with plain CG from x_i */
+    /* true residuals; finish any shift above tol with plain CG from x_i (finish == 0 skips both
+       and leaves true_resid at -1: timing of the multi-shift iterations alone) */
     if (refine_iters) *refine_iters = 0;
-    for (int i = 0; i < nshift; ++i) {
+    for (int i = 0; i < nshift && !finish; ++i) true_resid[i] = -1.0;
+    for (int i = 0; i < nshift && finish; ++i) {
         cplx *xi = x + (long)i * n;
         true_resid[i] = oracle_true_residual(L, antiperiodic, U, mass, sigma[i], b, xi);
         if (true_resid[i] > tol) {
@@ -421,5 +424,15 @@ int oracle_num_threads(void)
     return omp_get_max_threads();
 #else
     return 1;
+#endif
+}
+
+/* sets the number of OpenMP threads of the following calls (n >= 1) */
+void oracle_set_num_threads(int n)
+{
+#ifdef _OPENMP
+    if (n >= 1) omp_set_num_threads(n);
+#else
+    (void)n;
 #endif
 }

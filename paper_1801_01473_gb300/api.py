@@ -264,15 +264,19 @@ def _stats(nshift):
     tr = (ctypes.c_double * nshift)()
     si = (ctypes.c_int32 * nshift)()
     ir = (ctypes.c_double * nshift)()
-    st = MscgStats(0, 0, 0, ctypes.cast(tr, ctypes.POINTER(ctypes.c_double)),
-                   ctypes.cast(si, ctypes.POINTER(ctypes.c_int32)), ctypes.cast(ir, ctypes.POINTER(ctypes.c_double)), 0)
-    return st, tr, (si, ir)
+    rs = (ctypes.c_int32 * nshift)()
+    ru = (ctypes.c_int32 * nshift)()
+    i32p = ctypes.POINTER(ctypes.c_int32)
+    st = MscgStats(0, 0, 0, ctypes.cast(tr, ctypes.POINTER(ctypes.c_double)), ctypes.cast(si, i32p),
+                   ctypes.cast(ir, ctypes.POINTER(ctypes.c_double)), 0, ctypes.cast(rs, i32p), ctypes.cast(ru, i32p))
+    return st, tr, (si, ir, rs, ru)
 
 
 def _stats_dict(st, tr, extra):
-    si, ir = extra
+    si, ir, rs, ru = extra
     return dict(iters=st.iters, reliable_updates=st.reliable_updates, refine_iters=st.refine_iters,
-                true_resid=list(tr), shift_iters=list(si), inner_resid=list(ir), fp64_fallback=st.fp64_fallback)
+                true_resid=list(tr), shift_iters=list(si), inner_resid=list(ir), fp64_fallback=st.fp64_fallback,
+                refine_shift_iters=list(rs), shift_reliable_updates=list(ru))
 
 
 def mscg(g_f64: Gauge, b: torch.Tensor, shifts, mass: float, tol: float = 1e-10, g_inner: Gauge | None = None,

@@ -1449,6 +1449,8 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
                 if (S && S->true_resid) S->true_resid[i] = res;
                 if (S && S->inner_resid) S->inner_resid[i] = bb > 0 ? std::sqrt(trr0[pidx] / bb) : 0.0;
                 if (S && S->shift_iters) S->shift_iters[i] = f1[s].shift_iters[i] ? f1[s].shift_iters[i] : f1[s].iters;
+                if (S && S->refine_shift_iters) S->refine_shift_iters[i] = f2[pidx].iters;
+                if (S && S->shift_reliable_updates) S->shift_reliable_updates[i] = std::max(0, rc[pidx] - 1);
             }
             if (S) {
                 S->iters = f1[s].iters;

@@ -524,7 +524,7 @@ const char *stg_status_string(stg_status s)
 
 const char *stg_last_error(void) { return g_last_error.c_str(); }
 
-const char *stg_version(void) { return "stg 0.1 (sm_103a)"; }
+const char *stg_version(void) { return "stg 0.2 (sm_103a)"; }
 
 stg_status stg_lattice_create(const int32_t dims[4], int32_t t_antiperiodic, stg_lattice **out)
 {

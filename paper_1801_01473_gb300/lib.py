@@ -42,7 +42,9 @@ class MscgParams(ctypes.Structure):
 class MscgStats(ctypes.Structure):
     _fields_ = [("iters", ctypes.c_int32), ("reliable_updates", ctypes.c_int32), ("refine_iters", ctypes.c_int32),
                 ("true_resid", ctypes.POINTER(ctypes.c_double)), ("shift_iters", ctypes.POINTER(ctypes.c_int32)),
-                ("inner_resid", ctypes.POINTER(ctypes.c_double)), ("fp64_fallback", ctypes.c_int32)]
+                ("inner_resid", ctypes.POINTER(ctypes.c_double)), ("fp64_fallback", ctypes.c_int32),
+                ("refine_shift_iters", ctypes.POINTER(ctypes.c_int32)),
+                ("shift_reliable_updates", ctypes.POINTER(ctypes.c_int32))]
 
 
 class Instance(ctypes.Structure):

@@ -86,7 +86,9 @@ const char *stg_version(void);
  * into u_mu).  *out receives a new handle.  STG_ERR_SHAPE on odd or small extents. */
 stg_status stg_lattice_create(const int32_t dims[4], int32_t t_antiperiodic, stg_lattice **out);
 void stg_lattice_destroy(stg_lattice *lat);
-/* Number of sites of one parity (0 even, 1 odd) or of the whole lattice (-1); -1 on NULL. */
+/* Number of sites of one parity (0 even, 1 odd) or of the whole lattice (-1); -1 on NULL.
+ * The even/odd split is that of Eq. shift_eo (Sec. 2): fields live on one parity, each of
+ * V/2 sites (Sec. 4.1 stores them the same way). */
 int64_t stg_lattice_sites(const stg_lattice *lat, int32_t parity);
 
 /* ---- gauge field ----------------------------------------------------------------------- */
@@ -126,9 +128,16 @@ size_t stg_gauge_bytes(const stg_gauge *g);
 /* ---- fermion fields ----------------------------------------------------------------------- */
 
 /* Bytes of one parity's field in the internal layout for vector precision F64, DS or F32
- * (48, 48 or 24 bytes per site); 0 for any other precision or a NULL lattice. */
+ * (48, 48 or 24 bytes per site); 0 for any other precision or a NULL lattice.  The internal
+ * layout is a structure of arrays over the sites of one parity (Sec. 4.1's colour-vector
+ * layout, one array per colour component, so that consecutive threads read consecutive
+ * addresses); 48 bytes per site is the paper's FP64 figure for one colour vector (Sec. 3.1). */
 size_t stg_field_bytes(const stg_lattice *lat, stg_prec vec_prec);
-/* canonical complex128 [Vh][3] (device) <-> internal layout (device). vec_prec F64, DS or F32. */
+/* canonical complex128 [Vh][3] (device) <-> internal layout (device). vec_prec F64, DS or F32.
+ * The conversion between the array-of-structures interchange layout and the structure-of-arrays
+ * layout of Sec. 4.1 (see stg_field_bytes); F32 and DS round each FP64 component (to nearest,
+ * DS keeping the rounding error in its second float).  STG_ERR_ARG on NULL pointers or another
+ * precision; asynchronous on `stream`. */
 stg_status stg_field_pack(const stg_lattice *lat, stg_prec vec_prec, const void *canon_c128_dev, void *internal_dev,
                           void *stream);
 stg_status stg_field_unpack(const stg_lattice *lat, stg_prec vec_prec, const void *internal_dev, void *canon_c128_dev,
@@ -174,8 +183,12 @@ stg_status stg_normal_op(const stg_gauge *g, double mass, double shift, void *ou
  * device, or fail once memory is partitioned).  It needs no tmp_odd: the odd temporary and the
  * partial sums live in one 32 MiB file-scope __device__ array that every GPU loading the library
  * holds until exit.  The paper has no counterpart of this entry point.
- *   Limit: Vh <= 697232 sites per parity for F64 gauges, <= 1390848 for F32/BF16/F16 gauges
- *          (a 32^4 lattice fits at FP64); larger lattices return STG_ERR_ARG before any launch.
+ *   Limit: Vh <= 697232 sites per parity for F64 and DS (double-single) gauges, whose odd
+ *          temporary takes 48 B per site, and <= 1390848 for F32/BF16/F16 gauges (24 B per
+ *          site), with or without a U(1) phase field (a 32^4 lattice fits at FP64); larger
+ *          lattices return STG_ERR_ARG before any launch.
+ *   Arguments: in and out must not overlap (STG_ERR_ARG otherwise: the fused epilogue reads in
+ *          while it writes out); both 16-byte aligned.
  *   Set-up: the first call on a device looks up the array's device address (cudaGetSymbolAddress
  *          with that device current) and caches it; make that first call before any stream
  *          capture.  Nothing is allocated, here or later.
@@ -257,6 +270,25 @@ stg_status stg_rational_apply(const stg_gauge *g_f64, const stg_gauge *g_inner, 
                               double alpha0, const double *residues, const void *b_c128_dev, void *out_c128_dev,
                               stg_mscg_stats *stats, void *stream);
 
+/* The fermion action of one pseudofermion b from the solutions of its shifted systems (Sec. 2:
+ * the RHMC writes the fractional power of the staggered operator as a rational function, a
+ * constant plus one pole per system of Eq. shift_eo, and the action as b^dag R(A) b):
+ *   S = alpha0 |b|^2 + sum_i residues[i] Re(b^dag x_i),   x_i = (m^2 + sigma_i - D_eo D_oe)^-1 b
+ *   lat                  the lattice of the fields
+ *   nshift               0 .. 32 (0: alpha0 |b|^2 alone)
+ *   residues             host [nshift]
+ *   b_c128_dev           canonical complex128 [Vh][3] even-site field (device, 16-byte aligned)
+ *   x_c128_dev[nshift]   host array of device pointers to the solutions, same layout (for
+ *                        example the outputs of stg_mscg_solve)
+ *   s_dev                one device double (8-byte aligned) receiving S
+ * The sum runs in FP64 in a fixed order (per element in pole order, fixed block trees over a fixed
+ * grid, then one fixed-order sum of the 1024 block partials), so S does not depend on timing.
+ * Asynchronous on `stream`; takes an 8 KiB workspace from the stream-ordered allocator.
+ * STG_ERR_ARG on a null or misaligned pointer or nshift outside 0..32. */
+stg_status stg_pseudofermion_action(const stg_lattice *lat, int32_t nshift, double alpha0, const double *residues,
+                                    const void *b_c128_dev, const void *const *x_c128_dev, double *s_dev,
+                                    void *stream);
+
 /* One lattice of a batched solve: nrhs sources (pseudofermions) on the same gauge. */
 typedef struct {
     const stg_gauge *g_f64;
@@ -291,7 +323,7 @@ stg_status stg_mscg_solve_batched(int32_t ninst, const stg_instance *inst, const
 stg_status stg_fermion_force(const stg_gauge *g_f64, int32_t nshift, const double *residues,
                              const void *const *x_c128_dev, void *out_c128_dev, int32_t kind, void *stream);
 /* stg_fermion_force at a chosen precision.  prec = STG_F64: exactly stg_fermion_force (out
- * complex128).  prec = STG_F32 (single-precision MD forces, Sec. 5.3): x_i rounded to FP32, y_i from
+ * complex128).  prec = STG_F32 (single-precision MD forces, Sec. 5.4): x_i rounded to FP32, y_i from
  * the FP32 12-real companion of the links (created on first use and kept, like the double-single
  * one), W and the output in FP32 arithmetic; out_dev is canonical complex64 [4][V][3][3].  Relative
  * accuracy ~1e-6 against the F64 force.  STG_ERR_ARG for any other prec. */
@@ -308,7 +340,7 @@ stg_status stg_fermion_force_prec(const stg_gauge *g_f64, stg_prec prec, int32_t
  * from the Taylor series of exp reduced by the Cayley-Hamilton identity Q^3 = c1 Q + c0
  * (c0 = det Q, c1 = tr Q^2 / 2) to the precision's accuracy.
  * prec STG_F64: complex128 arrays, FP64 arithmetic; STG_F32: complex64 arrays, FP32 arithmetic
- * (the molecular dynamics runs in single precision, Sec. 5.3).
+ * (the molecular dynamics runs in single precision, Sec. 5.4).
  * links_dev: canonical [4][V][3][3] U^(0) (device, read only);
  * levels_dev: nstep consecutive canonical arrays U^(1) .. U^(nstep) (device, written).
  * 1 <= nstep <= 16, |rho| <= 0.5 (larger rho is refused: the series would cancel digits);
@@ -351,7 +383,7 @@ stg_status stg_gauge_action(const stg_lattice *lat, double beta, const void *lin
  * through the link (B = the rest of the loop after the link; 2 plaquettes and 6 rectangles per
  * other direction), written as kind 1: G, or kind 0: F = TA(U G^dag) (dS/deps = tr(X F) along
  * U -> exp(eps X) U).  prec STG_F64: complex128 arrays, FP64; STG_F32: complex64 arrays, FP32 (the
- * single-precision MD, Sec. 5.3).  links_dev / out_dev: canonical [4][V][3][3] (device), no
+ * single-precision MD, Sec. 5.4).  links_dev / out_dev: canonical [4][V][3][3] (device), no
  * aliasing.  Async on `stream`. */
 stg_status stg_gauge_force(const stg_lattice *lat, stg_prec prec, double beta, const void *links_dev, void *out_dev,
                            int32_t kind, void *stream);

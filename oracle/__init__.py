@@ -195,10 +195,13 @@ def force(dims, links, residues, x, kind: int = 0, antiperiodic: bool = True) ->
     return out
 
 
-def action(residues, b, x) -> float:
-    """S = sum_i r_i Re(b^dag x_i)."""
+def action(residues, b, x, alpha0: float = 0.0) -> float:
+    """S = alpha0 |b|^2 + sum_i r_i Re(b^dag x_i) (Sec. 2: the pseudofermion action b^dag R(A) b with
+    the rational function R written as a constant plus poles, x_i the solutions of the shifted
+    systems)."""
     b = np.asarray(b).reshape(-1)
-    return float(sum(r * np.vdot(b, np.asarray(xi).reshape(-1)).real for r, xi in zip(residues, x)))
+    s = alpha0 * np.vdot(b, b).real
+    return float(s + sum(r * np.vdot(b, np.asarray(xi).reshape(-1)).real for r, xi in zip(residues, x)))
 
 
 def u1_links(links, theta) -> np.ndarray:

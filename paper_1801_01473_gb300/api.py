@@ -319,6 +319,22 @@ def rational_apply(g_f64: Gauge, b: torch.Tensor, alpha0: float, residues, poles
     return out, _stats_dict(st, tr, si)
 
 
+def pseudofermion_action_value(lattice: Lattice, b: torch.Tensor, x: torch.Tensor, residues, alpha0: float = 0.0,
+                         stream=None) -> float:
+    """S = alpha0 |b|^2 + sum_i residues[i] Re(b^dag x_i) (stg_pseudofermion_action): b canonical
+    complex128 [Vh, 3], x [nshift, Vh, 3] (e.g. the output of mscg).  Synchronises to read S."""
+    bb = _dev(b).reshape(lattice.Vh, 3)
+    res = [float(r) for r in residues]
+    n = len(res)
+    xs = _dev(x).reshape(n, lattice.Vh, 3) if n else None
+    xp = (ctypes.c_void_p * max(n, 1))(*[xs[i].data_ptr() for i in range(n)])
+    rp = (ctypes.c_double * max(n, 1))(*res)
+    out = torch.empty(1, dtype=torch.float64, device="cuda")
+    check(lib().stg_pseudofermion_action(lattice.handle, n, float(alpha0), rp, _ptr(bb), xp, _ptr(out),
+                                         _stream(stream)), "stg_pseudofermion_action")
+    return float(_to_host(out)[0])
+
+
 def mscg_batched(instances, shifts, mass: float, tol: float = 1e-10, max_iter: int = 20000, inner_tol: float = 0.0,
                  reliable_delta: float = 0.0, history: int = 0, stream=None):
     """instances: list of (g_f64, g_inner or None, [b_r canonical [Vh,3] cuda tensors]).

@@ -1,7 +1,7 @@
 """The pseudofermion action as a differentiable torch function.
 
 S(U) = sum_i r_i Re(b^dag x_i),  x_i = (m^2 + sigma_i - D_eo D_oe)^-1 b  (Eq. shift_eo).
-forward runs the multi-shift CG (libstg); backward runs the hand-written
+forward runs the multi-shift CG and the action's reduction (libstg); backward runs the hand-written
 adjoint kernel (stg_fermion_force, kind 1), which returns W^dag per link:
 the gradient in torch's convention for a real loss of complex inputs,
 dS/dRe U + i dS/dIm U, since dS = Re tr(dU W).
@@ -10,7 +10,7 @@ from __future__ import annotations
 
 import torch
 
-from .api import Gauge, Lattice, fermion_force, mscg, stout_force, stout_smear
+from .api import Gauge, Lattice, fermion_force, mscg, pseudofermion_action_value as _action, stout_force, stout_smear
 
 
 class PseudofermionAction(torch.autograd.Function):
@@ -18,7 +18,7 @@ class PseudofermionAction(torch.autograd.Function):
     def forward(ctx, links, b, lattice: Lattice, shifts, residues, mass: float, tol: float = 1e-12):
         g = Gauge(lattice, links.detach(), "f64", 18)
         x, _ = mscg(g, b.detach(), shifts, mass, tol=tol)
-        s = sum(float(r) * torch.vdot(b.detach().reshape(-1), x[i].reshape(-1)).real for i, r in enumerate(residues))
+        s = _action(lattice, b.detach(), x, residues)
         ctx.save_for_backward(x)
         ctx.gauge = g
         ctx.residues = list(residues)

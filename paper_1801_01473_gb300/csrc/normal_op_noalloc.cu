@@ -15,9 +15,10 @@
 
 namespace stg {
 
-// Fixed scratch for every call on a device: holds the odd temporary (48 B per site for F64
-// gauges, 24 B for the others) and one double per 64 sites.  32 MiB covers a 32^4 lattice at
-// FP64 (25.2 MB + 64 KB).  Every GPU that loads the library holds it until the process exits.
+// Fixed scratch for every call on a device: holds the odd temporary (48 B per site for F64 and
+// double-single gauges, 24 B for the F32/BF16/F16 ones) and one double per 64 sites.  32 MiB
+// covers a 32^4 lattice at FP64 (25.2 MB + 64 KB).  Every GPU that loads the library holds it
+// until the process exits.
 constexpr size_t kStaticScratchBytes = 32u << 20;
 static __device__ __align__(256) unsigned char g_static_scratch[kStaticScratchBytes];
 
@@ -67,8 +68,13 @@ extern "C" stg_status stg_normal_op_noalloc(const stg_gauge *g, double mass, dou
     if (!g || !out_even_dev || !in_even_dev) return set_error(STG_ERR_ARG, "stg_normal_op_noalloc: null pointer");
     if ((reinterpret_cast<uintptr_t>(out_even_dev) & 15) || (reinterpret_cast<uintptr_t>(in_even_dev) & 15))
         return set_error(STG_ERR_ARG, "stg_normal_op_noalloc: pointers must be 16-byte aligned");
-    if (out_even_dev == in_even_dev) return set_error(STG_ERR_ARG, "stg_normal_op_noalloc: in and out must differ");
     const int Vh = g->g.Vh;
+    {
+        // any overlap of the two fields: the fused D_eo epilogue reads in while it writes out
+        const uintptr_t i0 = reinterpret_cast<uintptr_t>(in_even_dev), o0 = reinterpret_cast<uintptr_t>(out_even_dev);
+        const uintptr_t n = (uintptr_t)Vh * (uintptr_t)kind_vec_bytes(g->kind);
+        if (i0 < o0 + n && o0 < i0 + n) return set_error(STG_ERR_ARG, "stg_normal_op_noalloc: in and out overlap");
+    }
     const size_t tmp_bytes = ((size_t)Vh * kind_vec_bytes(g->kind) + 255) & ~(size_t)255;
     const size_t part_bytes = sizeof(double) * (size_t)dslash_partials(Vh);
     if (tmp_bytes + part_bytes > kStaticScratchBytes)

@@ -25,7 +25,8 @@ EXPORTS = [
     "stg_gauge_create", "stg_gauge_create_u1", "stg_gauge_update", "stg_gauge_destroy", "stg_gauge_bytes",
     "stg_field_bytes", "stg_field_pack", "stg_field_unpack",
     "stg_dslash", "stg_dslash_eo", "stg_dslash_oe", "stg_dslash_multi", "stg_dslash_host", "stg_normal_op", "stg_normal_op_noalloc",
-    "stg_mscg_solve", "stg_mscg_solve_batched", "stg_rational_apply", "stg_fermion_force", "stg_fermion_force_prec",
+    "stg_mscg_solve", "stg_mscg_solve_batched", "stg_rational_apply", "stg_pseudofermion_action",
+    "stg_fermion_force", "stg_fermion_force_prec",
     "stg_stout_smear", "stg_stout_force", "stg_gauge_action", "stg_gauge_force",
     "stg_md_momenta", "stg_md_update_links", "stg_md_update_momenta", "stg_md_kinetic", "stg_complex_convert",
 ]
@@ -99,6 +100,7 @@ def lib() -> ctypes.CDLL:
     L.stg_fermion_force.argtypes = [P, I32, ctypes.POINTER(D), PP, P, I32, P]
     L.stg_rational_apply.argtypes = [P, P, ctypes.POINTER(MscgParams), D, ctypes.POINTER(D), P, P,
                                      ctypes.POINTER(MscgStats), P]
+    L.stg_pseudofermion_action.argtypes = [P, I32, D, ctypes.POINTER(D), P, PP, P, P]
     L.stg_stout_smear.argtypes = [P, ctypes.c_int, I32, D, P, P, P]
     L.stg_stout_force.argtypes = [P, ctypes.c_int, I32, D, P, P, P, P, I32, P]
     L.stg_gauge_action.argtypes = [P, D, P, P, P]
@@ -117,7 +119,7 @@ def lib() -> ctypes.CDLL:
         if f.restype is ctypes.c_int or name in ("stg_lattice_create", "stg_gauge_create", "stg_field_pack",
                                                  "stg_field_unpack", "stg_dslash_eo", "stg_dslash_oe",
                                                  "stg_dslash_multi", "stg_dslash_host", "stg_normal_op", "stg_normal_op_noalloc", "stg_mscg_solve",
-                                                 "stg_mscg_solve_batched", "stg_rational_apply", "stg_fermion_force",
+                                                 "stg_mscg_solve_batched", "stg_rational_apply", "stg_pseudofermion_action", "stg_fermion_force",
                                                  "stg_stout_smear", "stg_stout_force", "stg_gauge_action",
                                                  "stg_gauge_force", "stg_gauge_create_u1", "stg_gauge_update", "stg_fermion_force_prec", "stg_dslash", "stg_md_momenta", "stg_md_update_links",
                                                  "stg_md_update_momenta", "stg_md_kinetic", "stg_complex_convert"):

@@ -2,13 +2,14 @@
 accept/reject step; Sec. 3: each MD iteration computes the forces, evolves the momenta, then
 the links).  Host-side sequencing only: every arithmetic step is a libstg kernel (gauge action and
 force, stout smearing and its chain rule, multi-shift CG, fermion force, the MD link/momentum
-updates and the kinetic energy).
+updates, the kinetic energy and the pseudofermion action); Python only adds the few resulting
+scalars of the Hamiltonian and takes the Metropolis decision.
 
 The fermion part is S_f = sum_pf sum_i r_i Re(b^dag x_i), x_i = (m^2 + sigma_i - D_eo D_oe)^-1 b
 on the k-times stout-smeared links (the pole part of the rational approximation; a constant
 term has no force).  Forces are Lie-algebra forces F = TA(U G^dag) on the unsmeared links.
 
-precision "f32" runs the molecular dynamics in single precision as Sec. 5.3 does: the gauge force,
+precision "f32" runs the molecular dynamics in single precision as Sec. 5.4 does: the gauge force,
 the stout smearing and its chain rule on complex64 copies of the links (GB300 issues FP32 ~64x
 faster than FP64), the fermion solve with the mixed solver on the smeared links; the MD state
 (links, momenta) and its updates stay FP64, and the Hamiltonian of the Metropolis test is FP64.
@@ -22,7 +23,8 @@ from typing import Sequence
 import torch
 
 from .api import (Gauge, Lattice, complex_convert, fermion_force, gauge_action, gauge_force, md_kinetic, md_momenta,
-                  md_update_links_, md_update_momenta_, mscg, mscg_batched, rational_apply, stout_force, stout_smear)
+                  md_update_links_, md_update_momenta_, mscg, mscg_batched, pseudofermion_action_value, rational_apply,
+                  stout_force, stout_smear)
 
 # Omelyan's second-order minimum-norm parameter
 OMELYAN_LAMBDA = 0.1931833275037836
@@ -112,9 +114,7 @@ class Action:
             _, uk = self._smeared(links)
             g64, gi = self._gauges(uk)
             for pf, x in zip(self.pseudofermions, self._solve_all(g64, gi, self.tol)):
-                bb = pf.b.reshape(-1)
-                s += float(pf.alpha0) * float(torch.vdot(bb, bb).real)
-                s += sum(float(r) * float(torch.vdot(bb, x[i].reshape(-1)).real) for i, r in enumerate(pf.residues))
+                s += pseudofermion_action_value(self.lattice, pf.b, x, pf.residues, pf.alpha0)
         return s
 
     def apply_force(self, links: torch.Tensor, mom: torch.Tensor, eps: float) -> None:

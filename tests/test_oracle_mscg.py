@@ -171,3 +171,20 @@ def test_refinement_branch_finishes_capped_shifts(small):
         xd = _dense_solution(small, i)
         kappa = (ev.max() + s) / (ev.min() + s)
         assert np.linalg.norm(x - xd) / np.linalg.norm(xd) <= kappa * tol, i
+
+
+def test_action_equals_spectral_rational_function(small):
+    """oracle.action with the msCG solutions equals b^dag R(A) b computed from the eigenvectors of
+    the dense 4^4 operator, R(l) = alpha0 + sum_i r_i / (l + sigma_i) (Sec. 2's rational form)."""
+    a, b = small["a"], small["b"].reshape(-1)
+    lam, vec = np.linalg.eigh(a)
+    c2 = np.abs(vec.conj().T @ b) ** 2
+    res = S.positive_residues(3001, len(small["shifts"]))
+    alpha0 = 0.21
+    want = float(np.sum(c2 * (alpha0 + sum(r / (lam + s) for r, s in zip(res, small["shifts"])))))
+    got = oracle.action(res, small["b"], small["res"]["x"], alpha0=alpha0)
+    ev = lam.min() + small["shifts"].min()
+    assert abs(got - want) <= 1e-9 * abs(want) + small["tol"] * np.linalg.norm(b) ** 2 / ev, (got, want)
+    # the residue-weighted terms alone: a sign flip of Re(b^dag x) or a dropped residue fails
+    got0 = oracle.action(res, small["b"], small["res"]["x"])
+    assert abs(got0 - (want - alpha0 * np.sum(c2))) <= 1e-8 * abs(want)

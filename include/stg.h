@@ -413,6 +413,83 @@ stg_status stg_complex_convert(int64_t count, stg_prec src_prec, const void *src
 /* *out_dev (one device double) = (1/2) sum_links tr H^2, summed in a fixed order. */
 stg_status stg_md_kinetic(const stg_lattice *lat, const void *mom_c128_dev, double *out_dev, void *stream);
 
+/* ---- one-dimensional slab decomposition along t (Sec. 3.1, Sec. 4.1, Sec. 4.2, Alg. 1) ----------
+ * The paper tiles the lattice along one direction only: every process holds whole x-y-z volumes of a
+ * range of time slices, so that the data it exchanges with its two neighbours are contiguous time
+ * slices (no gather or scatter), and D needs one halo slice of the input field on each side.  Here a
+ * process (one GPU) holds global slices [t0, t0 + Lt_loc) of a Lx x Ly x Lz x Lt_global lattice.  Its
+ * fields and links are stored over Lt_loc + 4 time slices in the usual layouts: the local slices at
+ * stored slices 2 .. Lt_loc + 1, the lower neighbour's last slice at stored slice 1, the upper
+ * neighbour's first slice at stored slice Lt_loc + 2 (the halos), and stored slices 0 and Lt_loc + 3
+ * as padding that keeps the stored parity equal to the global one.  The caller moves the halos
+ * (stg_slab_layout gives the byte ranges; the Python binding does it over torch.distributed); the
+ * library computes.  No device code waits on another process. */
+
+/* A slab lattice.  dims_local = {Lx, Ly, Lz, Lt_loc}, all even and >= 2; t0 even, Lt_global even,
+ * t0 + Lt_loc <= Lt_global.  The antiperiodic sign sits on the t-links at global time
+ * Lt_global - 1.  stg_lattice_sites and stg_field_bytes count stored sites (halos included);
+ * stg_field_pack / unpack and stg_gauge_create / update take stored canonical arrays (the links of
+ * stored slice 1 must hold the lower neighbour's, of which D reads the t-links).  On a slab,
+ * stg_dslash / _eo / _oe / _multi and the stg_slab_* calls write the local slices only and read the
+ * input's halo slices; every other entry point returns STG_ERR_SHAPE. */
+stg_status stg_lattice_create_slab(const int32_t dims_local[4], int32_t t0, int32_t Lt_global, int32_t t_antiperiodic,
+                                   stg_lattice **out);
+/* Byte layout of a slab field of vector precision vec_prec (F64, DS or F32), for the halo exchange:
+ * the internal field is *nchunk arrays, array k starting at byte offset[k] of the field with
+ * elem_bytes[k] bytes per site, and stored time slice s of the parity occupying sites
+ * [s * slice_sites, (s + 1) * slice_sites) of every array (time is the slowest coordinate), i.e.
+ * bytes offset[k] + elem_bytes[k] * [s * slice_sites, (s + 1) * slice_sites).  Exchange: stored slice
+ * 2 goes to the lower neighbour's stored slice Lt_loc + 2, stored slice Lt_loc + 1 to the upper
+ * neighbour's stored slice 1 (neighbours wrap around: the time direction is closed).  Host only. */
+stg_status stg_slab_layout(const stg_lattice *lat, stg_prec vec_prec, int32_t *nchunk, int64_t offset[3],
+                           int32_t elem_bytes[3], int64_t *slice_sites);
+
+/* out = coef p - D in on the output sites (the local slices of a slab, every site of a full
+ * lattice): D_eo for out_parity 0, D_oe for 1 (the second half of Eq. shift_eo's operator, with
+ * coef = m^2 + sigma).  pq_dev != NULL receives this process's part of Re<p, out> (FP64, fixed
+ * order).  Fields in the gauge's internal layout; in's halo slices must be current.  Uses the
+ * gauge's partial-sum buffer (concurrent calls on one gauge race, as for stg_normal_op). */
+stg_status stg_slab_dslash_xpay(const stg_gauge *g, int32_t out_parity, double coef, void *out_dev, const void *in_dev,
+                                const void *p_dev, double *pq_dev, void *stream);
+/* y += alpha x on the output sites (the local slices of a slab), fields of vector precision
+ * vec_prec F64 or F32 in the internal layout of lat; norm2_dev != NULL receives this process's
+ * part of |y|^2 after the update (FP64, fixed order).  Takes a workspace of one double per 256
+ * sites from the stream-ordered allocator. */
+stg_status stg_slab_axpy_norm(const stg_lattice *lat, stg_prec vec_prec, double alpha, const void *x_dev, void *y_dev,
+                              double *norm2_dev, void *stream);
+/* The multi-shift update of the solutions and search directions (Sec. 2) on the output sites:
+ * for i < n, x_i += cx[i] p_i if upd_x[i], then p_i = cr[i] r + cp[i] p_i if upd_p[i]; host arrays
+ * of n <= 32 coefficients and flags, device pointers x[i], p[i], r in the internal layout
+ * (vec_prec F64 or F32). */
+stg_status stg_slab_shift_update(const stg_lattice *lat, stg_prec vec_prec, int32_t n, const double *cx,
+                                 const double *cr, const double *cp, const int32_t *upd_x, const int32_t *upd_p,
+                                 void *const *x_dev, void *const *p_dev, const void *r_dev, void *stream);
+
+/* Host-side scalar recurrences of the multi-shift CG (Sec. 2, Eq. shift_eo; the shifted CG of
+ * Jegerlehner) for a driver that sums its reductions over processes itself: base shift
+ * sigma_0 = min sigma_i, relative shifts s_i = sigma_i - sigma_0, and per iteration
+ *   stg_mscg_state_alpha with Re<p, q> (summed over processes):  alpha = |r|^2 / Re<p, q>,
+ *     zeta_i' = zeta_i zeta_i_old alpha_old / (alpha beta_old (zeta_i_old - zeta_i)
+ *                                              + zeta_i_old alpha_old (1 + s_i alpha)),
+ *     cx_i = alpha zeta_i' / zeta_i  (x_i += cx_i p_i);
+ *   stg_mscg_state_beta with |r|^2 after r -= alpha q:  beta = |r|^2_new / |r|^2,
+ *     cr_i = zeta_i', cp_i = beta (zeta_i' / zeta_i)^2  (p_i = cr_i r + cp_i p_i), the stop test
+ *     zeta_i' |r| <= tol |b| per shift, the base direction kept while any shift runs, and the
+ *     history rotation; state.running = 0 once every shift has stopped or max_iter is reached.
+ * Plain FP64 host arithmetic, no GPU needed.  STG_ERR_ARG on a NULL state, nshift outside 1..32,
+ * a negative shift, or a step called out of order. */
+typedef struct {
+    int32_t nshift, i0, iters, max_iter, running, nactive, phase;  /* phase 0: alpha next, 1: beta next */
+    double s[32], zeta[32], zeta_old[32], zeta_new[32];
+    double alpha, alpha_old, beta_old, rr, tol2;
+    double cx[32], cr[32], cp[32];
+    int32_t active[32], upd_x[32], upd_p[32], shift_iters[32];
+} stg_mscg_state;
+stg_status stg_mscg_state_init(stg_mscg_state *st, int32_t nshift, const double *shifts, double tol, double bnorm2,
+                               int32_t max_iter);
+stg_status stg_mscg_state_alpha(stg_mscg_state *st, double pq);
+stg_status stg_mscg_state_beta(stg_mscg_state *st, double rr_new);
+
 #ifdef __cplusplus
 }
 #endif

@@ -57,6 +57,26 @@ class Lattice:
         self.V = int(lib().stg_lattice_sites(h, -1))
         self.Vh = int(lib().stg_lattice_sites(h, 0))
 
+    @classmethod
+    def slab(cls, dims_local: Sequence[int], t0: int, lt_global: int, antiperiodic: bool = True) -> "Lattice":
+        """The slab of global time slices [t0, t0 + Lt_loc) of a lattice split along t
+        (stg_lattice_create_slab): stored with two halo-side slices below and above."""
+        self = cls.__new__(cls)
+        dl = tuple(int(d) for d in dims_local)
+        arr = (ctypes.c_int32 * 4)(*dl)
+        h = ctypes.c_void_p()
+        check(lib().stg_lattice_create_slab(arr, int(t0), int(lt_global), int(bool(antiperiodic)), ctypes.byref(h)),
+              "stg_lattice_create_slab")
+        self._h = h
+        self.antiperiodic = bool(antiperiodic)
+        self.dims = (dl[0], dl[1], dl[2], dl[3] + 4)  # stored extents
+        self.dims_local = dl
+        self.t0 = int(t0)
+        self.lt_global = int(lt_global)
+        self.V = int(lib().stg_lattice_sites(h, -1))
+        self.Vh = int(lib().stg_lattice_sites(h, 0))
+        return self
+
     @property
     def handle(self):
         return self._h

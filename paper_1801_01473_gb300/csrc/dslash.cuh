@@ -121,7 +121,7 @@ __device__ __forceinline__ void dslash_epilogue(const DGroup &G, const bool act[
             __syncthreads();
             constexpr int kChunks = BS / kPartialSites;
             const int c = blockIdx.x * kChunks + threadIdx.x;
-            if (threadIdx.x < kChunks && c < dslash_partials(Vh))
+            if (threadIdx.x < kChunks && c < dslash_partials(G.g.h_end - G.g.h_begin))
                 G.partial[j][c] = sh[2 * threadIdx.x] + sh[2 * threadIdx.x + 1];
         }
     }
@@ -134,7 +134,8 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
     pdl_enter();
     const DGroup &G = a.grp[blockIdx.y];
     const int Vh = G.g.Vh;
-    if ((int)(blockIdx.x * BS) >= Vh) return;  // block-uniform
+    const int nout = G.g.h_end - G.g.h_begin;
+    if ((int)(blockIdx.x * BS) >= nout) return;  // block-uniform
 
     bool act[NRHS];
     bool any = false;
@@ -145,8 +146,8 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
     }
     if (!any) return;  // block-uniform
 
-    const int h = blockIdx.x * BS + threadIdx.x;
-    const bool live = h < Vh;
+    const int h = G.g.h_begin + blockIdx.x * BS + threadIdx.x;
+    const bool live = h < G.g.h_end;
     const int op = a.out_par;
 
     cx<R> acc[NRHS][3];
@@ -290,13 +291,15 @@ __global__ void __launch_bounds__(512) k_dslash_sh(const __grid_constant__ DArgs
     pdl_enter();
     const DGroup &G = a.grp[blockIdx.y];
     const int Vh = G.g.Vh;
-    const int h0 = blockIdx.x * kShSites;
-    if (h0 >= Vh) return;  // block-uniform
+    const int nout = G.g.h_end - G.g.h_begin;
+    if ((int)(blockIdx.x * kShSites) >= nout) return;  // block-uniform
+    const int h0 = G.g.h_begin + blockIdx.x * kShSites;
+    const int hend = G.g.h_end;
     const int op = a.out_par;
     // stage the links: hop k = 2 mu (forward) or 2 mu + 1 (backward) of site s
     for (int t = threadIdx.x; t < 8 * kShSites; t += blockDim.x) {
         const int k = t / kShSites, sl = t - k * kShSites, h = h0 + sl;
-        if (h >= Vh) continue;
+        if (h >= hend) continue;
         const int mu = k >> 1;
         const Hop hp = hop_of(G.g, site_of(G.g, op, h), mu);
         cx<R> U[3][3];
@@ -322,7 +325,7 @@ __global__ void __launch_bounds__(512) k_dslash_sh(const __grid_constant__ DArgs
     const int sl = ((warp & 1) << 5) + (threadIdx.x & 31);
     const int h = h0 + sl;
     const bool act = j < G.nrhs && !(G.skip[j] != nullptr && *G.skip[j] != 0);  // warp-uniform
-    const bool live = act && h < Vh;
+    const bool live = act && h < hend;
     ProdSum<R> part;
     if (live) {
         cx<R> acc[3];
@@ -451,7 +454,8 @@ inline void dslash_extent(const DArgs &a, int &maxv, int &maxr)
     maxv = 0;
     maxr = 0;
     for (int k = 0; k < a.ngroups; ++k) {
-        if (a.grp[k].g.Vh > maxv) maxv = a.grp[k].g.Vh;
+        const int nout = a.grp[k].g.h_end - a.grp[k].g.h_begin;  // output sites of the group
+        if (nout > maxv) maxv = nout;
         if (a.grp[k].nrhs > maxr) maxr = a.grp[k].nrhs;
     }
 }

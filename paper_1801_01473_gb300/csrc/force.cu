@@ -394,6 +394,8 @@ static stg_status force_f32(const stg_gauge *g, int32_t nshift, const double *re
 extern "C" stg_status stg_fermion_force_prec(const stg_gauge *g, stg_prec prec, int32_t nshift, const double *residues,
                                              const void *const *x_c128_dev, void *out_dev, int32_t kind, void *stream)
 {
+    if (g && stg::geom_is_slab(g->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_fermion_force_prec: not available on a slab lattice (stg_dslash* only)");
     if (prec == STG_F64) return stg_fermion_force(g, nshift, residues, x_c128_dev, out_dev, kind, stream);
     if (prec != STG_F32) return set_error(STG_ERR_ARG, "stg_fermion_force_prec: prec must be F64 or F32");
     if (!g || !residues || !x_c128_dev || !out_dev) return set_error(STG_ERR_ARG, "stg_fermion_force_prec: null pointer");
@@ -411,6 +413,8 @@ extern "C" stg_status stg_fermion_force_prec(const stg_gauge *g, stg_prec prec, 
 extern "C" stg_status stg_fermion_force(const stg_gauge *g, int32_t nshift, const double *residues,
                                         const void *const *x_c128_dev, void *out_c128_dev, int32_t kind, void *stream)
 {
+    if (g && stg::geom_is_slab(g->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_fermion_force: not available on a slab lattice (stg_dslash* only)");
     if (!g || !residues || !x_c128_dev || !out_c128_dev) return set_error(STG_ERR_ARG, "stg_fermion_force: null pointer");
     if (!kind_is_f64(g->kind)) return set_error(STG_ERR_ARG, "stg_fermion_force: needs an F64 gauge");
     if (nshift < 1 || nshift > kMaxShifts) return set_error(STG_ERR_ARG, "stg_fermion_force: nshift must be in 1..32");

@@ -225,6 +225,8 @@ static cudaError_t gauge_force_t(const stg_lattice *lat, double beta, const void
 extern "C" stg_status stg_gauge_force(const stg_lattice *lat, stg_prec prec, double beta, const void *links_dev,
                                       void *out_dev, int32_t kind, void *stream)
 {
+    if (lat && stg::geom_is_slab(lat->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_gauge_force: not available on a slab lattice (stg_dslash* only)");
     if (!lat) return set_error(STG_ERR_ARG, "stg_gauge_force: null lattice");
     if (prec != STG_F64 && prec != STG_F32) return set_error(STG_ERR_ARG, "stg_gauge_force: prec must be F64 or F32");
     if (misaligned(links_dev) || misaligned(out_dev))
@@ -241,6 +243,8 @@ extern "C" stg_status stg_gauge_force(const stg_lattice *lat, stg_prec prec, dou
 extern "C" stg_status stg_gauge_action(const stg_lattice *lat, double beta, const void *links_c128_dev, double *out3_dev,
                                        void *stream)
 {
+    if (lat && stg::geom_is_slab(lat->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_gauge_action: not available on a slab lattice (stg_dslash* only)");
     if (!lat) return set_error(STG_ERR_ARG, "stg_gauge_action: null lattice");
     if (misaligned(links_c128_dev)) return set_error(STG_ERR_ARG, "stg_gauge_action: links must be non-null and 16-byte aligned");
     if (!out3_dev || (reinterpret_cast<uintptr_t>(out3_dev) & 7))

@@ -68,6 +68,8 @@ using namespace stg;
 extern "C" stg_status stg_dslash_host(const stg_gauge *g, int32_t out_parity, stg_prec host_prec, int32_t nfield,
                                       const void *const *in_host, void *const *out_host, void *stream)
 {
+    if (g && stg::geom_is_slab(g->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_dslash_host: not available on a slab lattice (stg_dslash* only)");
     if (host_prec != STG_F64 && host_prec != STG_F32)
         return set_error(STG_ERR_ARG, "stg_dslash_host: host fields must be F64 (complex128) or F32 (complex64)");
     if (!g || (nfield > 0 && (!in_host || !out_host)))

@@ -177,6 +177,8 @@ using namespace stg;
 
 extern "C" stg_status stg_md_momenta(const stg_lattice *lat, const double *xi_dev, void *mom_c128_dev, void *stream)
 {
+    if (lat && stg::geom_is_slab(lat->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_md_momenta: not available on a slab lattice (stg_dslash* only)");
     if (!lat || !xi_dev || (reinterpret_cast<uintptr_t>(xi_dev) & 7) || bad(mom_c128_dev))
         return set_error(STG_ERR_ARG, "stg_md_momenta: null or misaligned pointer");
     MdArgs a = md_args(lat);
@@ -190,6 +192,8 @@ extern "C" stg_status stg_md_momenta(const stg_lattice *lat, const double *xi_de
 extern "C" stg_status stg_md_update_links(const stg_lattice *lat, double eps, const void *mom_c128_dev,
                                           void *links_c128_dev, void *stream)
 {
+    if (lat && stg::geom_is_slab(lat->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_md_update_links: not available on a slab lattice (stg_dslash* only)");
     if (!lat || bad(mom_c128_dev) || bad(links_c128_dev))
         return set_error(STG_ERR_ARG, "stg_md_update_links: null or misaligned pointer");
     if (mom_c128_dev == links_c128_dev) return set_error(STG_ERR_ARG, "stg_md_update_links: momenta alias the links");
@@ -207,6 +211,8 @@ extern "C" stg_status stg_md_update_links(const stg_lattice *lat, double eps, co
 extern "C" stg_status stg_md_update_momenta(const stg_lattice *lat, stg_prec force_prec, double eps,
                                             const void *force_dev, void *mom_c128_dev, void *stream)
 {
+    if (lat && stg::geom_is_slab(lat->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_md_update_momenta: not available on a slab lattice (stg_dslash* only)");
     if (!lat || bad(force_dev) || bad(mom_c128_dev))
         return set_error(STG_ERR_ARG, "stg_md_update_momenta: null or misaligned pointer");
     if (force_prec != STG_F64 && force_prec != STG_F32)
@@ -248,6 +254,8 @@ extern "C" stg_status stg_complex_convert(int64_t count, stg_prec src_prec, cons
 
 extern "C" stg_status stg_md_kinetic(const stg_lattice *lat, const void *mom_c128_dev, double *out_dev, void *stream)
 {
+    if (lat && stg::geom_is_slab(lat->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_md_kinetic: not available on a slab lattice (stg_dslash* only)");
     if (!lat || bad(mom_c128_dev) || !out_dev || (reinterpret_cast<uintptr_t>(out_dev) & 7))
         return set_error(STG_ERR_ARG, "stg_md_kinetic: null or misaligned pointer");
     cudaStream_t st = (cudaStream_t)stream;

@@ -65,6 +65,8 @@ using namespace stg;
 extern "C" stg_status stg_normal_op_noalloc(const stg_gauge *g, double mass, double shift, void *out_even_dev,
                                             const void *in_even_dev, double *pq_dev, void *stream)
 {
+    if (g && stg::geom_is_slab(g->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_normal_op_noalloc: not available on a slab lattice (stg_dslash* only)");
     if (!g || !out_even_dev || !in_even_dev) return set_error(STG_ERR_ARG, "stg_normal_op_noalloc: null pointer");
     if ((reinterpret_cast<uintptr_t>(out_even_dev) & 15) || (reinterpret_cast<uintptr_t>(in_even_dev) & 15))
         return set_error(STG_ERR_ARG, "stg_normal_op_noalloc: pointers must be 16-byte aligned");

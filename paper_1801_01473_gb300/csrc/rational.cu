@@ -91,6 +91,8 @@ extern "C" stg_status stg_pseudofermion_action(const stg_lattice *lat, int32_t n
                                                const double *residues, const void *b_c128_dev,
                                                const void *const *x_c128_dev, double *s_dev, void *stream)
 {
+    if (lat && stg::geom_is_slab(lat->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_pseudofermion_action: not available on a slab lattice (stg_dslash* only)");
     if (!lat || !b_c128_dev || !s_dev || (nshift > 0 && (!residues || !x_c128_dev)))
         return set_error(STG_ERR_ARG, "stg_pseudofermion_action: null pointer");
     if (nshift < 0 || nshift > kMaxShifts)
@@ -128,6 +130,8 @@ extern "C" stg_status stg_rational_apply(const stg_gauge *g_f64, const stg_gauge
                                          double alpha0, const double *residues, const void *b_c128_dev,
                                          void *out_c128_dev, stg_mscg_stats *stats, void *stream)
 {
+    if (g_f64 && stg::geom_is_slab(g_f64->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_rational_apply: not available on a slab lattice (stg_dslash* only)");
     if (!g_f64 || !params || !residues || !b_c128_dev || !out_c128_dev)
         return set_error(STG_ERR_ARG, "stg_rational_apply: null pointer");
     if (params->nshift < 1 || params->nshift > kMaxShifts)

@@ -1470,6 +1470,9 @@ static stg_status validate(int ninst, const stg_instance *inst, const stg_mscg_p
 {
     if (!inst || !prm) return set_error(STG_ERR_ARG, "stg_mscg_solve: null pointer");
     if (ninst < 1 || ninst > 16) return set_error(STG_ERR_ARG, "stg_mscg_solve: ninst must be in 1..16");
+    for (int k = 0; k < ninst; ++k)
+        if (inst[k].g_f64 && geom_is_slab(inst[k].g_f64->g))
+            return set_error(STG_ERR_SHAPE, "stg_mscg_solve: not available on a slab lattice (see slab.py)");
     if (prm->nshift < 1 || prm->nshift > kMaxShifts || !prm->shifts)
         return set_error(STG_ERR_ARG, "stg_mscg_solve: nshift must be in 1..32 with a shifts array");
     for (int i = 0; i < prm->nshift; ++i)

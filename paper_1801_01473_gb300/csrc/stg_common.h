@@ -19,6 +19,9 @@ constexpr int kU1 = 8;
 inline int base_kind(int kind) { return kind & 7; }
 inline bool kind_has_u1(int kind) { return (kind & kU1) != 0; }
 
+// A slab lattice (stg_lattice_create_slab): halo time slices around the interior outputs.
+inline bool geom_is_slab(const Geom &g) { return g.h_begin != 0 || g.h_end != g.Vh || g.t_off != 0; }
+
 int link_bytes(int kind);
 inline bool kind_is_f64(int kind) { return base_kind(kind) == kF64R18 || base_kind(kind) == kF64R12; }
 inline bool kind_is_ds(int kind) { return base_kind(kind) == kDSR18 || base_kind(kind) == kDSR12; }

@@ -548,6 +548,60 @@ stg_status stg_lattice_create(const int32_t dims[4], int32_t t_antiperiodic, stg
     return STG_OK;
 }
 
+stg_status stg_lattice_create_slab(const int32_t dims_local[4], int32_t t0, int32_t Lt_global, int32_t t_antiperiodic,
+                                   stg_lattice **out)
+{
+    if (!dims_local || !out) return set_error(STG_ERR_ARG, "stg_lattice_create_slab: null pointer");
+    *out = nullptr;
+    for (int k = 0; k < 4; ++k)
+        if (dims_local[k] < 2 || (dims_local[k] & 1))
+            return set_error(STG_ERR_SHAPE, "stg_lattice_create_slab: every local extent must be even and >= 2");
+    if ((t0 & 1) || t0 < 0 || Lt_global < 2 || (Lt_global & 1) || t0 + dims_local[3] > Lt_global)
+        return set_error(STG_ERR_SHAPE, "stg_lattice_create_slab: need t0 even, Lt_global even and "
+                                        "0 <= t0, t0 + Lt_loc <= Lt_global");
+    // stored lattice: the local slices plus two halo-side slices below and above (the inner one of
+    // each pair holds the neighbour's border; the outer one keeps the stored parity equal to the
+    // global one, since stored slice 0 then sits at the even global time t0 - 2)
+    const int32_t ext[4] = {dims_local[0], dims_local[1], dims_local[2], dims_local[3] + 4};
+    stg_status st = stg_lattice_create(ext, t_antiperiodic, out);
+    if (st != STG_OK) return st;
+    Geom &g = (*out)->g;
+    const int half_slice = dims_local[0] * dims_local[1] * dims_local[2] / 2;
+    g.h_begin = 2 * half_slice;
+    g.h_end = (dims_local[3] + 2) * half_slice;
+    g.t_off = t0 - 2;
+    g.Lt_glob = Lt_global;
+    return STG_OK;
+}
+
+stg_status stg_slab_layout(const stg_lattice *lat, stg_prec vec_prec, int32_t *nchunk, int64_t offset[3],
+                           int32_t elem_bytes[3], int64_t *slice_sites)
+{
+    if (!lat || !nchunk || !offset || !elem_bytes || !slice_sites)
+        return set_error(STG_ERR_ARG, "stg_slab_layout: null pointer");
+    const long long Vh = lat->g.Vh;
+    *slice_sites = (long long)lat->g.L[0] * lat->g.L[1] * lat->g.L[2] / 2;
+    if (vec_prec == STG_F64 || vec_prec == STG_DS) {  // three arrays of one 16-byte word per site
+        *nchunk = 3;
+        for (int k = 0; k < 3; ++k) {
+            offset[k] = 16LL * Vh * k;
+            elem_bytes[k] = 16;
+        }
+        return STG_OK;
+    }
+    if (vec_prec == STG_F32) {  // colours 0, 1 as one float4 per site, then colour 2 as a float2
+        *nchunk = 2;
+        offset[0] = 0;
+        elem_bytes[0] = 16;
+        offset[1] = 16LL * Vh;
+        elem_bytes[1] = 8;
+        offset[2] = 0;
+        elem_bytes[2] = 0;
+        return STG_OK;
+    }
+    return set_error(STG_ERR_ARG, "stg_slab_layout: vec_prec must be F64, DS or F32");
+}
+
 void stg_lattice_destroy(stg_lattice *lat) { delete lat; }
 
 int64_t stg_lattice_sites(const stg_lattice *lat, int32_t parity)
@@ -758,6 +812,8 @@ stg_status stg_dslash(const stg_gauge *g, int32_t out_parity, void *out_dev, con
 stg_status stg_normal_op(const stg_gauge *g, double mass, double shift, void *out_even_dev, const void *in_even_dev,
                          void *tmp_odd_dev, double *pq_dev, void *stream)
 {
+    if (g && stg::geom_is_slab(g->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_normal_op: not available on a slab lattice (stg_dslash* only)");
     if (!g || !out_even_dev || !in_even_dev || !tmp_odd_dev) return set_error(STG_ERR_ARG, "stg_normal_op: null pointer");
     if (!aligned16(out_even_dev) || !aligned16(in_even_dev) || !aligned16(tmp_odd_dev))
         return set_error(STG_ERR_ARG, "stg_normal_op: pointers must be 16-byte aligned");

@@ -268,18 +268,29 @@ __device__ __forceinline__ int fast_div(int n, const FastDiv &f)
 }
 
 struct Geom {
-    int L[4];       // Lx Ly Lz Lt
-    int Vh;         // sites per parity
+    int L[4];       // Lx Ly Lz Lt (of the stored lattice)
+    int Vh;         // sites per parity (the stride of every field and link array)
     int antiperiodic;
     FastDiv div[3];  // by Lx / 2, Ly and Lz (geom_init)
+    // Output half-index range of the D kernels, [h_begin, h_end): the whole parity on a full
+    // lattice; the interior time slices on a slab, whose stored lattice carries halo slices.
+    int h_begin, h_end;
+    // global time of stored slice 0 and the global time extent (0 and Lt on a full lattice): the
+    // antiperiodic sign sits on the t-links at global time Lt_glob - 1
+    int t_off, Lt_glob;
 };
 
-// Fills the derived members of a Geom whose extents are set.
+// Fills the derived members of a Geom whose extents, Vh and antiperiodic flag are set (a full
+// lattice: every site is an output, stored time = global time).
 inline void geom_init(Geom &g)
 {
     g.div[0] = make_fast_div((unsigned)(g.L[0] >> 1));
     g.div[1] = make_fast_div((unsigned)g.L[1]);
     g.div[2] = make_fast_div((unsigned)g.L[2]);
+    g.h_begin = 0;
+    g.h_end = g.Vh;
+    g.t_off = 0;
+    g.Lt_glob = g.L[3];
 }
 
 // Coordinates and lexicographic index of the site with half index h on parity par.
@@ -330,8 +341,9 @@ __device__ __forceinline__ Hop hop_of(const Geom &g, const Site &s, int mu)
     o.sf = eta;
     o.sb = eta;
     if (mu == 3 && g.antiperiodic) {
-        if (s.t == L - 1) o.sf = -o.sf;  // forward link sits on x_t = Lt-1
-        if (s.t == 0) o.sb = -o.sb;      // backward link (x - t) sits on x_t = Lt-1
+        const int tg = s.t + g.t_off;          // global time of the site
+        if (tg == g.Lt_glob - 1) o.sf = -o.sf;  // forward link sits on x_t = Lt-1
+        if (tg == 0) o.sb = -o.sb;              // backward link (x - t) sits on x_t = Lt-1
     }
     return o;
 }

@@ -306,6 +306,8 @@ using namespace stg;
 extern "C" stg_status stg_stout_smear(const stg_lattice *lat, stg_prec prec, int32_t nstep, double rho,
                                       const void *links_dev, void *levels_dev, void *stream)
 {
+    if (lat && stg::geom_is_slab(lat->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_stout_smear: not available on a slab lattice (stg_dslash* only)");
     stg_status s = check_common(lat, nstep, rho, "stg_stout_smear");
     if (s != STG_OK) return s;
     if (prec != STG_F64 && prec != STG_F32) return set_error(STG_ERR_ARG, "stg_stout_smear: prec must be F64 or F32");
@@ -322,6 +324,8 @@ extern "C" stg_status stg_stout_force(const stg_lattice *lat, stg_prec prec, int
                                       const void *links_dev, const void *levels_dev, const void *grad_dev,
                                       void *out_dev, int32_t kind, void *stream)
 {
+    if (lat && stg::geom_is_slab(lat->g))
+        return stg::set_error(STG_ERR_SHAPE, "stg_stout_force: not available on a slab lattice (stg_dslash* only)");
     stg_status s = check_common(lat, nstep, rho, "stg_stout_force");
     if (s != STG_OK) return s;
     if (prec != STG_F64 && prec != STG_F32) return set_error(STG_ERR_ARG, "stg_stout_force: prec must be F64 or F32");

@@ -29,6 +29,8 @@ EXPORTS = [
     "stg_fermion_force", "stg_fermion_force_prec",
     "stg_stout_smear", "stg_stout_force", "stg_gauge_action", "stg_gauge_force",
     "stg_md_momenta", "stg_md_update_links", "stg_md_update_momenta", "stg_md_kinetic", "stg_complex_convert",
+    "stg_lattice_create_slab", "stg_slab_layout", "stg_slab_dslash_xpay", "stg_slab_axpy_norm", "stg_slab_shift_update",
+    "stg_mscg_state_init", "stg_mscg_state_alpha", "stg_mscg_state_beta",
 ]
 
 
@@ -46,6 +48,20 @@ class MscgStats(ctypes.Structure):
                 ("inner_resid", ctypes.POINTER(ctypes.c_double)), ("fp64_fallback", ctypes.c_int32),
                 ("refine_shift_iters", ctypes.POINTER(ctypes.c_int32)),
                 ("shift_reliable_updates", ctypes.POINTER(ctypes.c_int32))]
+
+
+class MscgState(ctypes.Structure):
+    """stg_mscg_state: host-side scalar recurrences of the multi-shift CG."""
+    _fields_ = [("nshift", ctypes.c_int32), ("i0", ctypes.c_int32), ("iters", ctypes.c_int32),
+                ("max_iter", ctypes.c_int32), ("running", ctypes.c_int32), ("nactive", ctypes.c_int32),
+                ("phase", ctypes.c_int32),
+                ("s", ctypes.c_double * 32), ("zeta", ctypes.c_double * 32), ("zeta_old", ctypes.c_double * 32),
+                ("zeta_new", ctypes.c_double * 32),
+                ("alpha", ctypes.c_double), ("alpha_old", ctypes.c_double), ("beta_old", ctypes.c_double),
+                ("rr", ctypes.c_double), ("tol2", ctypes.c_double),
+                ("cx", ctypes.c_double * 32), ("cr", ctypes.c_double * 32), ("cp", ctypes.c_double * 32),
+                ("active", ctypes.c_int32 * 32), ("upd_x", ctypes.c_int32 * 32), ("upd_p", ctypes.c_int32 * 32),
+                ("shift_iters", ctypes.c_int32 * 32)]
 
 
 class Instance(ctypes.Structure):
@@ -114,6 +130,16 @@ def lib() -> ctypes.CDLL:
     L.stg_md_update_momenta.argtypes = [P, ctypes.c_int, D, P, P, P]
     L.stg_complex_convert.argtypes = [ctypes.c_int64, ctypes.c_int, P, ctypes.c_int, P, P]
     L.stg_md_kinetic.argtypes = [P, P, P, P]
+    L.stg_lattice_create_slab.argtypes = [ctypes.POINTER(I32), I32, I32, I32, PP]
+    L.stg_slab_layout.argtypes = [P, ctypes.c_int, ctypes.POINTER(I32), ctypes.POINTER(I64), ctypes.POINTER(I32),
+                                  ctypes.POINTER(I64)]
+    L.stg_slab_dslash_xpay.argtypes = [P, I32, D, P, P, P, P, P]
+    L.stg_slab_axpy_norm.argtypes = [P, ctypes.c_int, D, P, P, P, P]
+    L.stg_slab_shift_update.argtypes = [P, ctypes.c_int, I32, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
+                                        ctypes.POINTER(I32), ctypes.POINTER(I32), PP, PP, P, P]
+    L.stg_mscg_state_init.argtypes = [ctypes.POINTER(MscgState), I32, ctypes.POINTER(D), D, D, I32]
+    L.stg_mscg_state_alpha.argtypes = [ctypes.POINTER(MscgState), D]
+    L.stg_mscg_state_beta.argtypes = [ctypes.POINTER(MscgState), D]
     for name in EXPORTS:
         f = getattr(L, name)
         if f.restype is ctypes.c_int or name in ("stg_lattice_create", "stg_gauge_create", "stg_field_pack",
@@ -122,7 +148,10 @@ def lib() -> ctypes.CDLL:
                                                  "stg_mscg_solve_batched", "stg_rational_apply", "stg_pseudofermion_action", "stg_fermion_force",
                                                  "stg_stout_smear", "stg_stout_force", "stg_gauge_action",
                                                  "stg_gauge_force", "stg_gauge_create_u1", "stg_gauge_update", "stg_fermion_force_prec", "stg_dslash", "stg_md_momenta", "stg_md_update_links",
-                                                 "stg_md_update_momenta", "stg_md_kinetic", "stg_complex_convert"):
+                                                 "stg_md_update_momenta", "stg_md_kinetic", "stg_complex_convert",
+                                                 "stg_lattice_create_slab", "stg_slab_layout", "stg_slab_dslash_xpay",
+                                                 "stg_slab_axpy_norm", "stg_slab_shift_update", "stg_mscg_state_init",
+                                                 "stg_mscg_state_alpha", "stg_mscg_state_beta"):
             f.restype = ctypes.c_int
     _lib = L
     return L

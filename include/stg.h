@@ -444,6 +444,14 @@ stg_status stg_lattice_create_slab(const int32_t dims_local[4], int32_t t0, int3
 stg_status stg_slab_layout(const stg_lattice *lat, stg_prec vec_prec, int32_t *nchunk, int64_t offset[3],
                            int32_t elem_bytes[3], int64_t *slice_sites);
 
+/* D (D_eo for out_parity 0, D_oe for 1) on part of a slab's local slices, the split of Alg. 1:
+ * part 1 the two border slices (stored slices 2 and Lt_loc + 1, in one launch), part 2 the bulk
+ * (stored slices 3 .. Lt_loc; nothing when Lt_loc = 2), part 0 every local slice (as stg_dslash).
+ * The border outputs can then travel to the neighbours while the bulk computes on another stream
+ * (the bulk writes none of the bytes the exchange reads or writes).  in's halo slices must be
+ * current.  STG_ERR_ARG for another part; STG_ERR_SHAPE on a full lattice. */
+stg_status stg_slab_dslash_part(const stg_gauge *g, int32_t out_parity, int32_t part, void *out_dev, const void *in_dev,
+                                void *stream);
 /* out = coef p - D in on the output sites (the local slices of a slab, every site of a full
  * lattice): D_eo for out_parity 0, D_oe for 1 (the second half of Eq. shift_eo's operator, with
  * coef = m^2 + sigma).  pq_dev != NULL receives this process's part of Re<p, out> (FP64, fixed

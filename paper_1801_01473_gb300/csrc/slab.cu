@@ -96,6 +96,43 @@ bool aligned(const void *p, unsigned a) { return (reinterpret_cast<uintptr_t>(p)
 
 using namespace stg;
 
+extern "C" stg_status stg_slab_dslash_part(const stg_gauge *g, int32_t out_parity, int32_t part, void *out_dev,
+                                           const void *in_dev, void *stream)
+{
+    if (!g || !out_dev || !in_dev) return set_error(STG_ERR_ARG, "stg_slab_dslash_part: null pointer");
+    if (out_parity != 0 && out_parity != 1) return set_error(STG_ERR_ARG, "stg_slab_dslash_part: out_parity must be 0 or 1");
+    if (part < 0 || part > 2) return set_error(STG_ERR_ARG, "stg_slab_dslash_part: part must be 0, 1 or 2");
+    if (!geom_is_slab(g->g)) return set_error(STG_ERR_SHAPE, "stg_slab_dslash_part: needs a slab lattice");
+    if (!aligned(out_dev, 16) || !aligned(in_dev, 16))
+        return set_error(STG_ERR_ARG, "stg_slab_dslash_part: pointers must be 16-byte aligned");
+    if (out_dev == in_dev) return set_error(STG_ERR_ARG, "stg_slab_dslash_part: out and in must differ");
+    const int hs = g->g.L[0] * g->g.L[1] * g->g.L[2] / 2;  // sites of one parity per time slice
+    const int lt = g->g.L[3] - 4;                          // local slices
+    DArgs a;
+    memset(&a, 0, sizeof(a));
+    a.out_par = out_parity;
+    auto add = [&](int s0, int s1) {  // stored slices [s0, s1)
+        if (s1 <= s0) return;
+        DGroup &G = a.grp[a.ngroups++];
+        G.g = g->g;
+        G.g.h_begin = s0 * hs;
+        G.g.h_end = s1 * hs;
+        G.links = g->links;
+        G.nrhs = 1;
+        G.in[0] = in_dev;
+        G.out[0] = out_dev;
+    };
+    if (part == 0) add(2, lt + 2);
+    if (part == 1) {
+        add(2, 3);
+        add(lt + 1, lt + 2);
+    }
+    if (part == 2) add(3, lt + 1);
+    if (a.ngroups == 0) return STG_OK;
+    STG_CUDA_TRY(launch_dslash(g->kind, a, 0, (cudaStream_t)stream));
+    return STG_OK;
+}
+
 extern "C" stg_status stg_slab_dslash_xpay(const stg_gauge *g, int32_t out_parity, double coef, void *out_dev,
                                            const void *in_dev, const void *p_dev, double *pq_dev, void *stream)
 {

@@ -29,7 +29,7 @@ EXPORTS = [
     "stg_fermion_force", "stg_fermion_force_prec",
     "stg_stout_smear", "stg_stout_force", "stg_gauge_action", "stg_gauge_force",
     "stg_md_momenta", "stg_md_update_links", "stg_md_update_momenta", "stg_md_kinetic", "stg_complex_convert",
-    "stg_lattice_create_slab", "stg_slab_layout", "stg_slab_dslash_xpay", "stg_slab_axpy_norm", "stg_slab_shift_update",
+    "stg_lattice_create_slab", "stg_slab_layout", "stg_slab_dslash_part", "stg_slab_dslash_xpay", "stg_slab_axpy_norm", "stg_slab_shift_update",
     "stg_mscg_state_init", "stg_mscg_state_alpha", "stg_mscg_state_beta",
 ]
 
@@ -133,6 +133,7 @@ def lib() -> ctypes.CDLL:
     L.stg_lattice_create_slab.argtypes = [ctypes.POINTER(I32), I32, I32, I32, PP]
     L.stg_slab_layout.argtypes = [P, ctypes.c_int, ctypes.POINTER(I32), ctypes.POINTER(I64), ctypes.POINTER(I32),
                                   ctypes.POINTER(I64)]
+    L.stg_slab_dslash_part.argtypes = [P, I32, I32, P, P, P]
     L.stg_slab_dslash_xpay.argtypes = [P, I32, D, P, P, P, P, P]
     L.stg_slab_axpy_norm.argtypes = [P, ctypes.c_int, D, P, P, P, P]
     L.stg_slab_shift_update.argtypes = [P, ctypes.c_int, I32, ctypes.POINTER(D), ctypes.POINTER(D), ctypes.POINTER(D),
@@ -149,7 +150,8 @@ def lib() -> ctypes.CDLL:
                                                  "stg_stout_smear", "stg_stout_force", "stg_gauge_action",
                                                  "stg_gauge_force", "stg_gauge_create_u1", "stg_gauge_update", "stg_fermion_force_prec", "stg_dslash", "stg_md_momenta", "stg_md_update_links",
                                                  "stg_md_update_momenta", "stg_md_kinetic", "stg_complex_convert",
-                                                 "stg_lattice_create_slab", "stg_slab_layout", "stg_slab_dslash_xpay",
+                                                 "stg_lattice_create_slab", "stg_slab_layout", "stg_slab_dslash_part",
+                                                 "stg_slab_dslash_xpay",
                                                  "stg_slab_axpy_norm", "stg_slab_shift_update", "stg_mscg_state_init",
                                                  "stg_mscg_state_alpha", "stg_mscg_state_beta"):
             f.restype = ctypes.c_int

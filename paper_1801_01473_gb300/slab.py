@@ -204,6 +204,10 @@ class LibraryOps:
     def dslash(self, out_parity: int, out: torch.Tensor, inp: torch.Tensor) -> None:
         check(lib().stg_dslash(self.g.handle, int(out_parity), _ptr(out), _ptr(inp), _stream()), "stg_dslash")
 
+    def dslash_part(self, out_parity: int, part: int, out: torch.Tensor, inp: torch.Tensor) -> None:
+        check(lib().stg_slab_dslash_part(self.g.handle, int(out_parity), int(part), _ptr(out), _ptr(inp), _stream()),
+              "stg_slab_dslash_part")
+
     def dslash_xpay(self, out_parity: int, coef: float, out, inp, p) -> float:
         check(lib().stg_slab_dslash_xpay(self.g.handle, int(out_parity), float(coef), _ptr(out), _ptr(inp), _ptr(p),
                                          _ptr(self._d), _stream()), "stg_slab_dslash_xpay")
@@ -230,13 +234,36 @@ def dslash(slab: Slab, ops, out_parity: int, out: torch.Tensor, inp: torch.Tenso
     return out
 
 
+def dslash_overlapped(slab: Slab, ops, out_parity: int, out: torch.Tensor, inp: torch.Tensor, transport) -> torch.Tensor:
+    """D on the local slices with the schedule of Alg. 1, for an input whose halos are current:
+    the two border slices first, then the bulk on a second stream while the border outputs go to
+    the neighbours, so that `out` leaves with its own halos current (the next operator's input)."""
+    if not out.is_cuda:
+        ops.dslash_part(out_parity, 1, out, inp)
+        ops.dslash_part(out_parity, 2, out, inp)
+        exchange_halos(slab, out, ops.prec, transport)
+        return out
+    main = torch.cuda.current_stream()
+    side = getattr(ops, "_side", None)
+    if side is None:
+        side = ops._side = torch.cuda.Stream()
+    ops.dslash_part(out_parity, 1, out, inp)  # borders on the main stream
+    side.wait_stream(main)
+    with torch.cuda.stream(side):
+        ops.dslash_part(out_parity, 2, out, inp)  # bulk, concurrently with the exchange below
+    exchange_halos(slab, out, ops.prec, transport)
+    main.wait_stream(side)
+    return out
+
+
 def mscg(slab: Slab, ops, b: torch.Tensor, shifts: Sequence[float], mass: float, transport, tol: float = 1e-10,
-         max_iter: int = 10000):
+         max_iter: int = 10000, overlap: bool = True):
     """Multi-shift CG (Sec. 2, Eq. shift_eo) for (m^2 + sigma_i - D_eo D_oe) x_i = b across the slabs:
     b an internal even field of this slab (halos need not be set); returns the solutions (internal
-    fields, local slices valid) and the statistics.  Per iteration: the halo exchange of p, D_oe,
-    the halo exchange of t, q = (m^2 + sigma_0) p - D_eo t with Re<p, q>, one sum over slabs, the
-    alpha step, r -= alpha q with |r|^2, one sum, the beta step, the shift update."""
+    fields, local slices valid) and the statistics.  Per iteration: the halo exchange of p, D_oe
+    (with overlap: borders, then the bulk while t's borders travel, Alg. 1), the halo exchange of t
+    otherwise, q = (m^2 + sigma_0) p - D_eo t with Re<p, q>, one sum over slabs, the alpha step,
+    r -= alpha q with |r|^2, one sum, the beta step, the shift update."""
     L = lib()
     ns = len(shifts)
     sig = (ctypes.c_double * ns)(*[float(s) for s in shifts])
@@ -254,8 +281,12 @@ def mscg(slab: Slab, ops, b: torch.Tensor, shifts: Sequence[float], mass: float,
     coef = mass * mass + float(min(shifts))
     p0 = ps[st.i0]
     while st.running:
-        dslash(slab, ops, 1, t, p0, transport)
-        exchange_halos(slab, t, ops.prec, transport)
+        exchange_halos(slab, p0, ops.prec, transport)
+        if overlap:
+            dslash_overlapped(slab, ops, 1, t, p0, transport)
+        else:
+            ops.dslash(1, t, p0)
+            exchange_halos(slab, t, ops.prec, transport)
         pq = total(ops.dslash_xpay(0, coef, q, t, p0))
         check(L.stg_mscg_state_alpha(ctypes.byref(st), pq), "stg_mscg_state_alpha")
         rr = total(ops.axpy_norm(-st.alpha, q, r))

@@ -55,6 +55,14 @@ class OracleOps:
     def dslash(self, out_parity, out, inp):
         from_canon(self._d(out_parity, inp), out, self.local)
 
+    def dslash_part(self, out_parity, part, out, inp):
+        hs, lt = self.slab.half_slice, self.slab.lt_loc
+        rows = {0: [self.local], 1: [slice(2 * hs, 3 * hs), slice((lt + 1) * hs, (lt + 2) * hs)],
+                2: [slice(3 * hs, (lt + 1) * hs)]}[part]
+        d = self._d(out_parity, inp)
+        for r in rows:
+            from_canon(d, out, r)
+
     def dslash_xpay(self, out_parity, coef, out, inp, p):
         pc = to_canon(p, self.vh)
         o = coef * pc - self._d(out_parity, inp)

@@ -78,7 +78,46 @@ def test_slab_dslash_matches_oracle(variant, dims, nslab):
         assert np.abs(got - ref).max() <= TOL[variant] * np.abs(ref).max(), (variant, out_par)
 
 
-def test_slab_mscg_matches_oracle():
+@pytest.mark.parametrize("lt_loc", [2, 4, 8])
+def test_border_and_bulk_parts_cover_the_slab(lt_loc):
+    """Alg. 1's split: the border launch and the bulk launch together write bitwise what one launch
+    over all local slices writes, and the overlapped schedule leaves the output's halos current."""
+    import paper_1801_01473_gb300 as p
+    from paper_1801_01473_gb300 import slab as sl
+    dims = (6, 4, 4, 2 * lt_loc)
+    u = S.gauge_links(dims, "haar", 1407)
+    psi = S.gaussian_field(dims, 1408)
+    ut = torch.from_numpy(u).cuda()
+
+    def fn(rank, tr):
+        slab = sl.Slab(dims, rank, 2)
+        g = p.Gauge(slab.lattice, slab.stored_links(ut), "f64", 12)
+        ops = sl.LibraryOps(slab, g)
+        x = _stored(p, slab, psi, "f64")
+        sl.exchange_halos(slab, x, "f64", tr)
+        whole, split = g.new_field().zero_(), g.new_field().zero_()
+        ops.dslash(1, whole, x)
+        sl.dslash_overlapped(slab, ops, 1, split, x, tr)
+        torch.cuda.synchronize()
+        loc = slice(2 * slab.half_slice, (slab.lt_loc + 2) * slab.half_slice)
+        a, b = whole.reshape(3, -1, 2)[:, loc], split.reshape(3, -1, 2)[:, loc]
+        assert torch.equal(a, b)
+        return p.unpack(slab.lattice, split).cpu().numpy()
+
+    out = _run_threads(2, fn)
+    # the halos of each slab's output now hold the neighbour's border outputs
+    ref = oracle.dslash_oe(dims, u, psi)
+    hs = dims[0] * dims[1] * dims[2] // 2
+    for rank in range(2):
+        st = out[rank].reshape(lt_loc + 4, hs, 3)
+        gl = ref.reshape(dims[3], hs, 3)
+        t_lo, t_hi = (rank * lt_loc - 1) % dims[3], ((rank + 1) * lt_loc) % dims[3]
+        assert np.abs(st[1] - gl[t_lo]).max() <= 1e-12 * np.abs(ref).max()
+        assert np.abs(st[lt_loc + 2] - gl[t_hi]).max() <= 1e-12 * np.abs(ref).max()
+
+
+@pytest.mark.parametrize("overlap", [True, False])
+def test_slab_mscg_matches_oracle(overlap):
     import paper_1801_01473_gb300 as p
     from paper_1801_01473_gb300 import slab as sl
     dims, mass, shifts, tol = (8, 8, 8, 16), 0.1, [1e-3, 0.02, 0.3, 1.5], 1e-10
@@ -90,7 +129,7 @@ def test_slab_mscg_matches_oracle():
         slab = sl.Slab(dims, rank, 2)
         g = p.Gauge(slab.lattice, slab.stored_links(ut), "f64", 18)
         ops = sl.LibraryOps(slab, g)
-        xs, st = sl.mscg(slab, ops, _stored(p, slab, b, "f64"), shifts, mass, tr, tol=tol)
+        xs, st = sl.mscg(slab, ops, _stored(p, slab, b, "f64"), shifts, mass, tr, tol=tol, overlap=overlap)
         return [slab.local_part(p.unpack(slab.lattice, x).cpu().numpy()) for x in xs], st
 
     out = _run_threads(2, fn)

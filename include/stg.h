@@ -208,9 +208,9 @@ typedef struct {
     double tol;              /* target relative FP64 true residual |b - A_i x_i| / |b| per shift   */
     int32_t max_iter;        /* iteration cap of each phase (> 0)                                 */
     double inner_tol;        /* mixed solves: stopping residual of the inner multi-shift phase
-                                (0 -> 1e-9 for F32 gauges, 1e-4 for BF16/F16 gauges)             */
+                                (0 -> 1e-8 for F32 gauges, 1e-4 for BF16/F16 gauges)             */
     double reliable_delta;   /* mixed solves: reliable update once |r| fell by this factor since
-                                the last one (0 -> 0.01)                                          */
+                                the last one (0 -> 1e-3)                                          */
     int32_t log_rows;        /* optional: rows of scalar_log to fill (0 = none)                    */
     double *scalar_log;      /* host [log_rows][2 + nshift]: alpha_k, beta_k, zeta_i^{k+1} of the
                                 first multi-shift iterations of system 0                         */

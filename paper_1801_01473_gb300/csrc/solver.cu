@@ -884,13 +884,16 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         }
     }
     const int kind_h = ii[0].gh->kind;
-    // defaults measured on the 32^4, 16-pole workload: running the FP32 multi-shift phase on to an
-    // iterated 1e-9 costs fewer iterations than it saves in refinement; reliable updates every
-    // two decades keep the FP32 recurrences well inside their accuracy
+    // defaults measured on the 32^4, 16-pole workload (m = 0.01, tol 1e-10): the true residual of
+    // the FP32 multi-shift solutions stalls near 3e-7 whatever the iterated residual, so the phase
+    // stops at an iterated 1e-8 (175 iterations; 1e-9: 207, refinement 59 -> 70 iterations), and
+    // reliable updates every three decades take 20 double-single residuals instead of 29 (0.0855 ->
+    // 0.0818 s per solve; 1e-7 and 3e-8 were slower: the refinement grows faster than the phase
+    // shrinks)
     const double inner_tol = mixed ? (prm->inner_tol > 0 ? prm->inner_tol
-                                                          : (base_kind(kind_i) == kBF16R12 || base_kind(kind_i) == kF16R12 ? 1e-4 : 1e-9))
+                                                          : (base_kind(kind_i) == kBF16R12 || base_kind(kind_i) == kF16R12 ? 1e-4 : 1e-8))
                                    : prm->tol;
-    const double delta = prm->reliable_delta > 0 ? prm->reliable_delta : 0.01;
+    const double delta = prm->reliable_delta > 0 ? prm->reliable_delta : 1e-3;
     const int vb = Field<R>::kBytesPerSite;
 
     // The workspace comes from the device's default stream-ordered memory pool.  Keep up to

@@ -93,8 +93,9 @@ class Action:
             groups.setdefault(tuple(float(v) for v in shifts), []).append(k)
         xs = [None] * len(self.pseudofermions)
         # loose (MD) mixed solves stop their FP32 multi-shift phase at 0.3 tol rather than the library's
-        # 1e-9: at 32^4, m = 0.3, 10 poles, tol 1e-7 this cut the solve from 13.0 to 11.4 ms with the
-        # same refinement (the certified residual is unchanged; only the split between phases moves)
+        # default (then 1e-9): at 32^4, m = 0.3, 10 poles, tol 1e-7 this cut the solve from 13.0 to
+        # 11.4 ms with the same refinement (the certified residual is unchanged; only the split
+        # between phases moves)
         itol = max(1e-9, 0.3 * tol) if (md and gi is not None) else 0.0
         for shifts, ks in groups.items():
             if len(ks) == 1:

@@ -276,8 +276,8 @@ class L2Flush:
 
 def time_deo_sweep(torch, p, dims, peak, reps=50, b2b_batch=32):
     """D_eo per storage kind at `dims`: single launches after an L2 flush (median of reps), and
-    back-to-back launches over distinct sources alternating two copies of the links (inputs larger
-    than L2, the configuration of the headline number)."""
+    back-to-back launches over distinct sources alternating two copies of the links (the
+    configuration of the headline number; replayed from a CUDA graph)."""
     cfg_links = links_cached(dims, "expih", 1000 + 2)
     ut = torch.from_numpy(cfg_links).cuda()
     lat = p.Lattice(dims)
@@ -305,16 +305,24 @@ def time_deo_sweep(torch, p, dims, peak, reps=50, b2b_batch=32):
             torch.cuda.synchronize()
             ts.append(e0.elapsed_time(e1) * 1e-3)
         t = float(np.median(ts))
-        e0, e1 = events(torch)
+        # back to back: the launches captured once into a CUDA graph, so that host launch overhead
+        # (~10 us per ctypes call) cannot starve the small lattices
         for j in range(b2b_batch):
             p.dslash_eo_(gs[j & 1], dst[j], src[j])
-        e0.record()
-        for _ in range(3):
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
             for j in range(b2b_batch):
                 p.dslash_eo_(gs[j & 1], dst[j], src[j])
+        graph.replay()
+        e0, e1 = events(torch)
+        e0.record()
+        for _ in range(3):
+            graph.replay()
         e1.record()
         torch.cuda.synchronize()
         tb = e0.elapsed_time(e1) * 1e-3 / (3 * b2b_batch)
+        del graph
         # a U(1) phase field adds one stored phase per link ((cos, sin) doubles for f64/ds, a float angle otherwise)
         byt = (bytes_per_site(prec, recon) + (8 * (16 if prec in ("f64", "ds") else 4) if u1 else 0)) * lat.Vh
         out.append({"lattice": "x".join(map(str, dims)), "links": f"{prec}-{recon}" + ("+u1" if u1 else ""),
@@ -702,7 +710,8 @@ def run_gpu(args):
 
 
 def run_case(name):
-    """One small workload for a profiler to capture (no timing, no JSON line): `mscg` runs two mixed
+    """One small workload for a profiler to capture (no timing, no JSON line): `deo32_<storage>`
+    four D_eo launches at 32^4 on that link storage (e.g. deo32_bf16r12); `mscg` runs two mixed
     FP32-inner solves of the 32^4 msCG workload; `force32` three double-single D_eo applications and
     one 4-shift fermion force at 32^4; `stout24` one stout step and its chain rule at 24^4;
     `gauge24` the gauge force and action at 24^4; `fp32links24` the single-precision gauge force,
@@ -710,6 +719,21 @@ def run_case(name):
     trajectory (inside the NVTX range "force_eval")."""
     import torch
     import paper_1801_01473_gb300 as p
+    if name.startswith("deo32_"):
+        # four D_eo launches at 32^4 on one link storage (f32r12, f32r18, bf16r12, f16r12, dsr18, f64r18)
+        kind = name[len("deo32_"):]
+        prec, recon = kind[:-3] if kind[-3:-2] == "r" else kind[:-2], int(kind[-2:])
+        dims = (32, 32, 32, 32)
+        lat = p.Lattice(dims)
+        g = p.Gauge(lat, torch.from_numpy(links_cached(dims, "expih", 1002)).cuda(), prec, recon)
+        gen = torch.Generator(device="cuda").manual_seed(2002)
+        src = torch.randn((4,) + tuple(g.new_field().shape), dtype=g.new_field().dtype, device="cuda", generator=gen)
+        dst = torch.empty_like(src)
+        for j in range(4):
+            p.dslash_eo_(g, dst[j], src[j])
+        torch.cuda.synchronize()
+        print(name, float(dst.abs().max()))
+        return 0
     if name == "mscg":
         cfg = S.CONFIGS["mscg_32x32x32x32"]
         dims = cfg["dims"]
@@ -793,7 +817,9 @@ def main():
     ap.add_argument("--batch", type=int, default=256)
     ap.add_argument("--impl", default="stg", choices=["stg", "reference"])
     ap.add_argument("--no-extras", action="store_true")
-    ap.add_argument("--case", default=None, choices=["mscg", "force32", "stout24", "gauge24", "fp32links24", "rhmc_force32"],
+    ap.add_argument("--case", default=None,
+                    choices=["mscg", "force32", "stout24", "gauge24", "fp32links24", "rhmc_force32", "deo32_f32r12",
+                             "deo32_f32r18", "deo32_bf16r12", "deo32_f16r12", "deo32_dsr18", "deo32_f64r18"],
                     help="run one small workload for a profiler instead of the benchmark")
     args = ap.parse_args()
     if args.case:

@@ -413,13 +413,22 @@ def time_batched(torch, p, peak, reps=2):
     per_inst = [{"lattice": "x".join(map(str, g64.lattice.dims)), "iters": [s["iters"] for s in sts],
                  "refine_iters": [s["refine_iters"] for s in sts]} for (g64, _, _), (_, sts) in zip(insts, out)]
     ts = 0.0
-    for g64, gi, bs in insts:
+    for k, (g64, gi, bs) in enumerate(insts):
+        sep = 0.0
         for b in bs:
             torch.cuda.synchronize()
             t0 = time.perf_counter()
             p.mscg(g64, b, shifts, cfg["mass"], tol=cfg["tol"], g_inner=gi)
             torch.cuda.synchronize()
-            ts += time.perf_counter() - t0
+            sep += time.perf_counter() - t0
+        ts += sep
+        # the lattice's four sources as a batch of their own (link loads shared, no other lattice)
+        p.mscg_batched([(g64, gi, bs)], shifts, cfg["mass"], tol=cfg["tol"])
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        p.mscg_batched([(g64, gi, bs)], shifts, cfg["mass"], tol=cfg["tol"])
+        torch.cuda.synchronize()
+        per_inst[k].update({"separate_s": round(sep, 5), "own_batch_s": round(time.perf_counter() - t0, 5)})
     t = float(np.median(tb))
     return {"s_per_batch": round(t, 5), "sum_of_separate_s": round(ts, 5),
             "speedup": round(ts / t, 3), "systems": 16, "shifts": 16,

@@ -115,37 +115,13 @@ struct ForceArgsDS {
     Geom g;
     const void *links;          // double-single companion links (possibly with U(1) phases)
     const void *x[kMaxShifts];  // even double-single fields
-    const void *y[kMaxShifts];  // odd double-single fields D_oe (r_i x_i)
+    const void *y[kMaxShifts];  // odd double-single fields D_oe x_i
+    float2 res[kMaxShifts];     // residues as double-single (hi, lo), split on the host
     int nshift;
     int kind;
     double2 *out;  // canonical [4][V][3][3]
 };
 
-// double-single -> FP64: both halves converted on the integer pipes, then one FP64 add (exact:
-// hi + lo has at most 49 significant bits)
-__device__ __forceinline__ double ds_to_f64(const dsf &v) { return f32_to_f64(v.hi) + f32_to_f64(v.lo); }
-
-// W_rc (+)= f_r conj(g_c) for double-single f, g, one compensated accumulator (head, tail) per real
-// component (the products of lazy_mac: TwoProduct of the high parts and the cross terms, TwoSum
-// into the head, all rounding errors into the tail)
-__device__ __forceinline__ void outer_conj_lazy(float whi[3][3][2], float wlo[3][3][2], const cx<dsf> f[3],
-                                                const cx<dsf> g[3])
-{
-#pragma unroll
-    for (int r = 0; r < 3; ++r)
-#pragma unroll
-        for (int c = 0; c < 3; ++c) {
-            lazy_mac(whi[r][c][0], wlo[r][c][0], f[r].re, g[c].re);
-            lazy_mac(whi[r][c][0], wlo[r][c][0], f[r].im, g[c].im);
-            lazy_mac(whi[r][c][1], wlo[r][c][1], f[r].im, g[c].re);
-            lazy_mac(whi[r][c][1], wlo[r][c][1], -f[r].re, g[c].im);
-        }
-}
-
-// The gather in double-single on the FP32 pipes.  The residues are folded into y'_i = D_oe (r_i x_i)
-// (the host packs r_i x_i for D_oe), so that
-//   z even:  W = + sum_i y'_i(z+mu) x_i(z)^dag        z odd:  W = - sum_i x_i(z+mu) y'_i(z)^dag
-// and W, Z = U W and TA(Z) run in double-single, converted to FP64 only for the output.
 template <typename LinkT>
 __global__ void __launch_bounds__(kForceBlock) k_force_ds(const __grid_constant__ ForceArgsDS a)
 {
@@ -157,11 +133,12 @@ __global__ void __launch_bounds__(kForceBlock) k_force_ds(const __grid_constant_
     const long long V = 2LL * Vh;
     for (int mu = 0; mu < 4; ++mu) {
         const Hop hp = hop_of(a.g, s, mu);
-        float whi[3][3][2], wlo[3][3][2];
+        cx<dsf> W[3][3];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int c = 0; c < 3; ++c) whi[r][c][0] = whi[r][c][1] = wlo[r][c][0] = wlo[r][c][1] = 0.f;
+            for (int c = 0; c < 3; ++c) W[r][c] = cx<dsf>{dsf(0.f, 0.f), dsf(0.f, 0.f)};
+        // W = sum_i r_i f_i g_i^dag  (f = y(z+mu), g = x(z) for even z; f = x(z+mu), g = y(z) for odd z)
         for (int i = 0; i < a.nshift; ++i) {
             cx<dsf> f[3], g[3];
             if (par == 0) {
@@ -171,69 +148,52 @@ __global__ void __launch_bounds__(kForceBlock) k_force_ds(const __grid_constant_
                 Field<dsf>::load(a.x[i], Vh, hp.hf, f);
                 Field<dsf>::load(a.y[i], Vh, h, g);
             }
-            outer_conj_lazy(whi, wlo, f, g);
+            const dsf ri = dsf(a.res[i].x, a.res[i].y);
+#pragma unroll
+            for (int c = 0; c < 3; ++c) f[c] = cx<dsf>{ri * f[c].re, ri * f[c].im};
+#pragma unroll
+            for (int r = 0; r < 3; ++r)
+#pragma unroll
+                for (int c = 0; c < 3; ++c) cmac_conj(W[r][c], g[c], f[r]);  // W_rc += f_r conj(g_c)
         }
-        cx<dsf> W[3][3];
+        // u = sign * exp(i theta) (theta = 0 without a phase field); sign = +u_mu(z) even, -u_mu(z) odd
+        const void *blk = link_block<LinkT>(a.links, Vh, mu, par);
+        cx<dsf> ph = LinkTraits<LinkT>::phase(blk, Vh, h);
+        if ((par == 0 ? hp.sf : -hp.sf) < 0.f) ph = cx<dsf>{-ph.re, -ph.im};
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
-            for (int c = 0; c < 3; ++c)
-                W[r][c] = cx<dsf>{ds_two_sum(whi[r][c][0], wlo[r][c][0]), ds_two_sum(whi[r][c][1], wlo[r][c][1])};
-        // u = sign * exp(i theta) (theta = 0 without a phase field); sign = +u_mu(z) even, -u_mu(z) odd
-        const void *blk = link_block<LinkT>(a.links, Vh, mu, par);
-        const bool neg = (par == 0 ? hp.sf : -hp.sf) < 0.f;
-        if constexpr (LinkTraits<LinkT>::kU1) {
-            cx<dsf> ph = LinkTraits<LinkT>::phase(blk, Vh, h);
-            if (neg) ph = cx<dsf>{-ph.re, -ph.im};
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) W[r][c] = cmul(ph, W[r][c]);
-        } else if (neg) {
-#pragma unroll
-            for (int r = 0; r < 3; ++r)
-#pragma unroll
-                for (int c = 0; c < 3; ++c) W[r][c] = cx<dsf>{-W[r][c].re, -W[r][c].im};
-        }
+            for (int c = 0; c < 3; ++c) W[r][c] = cmul(ph, W[r][c]);
         double2 *o = a.out + ((long long)mu * V + s.i) * 9;
         if (a.kind == 1) {
 #pragma unroll
             for (int r = 0; r < 3; ++r)
 #pragma unroll
-                for (int c = 0; c < 3; ++c) o[r * 3 + c] = make_double2(ds_to_f64(W[c][r].re), -ds_to_f64(W[c][r].im));
+                for (int c = 0; c < 3; ++c) o[r * 3 + c] = make_double2((double)W[c][r].re, -(double)W[c][r].im);
             continue;
         }
-        // Z = U W with the SU(3) link in double-single (compensated sums of 6 products per real part)
+        // Z = U W with the SU(3) link in double-single, then TA(Z) in FP64
         cx<dsf> U[3][3];
         LinkTraits<LinkT>::Base::load(blk, Vh, h, U);
-        cx<dsf> Z[3][3];
+        cx<double> Z[3][3];
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                float zh[2] = {0.f, 0.f}, zl[2] = {0.f, 0.f};
+                cx<dsf> z = cx<dsf>{dsf(0.f, 0.f), dsf(0.f, 0.f)};
 #pragma unroll
-                for (int k = 0; k < 3; ++k) {
-                    lazy_mac(zh[0], zl[0], U[r][k].re, W[k][c].re);
-                    lazy_mac(zh[0], zl[0], -U[r][k].im, W[k][c].im);
-                    lazy_mac(zh[1], zl[1], U[r][k].re, W[k][c].im);
-                    lazy_mac(zh[1], zl[1], U[r][k].im, W[k][c].re);
-                }
-                Z[r][c] = cx<dsf>{ds_two_sum(zh[0], zl[0]), ds_two_sum(zh[1], zl[1])};
+                for (int k = 0; k < 3; ++k) cmac(z, U[r][k], W[k][c]);
+                Z[r][c] = cx<double>{(double)z.re, (double)z.im};
             }
-        // TA(Z) = (Z - Z^dag)/2 - tr(Z - Z^dag)/6 in double-single: the trace part is i Im tr Z / 3
-        const float third_hi = __fdiv_rn(1.f, 3.f);
-        const dsf third(third_hi, __fdiv_rn(__fmaf_rn(-3.f, third_hi, 1.f), 3.f));
-        const dsf im_tr = (Z[0][0].im + Z[1][1].im + Z[2][2].im) * third;
+        const double im_tr = (Z[0][0].im + Z[1][1].im + Z[2][2].im) / 3.0;
 #pragma unroll
         for (int r = 0; r < 3; ++r)
 #pragma unroll
             for (int c = 0; c < 3; ++c) {
-                const dsf dre = Z[r][c].re - Z[c][r].re, sim = Z[r][c].im + Z[c][r].im;
-                dsf re(__fmul_rn(0.5f, dre.hi), __fmul_rn(0.5f, dre.lo));
-                dsf im(__fmul_rn(0.5f, sim.hi), __fmul_rn(0.5f, sim.lo));
-                if (r == c) im = im - im_tr;
-                o[r * 3 + c] = make_double2(ds_to_f64(re), ds_to_f64(im));
+                double re = 0.5 * (Z[r][c].re - Z[c][r].re);
+                double im = 0.5 * (Z[r][c].im + Z[c][r].im);
+                if (r == c) im -= im_tr;
+                o[r * 3 + c] = make_double2(re, im);
             }
     }
 }
@@ -345,22 +305,6 @@ __global__ void k_pack_many(int Vh, const double2 *const *__restrict__ canon, vo
 struct Residues {
     double r[kMaxShifts];
 };
-
-// canonical complex128 field i = blockIdx.y, times r_i in FP64, into double-single
-__global__ void k_pack_many_scaled(int Vh, const double2 *const *__restrict__ canon, void *const *__restrict__ out,
-                                   const Residues res)
-{
-    int h = blockIdx.x * blockDim.x + threadIdx.x;
-    if (h >= Vh) return;
-    const double2 *src = canon[blockIdx.y];
-    const double r = res.r[blockIdx.y];
-    cx<dsf> v[3];
-    for (int c = 0; c < 3; ++c) {
-        double2 d = src[(size_t)h * 3 + c];
-        v[c] = cx<dsf>{dsf(r * d.x), dsf(r * d.y)};
-    }
-    Field<dsf>::store(out[blockIdx.y], Vh, h, v);
-}
 
 // field i = blockIdx.y at y0 + i * stride: double-single -> FP64 scaled by the residue r_i, in place
 __global__ void k_ds_to_f64_scaled(int Vh, const void *y0, size_t stride, const Residues res)
@@ -525,16 +469,8 @@ extern "C" stg_status stg_fermion_force(const stg_gauge *g, int32_t nshift, cons
     k_pack_many<dsf><<<dim3((Vh + 255) / 256, nshift), 256, 0, st>>>(
         Vh, reinterpret_cast<const double2 *const *>(d_ptrs), d_ptrs + 2 * kMaxShifts);
     STG_CUDA_TRY(cudaGetLastError());
-    Residues rs;
-    for (int i = 0; i < kMaxShifts; ++i) rs.r[i] = i < nshift ? residues[i] : 0.0;
-    if (!fp64_gather) {  // r_i x_i in double-single (in the FP64 copies' slots), the input of D_oe
-        k_pack_many_scaled<<<dim3((Vh + 255) / 256, nshift), 256, 0, st>>>(
-            Vh, reinterpret_cast<const double2 *const *>(d_ptrs), d_ptrs + kMaxShifts, rs);
-        STG_CUDA_TRY(cudaGetLastError());
-    }
 
-    // y_i = D_oe x_i (y'_i = D_oe r_i x_i for the double-single gather), link loads shared across
-    // up to kMaxRhs shifts per group
+    // y_i = D_oe x_i, link loads shared across up to kMaxRhs shifts per group
     for (int base = 0; base < nshift;) {
         DArgs d;
         memset(&d, 0, sizeof(d));
@@ -546,7 +482,7 @@ extern "C" stg_status stg_fermion_force(const stg_gauge *g, int32_t nshift, cons
             G.links = gds->links;
             G.nrhs = (nshift - base) < kMaxRhs ? (nshift - base) : kMaxRhs;
             for (int j = 0; j < G.nrhs; ++j) {
-                G.in[j] = fp64_gather ? ptrs[2 * kMaxShifts + base + j] : a.x[base + j];
+                G.in[j] = ptrs[2 * kMaxShifts + base + j];
                 G.out[j] = const_cast<void *>(a.y[base + j]);
             }
             base += G.nrhs;
@@ -564,7 +500,9 @@ extern "C" stg_status stg_fermion_force(const stg_gauge *g, int32_t nshift, cons
         b.out = static_cast<double2 *>(out_c128_dev);
         for (int i = 0; i < nshift; ++i) {
             b.x[i] = ptrs[2 * kMaxShifts + i];
-            b.y[i] = a.y[i];  // r_i y_i
+            b.y[i] = a.y[i];
+            const float hi = (float)residues[i];
+            b.res[i] = make_float2(hi, (float)(residues[i] - (double)hi));
         }
         const dim3 grid_ds((Vh + kForceBlock - 1) / kForceBlock, 2);
         switch (gds->kind) {
@@ -577,6 +515,8 @@ extern "C" stg_status stg_fermion_force(const stg_gauge *g, int32_t nshift, cons
         return STG_OK;
     }
     // FP64 gather: r_i y_i, double-single -> FP64 in place (same 48-byte site layout)
+    Residues rs;
+    for (int i = 0; i < kMaxShifts; ++i) rs.r[i] = i < nshift ? residues[i] : 0.0;
     k_ds_to_f64_scaled<<<dim3((Vh + 255) / 256, nshift), 256, 0, st>>>(Vh, a.y[0], fb, rs);
     STG_CUDA_TRY(cudaGetLastError());
     dim3 grid((Vh + kForceBlock - 1) / kForceBlock, 2);

@@ -227,11 +227,13 @@ typedef struct {
     int32_t iters;            /* multi-shift iterations                                            */
     int32_t reliable_updates; /* FP64 true-residual recomputations during refinement               */
     int32_t refine_iters;     /* largest refinement iteration count over the shifts                */
-    double *true_resid;       /* host [nshift] (may be NULL): final |b - A_i x_i| / |b|, in FP64;
-                                 for a mixed solve whose tol is at least ten times the rounding-
-                                 error bound e_i = 64 * 2^-44 (1 + 16 / (m^2 + sigma_i)) of the
-                                 double-single residual, and whose double-single residual is
-                                 below tol - e_i, that value (no FP64 operator applied)          */
+    double *true_resid;       /* host [nshift] (may be NULL): final |b - A_i x_i| / |b|.  Pure FP64
+                                 solves: the FP64 residual.  Mixed solves whose tol is at least
+                                 ten times e_i = 64 * 2^-44 (1 + 16 / (m^2 + sigma_i)) for every
+                                 shift: the double-single residual (FP64-verified for shifts it
+                                 does not clear by e_i).  Tighter mixed solves: the FP64 residual of
+                                 the multi-shift solution, updated by - A y in double-single for
+                                 every refinement correction y                                   */
     int32_t *shift_iters;     /* host [nshift] (may be NULL): multi-shift iteration at which each
                                  shift stopped                                                    */
     double *inner_resid;      /* host [nshift] (may be NULL): true residual of each shift right
@@ -248,9 +250,12 @@ typedef struct {
  *   g_inner  NULL -> pure FP64 solve.  Otherwise an F32/BF16/F16 gauge on the same lattice:
  *            multi-shift phase in that precision (FP32 vectors, FP64 scalars and reductions,
  *            solutions accumulated in double-single), then each shift above tol is refined by CG
- *            (FP32 links) with reliable updates in double-single arithmetic; each final residual
- *            that the double-single one does not certify (see true_resid) is checked in FP64, and
- *            the solve is repeated with FP64 reliable updates if a shift fails that check.
+ *            (FP32 links) with reliable updates in double-single arithmetic.  When tol is loose
+ *            enough for double-single residuals to certify every shift, the residuals are
+ *            recomputed in double-single and any the bound does not clear is checked in FP64 (the
+ *            solve is repeated with FP64 reliable updates if one fails); otherwise the residual of
+ *            each multi-shift solution is computed once in FP64 and each reliable update
+ *            subtracts A y of its correction y in double-single (see true_resid).
  *   b_c128_dev          canonical complex128 [Vh][3] even-site source (device).
  *   x_c128_dev[nshift]  canonical complex128 [Vh][3] outputs (device), may not alias b.
  * Synchronises `stream` before returning.  STG_ERR_NOCONV if a shift is still above tol

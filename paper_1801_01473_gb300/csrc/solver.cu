@@ -82,6 +82,7 @@ struct SysVecs {
     void *r, *q, *t;                         // inner precision: r, q even; t odd
     void *x[kMaxShifts], *p[kMaxShifts];     // inner precision
     void *xhi, *rhi, *t64, *b64;             // phase 2: FP64 solution, residual, odd temp, source
+    void *yhi;                               // anchored refinement: the correction y in precision H
     const double2 *bcanon;                   // canonical source (phase 1)
     double *part_d, *part_v, *part_v2;       // partial sums (64-site dslash chunks / 32-site warps)
     int Vh, nblk_d, nblk_v, npart_v;  // nblk_v: kVecBlock-site blocks; npart_v: partials (one per 32 sites)
@@ -658,6 +659,29 @@ __global__ void __launch_bounds__(kVecBlock) k_rel_fold(const SysVecs *__restric
     Field<R>::store(V.x[0], V.Vh, h, z);
 }
 
+// x_hi (H) += y, y_hi = y (H), y = 0: the anchored refinement then updates r_hi -= A y_hi
+template <typename R, typename H>
+__global__ void __launch_bounds__(kVecBlock) k_rel_fold_keep(const SysVecs *__restrict__ sv, const int *__restrict__ noupd)
+{
+    if (noupd[blockIdx.y]) return;
+    const SysVecs &V = sv[blockIdx.y];
+    int h = blockIdx.x * kVecBlock + threadIdx.x;
+    if (h >= V.Vh) return;
+    cx<R> y[3], z[3];
+    cx<H> x[3], yh[3];
+    Field<R>::load_rw(V.x[0], V.Vh, h, y);
+    Field<H>::load_rw(V.xhi, V.Vh, h, x);
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+        yh[c] = cx<H>{H(y[c].re), H(y[c].im)};
+        x[c] = cx<H>{x[c].re + yh[c].re, x[c].im + yh[c].im};
+        z[c] = cx<R>{R(0), R(0)};
+    }
+    Field<H>::store(V.xhi, V.Vh, h, x);
+    Field<H>::store(V.yhi, V.Vh, h, yh);
+    Field<R>::store(V.x[0], V.Vh, h, z);
+}
+
 // after the FP64 residual r_hi = b - A x_hi (partials of |r_hi|^2 in part_d): decide per pair
 __global__ void k_rel_finish(SysScal *sc, const SysVecs *sv, const int *noupd, int *done, int *need_rel,
                              int *finished, double *true_rr, int *rel_count)
@@ -894,6 +918,19 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
                                                           : (base_kind(kind_i) == kBF16R12 || base_kind(kind_i) == kF16R12 ? 1e-4 : 1e-8))
                                    : prm->tol;
     const double delta = prm->reliable_delta > 0 ? prm->reliable_delta : 1e-3;
+    // A double-single residual certifies a shift on its own when tol exceeds tenfold a worst-case
+    // bound e of its rounding error relative to |b| (64 operations of relative error 2^-44 on terms
+    // of size (m^2 + sigma + 16) |x|, |x| <= |b| / (m^2 + sigma)).  When some shift's tol is below
+    // that (tight solves), the refinement is anchored instead: one FP64 residual b - A x of each
+    // multi-shift solution at its start, then each reliable update subtracts A y of the correction
+    // y in double-single (an error of the order 2^-44 (m^2 + sigma + 16) |y|, |y| far below |x|),
+    // with no FP64 operator afterwards.
+    bool anchored = false;
+    if (kDS)
+        for (int i = 0; i < ns; ++i) {
+            const double e = 64.0 * std::ldexp(1.0, -44) * (1.0 + 16.0 / (mass2 + prm->shifts[i]));
+            if (prm->tol < 10.0 * e) anchored = true;
+        }
     const int vb = Field<R>::kBytesPerSite;
 
     // The workspace comes from the device's default stream-ordered memory pool.  Keep up to
@@ -1011,6 +1048,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
                 W.xhi = mem.alloc(f64b);
                 V.x[i] = W.xhi;
                 W.rhi = mem.alloc(f64b);
+                W.yhi = anchored ? mem.alloc(f64b) : nullptr;
                 W.t64 = mem.alloc(f64b);
                 W.b64 = V.b64;
                 W.part_d = static_cast<double *>(mem.alloc(sizeof(double) * nbd));
@@ -1036,7 +1074,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     double *d_true_rr = static_cast<double *>(mem.alloc(sizeof(double) * npair));
     double *d_log = prm->log_rows > 0 ? static_cast<double *>(mem.alloc(sizeof(double) * prm->log_rows * (2 + ns)))
                                       : nullptr;
-    ConvPair *d_pairs = static_cast<ConvPair *>(mem.alloc(sizeof(ConvPair) * (npair + nsys)));
+    ConvPair *d_pairs = static_cast<ConvPair *>(mem.alloc(sizeof(ConvPair) * (2 * npair + nsys)));
     if (mem.err != cudaSuccess) return cuda_error(mem.err, "stg_mscg_solve: workspace allocation");
     int *done1 = d_flags, *need1 = d_flags + nsys, *done2 = d_flags + 2 * nsys, *need2 = done2 + npair,
         *noupd = need2 + npair, *finished = noupd + npair, *relcnt = finished + npair;
@@ -1092,6 +1130,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     int rg = 4;
     if (const char *e = getenv("STG_REFINE_GROUP")) rg = std::max(1, std::min(kMaxRhs, atoi(e)));
     DPlan p2, p64, p64f;  // p64: residuals with gh; p64f: the same with the F64 gauge (verification)
+    DPlan pinc;           // anchored refinement: r_hi = r_hi - A y_hi with gh
     for (int k = 0; k < ninst; ++k) {
         const int first = ii[k].sys0 * ns, cnt = ii[k].nrhs * ns;
         for (int q0 = 0; q0 < cnt; q0 += rg) {
@@ -1132,6 +1171,17 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
             add_group(p2.eo, Geo, 0);
             add_group(p64.oe, Hoe, 1);
             add_group(p64.eo, Heo, 0);
+            if (anchored) {
+                DGroup Ioe = Hoe, Ieo = Heo;
+                for (int j = 0; j < Goe.nrhs; ++j) {
+                    const SysVecs &W = v2[first + q0 + j];
+                    Ioe.in[j] = W.yhi;
+                    Ieo.epi_p[j] = W.yhi;
+                    Ieo.epi_b[j] = W.rhi;  // out = r_hi - A y_hi, in place
+                }
+                add_group(pinc.oe, Ioe, 1);
+                add_group(pinc.eo, Ieo, 0);
+            }
             Hoe.links = Heo.links = ii[k].g64->links;
             add_group(p64f.oe, Hoe, 1);
             add_group(p64f.eo, Heo, 0);
@@ -1309,11 +1359,41 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         STG_CUDA_TRY(cudaMemcpyAsync(d_s2, s2.data(), sizeof(SysScal) * npair, cudaMemcpyHostToDevice, ws));
     }
     std::vector<int> h_done2(npair, 1), h_need2(npair, 1), h_fin(npair, 0), h_noupd(npair, 0);
+    // x_hi of every pair and b of every system between precision H and FP64, in place
+    auto convert_xb = [&](bool to_f64, bool with_r) -> stg_status {
+        std::vector<ConvPair> cp;
+        for (int q = 0; q < npair; ++q) {
+            cp.push_back(ConvPair{v2[q].xhi, v2[q].xhi, v2[q].Vh});
+            if (with_r) cp.push_back(ConvPair{v2[q].rhi, v2[q].rhi, v2[q].Vh});
+        }
+        for (int s = 0; s < nsys; ++s) cp.push_back(ConvPair{v1[s].b64, v1[s].b64, v1[s].Vh});
+        STG_CUDA_TRY(cudaMemcpyAsync(d_pairs, cp.data(), sizeof(ConvPair) * cp.size(), cudaMemcpyHostToDevice, ws));
+        if (to_f64)
+            k_convert_pairs<H, double><<<dim3(nblkv_max, (unsigned)cp.size()), kVecBlock, 0, ws>>>(d_pairs);
+        else
+            k_convert_pairs<double, H><<<dim3(nblkv_max, (unsigned)cp.size()), kVecBlock, 0, ws>>>(d_pairs);
+        STG_CUDA_TRY(cudaGetLastError());
+        return STG_OK;
+    };
     auto reliable_update = [&](bool start) -> stg_status {
         STG_CUDA_TRY(cudaMemcpyAsync(noupd, h_noupd.data(), sizeof(int) * npair, cudaMemcpyHostToDevice, ws));
-        if (!start) k_rel_fold<R, H><<<vgrid2, kVecBlock, 0, ws>>>(d_v2, noupd);
-        for (const DArgs &a : p64.oe) STG_CUDA_TRY(launch_dslash(kind_h, a, 0, ws));
-        for (const DArgs &a : p64.eo) STG_CUDA_TRY(launch_dslash(kind_h, a, 2, ws));
+        if (anchored && start) {
+            // the FP64 anchor: r_hi = b - A x_hi with the F64 gauge, then everything back to H
+            stg_status cs = convert_xb(true, false);
+            if (cs != STG_OK) return cs;
+            for (const DArgs &a : p64f.oe) STG_CUDA_TRY(launch_dslash(kind_64, a, 0, ws));
+            for (const DArgs &a : p64f.eo) STG_CUDA_TRY(launch_dslash(kind_64, a, 2, ws));
+            cs = convert_xb(false, true);
+            if (cs != STG_OK) return cs;
+        } else if (anchored) {
+            k_rel_fold_keep<R, H><<<vgrid2, kVecBlock, 0, ws>>>(d_v2, noupd);
+            for (const DArgs &a : pinc.oe) STG_CUDA_TRY(launch_dslash(kind_h, a, 0, ws));
+            for (const DArgs &a : pinc.eo) STG_CUDA_TRY(launch_dslash(kind_h, a, 2, ws));
+        } else {
+            if (!start) k_rel_fold<R, H><<<vgrid2, kVecBlock, 0, ws>>>(d_v2, noupd);
+            for (const DArgs &a : p64.oe) STG_CUDA_TRY(launch_dslash(kind_h, a, 0, ws));
+            for (const DArgs &a : p64.eo) STG_CUDA_TRY(launch_dslash(kind_h, a, 2, ws));
+        }
         k_rel_finish<<<npair, 32, 0, ws>>>(d_s2, d_v2, noupd, done2, need2, finished, d_true_rr, relcnt);
         k_rel_copy<R, H><<<vgrid2, kVecBlock, 0, ws>>>(d_v2, noupd, finished, start ? 1 : 0);
         k_rel_scal<<<npair, 32, 0, ws>>>(d_s2, d_v2, noupd, finished, start ? 1 : 0);
@@ -1359,14 +1439,15 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     }
 
     // ---------------- FP64 verification of double-single results
-    if (kDS) {
+    if (kDS && anchored) {
+        // the residuals are FP64-anchored: x_hi to FP64 for the output, no further operator
+        st = convert_xb(true, false);
+        if (st != STG_OK) return st;
+        stamp("anchored refinement: no FP64 verification needed");
+    } else if (kDS) {
         // x_hi (per pair) and b (per system) to FP64 in place: same 48-byte site layout
-        std::vector<ConvPair> cp;
-        for (int q = 0; q < npair; ++q) cp.push_back(ConvPair{v2[q].xhi, v2[q].xhi, v2[q].Vh});
-        for (int s = 0; s < nsys; ++s) cp.push_back(ConvPair{v1[s].b64, v1[s].b64, v1[s].Vh});
-        STG_CUDA_TRY(cudaMemcpyAsync(d_pairs, cp.data(), sizeof(ConvPair) * cp.size(), cudaMemcpyHostToDevice, ws));
-        k_convert_pairs<dsf, double><<<dim3(nblkv_max, (unsigned)cp.size()), kVecBlock, 0, ws>>>(d_pairs);
-        STG_CUDA_TRY(cudaGetLastError());
+        st = convert_xb(true, false);
+        if (st != STG_OK) return st;
         // A pair's double-single residual certifies it on its own when tol exceeds tenfold a
         // worst-case bound e of that residual's rounding error relative to |b| (64 operations of
         // relative error 2^-44 on terms of size (m^2 + sigma + 16) |x|, |x| <= |b| / (m^2 + sigma))

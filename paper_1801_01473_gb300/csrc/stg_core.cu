@@ -76,8 +76,8 @@ bool pdl_enabled()
 // template, largest Vh of the launch): the first launch of a key outside stream capture runs
 // the kernel with 64-, 128- and 256-thread blocks and, for several right-hand sides on FP32 /
 // 16-bit links, the shared-link operator (each launch recomputes the same outputs, so the
-// repetition is harmless), times them with CUDA events on the launch stream and keeps the
-// fastest.  Launches during capture use the tuned size when known, else 128.  STG_AUTOTUNE=0
+// repetition is harmless; launches that update an input in place are never tuned), times them
+// with CUDA events on the launch stream and keeps the fastest.  Launches during capture use the tuned size when known, else 128.  STG_AUTOTUNE=0
 // disables tuning.
 namespace {
 std::mutex g_tune_mu;
@@ -146,6 +146,15 @@ static cudaError_t launch_dslash_tuned(int kind, const DArgs &a, int mode, cudaS
     cudaStreamCaptureStatus cs = cudaStreamCaptureStatusNone;
     if (cudaStreamIsCapturing(st, &cs) != cudaSuccess || cs != cudaStreamCaptureStatusNone)
         return launch_dslash_bs(kind, a, mode, kDslashBlock, st);
+    // a launch that updates one of its own inputs in place (out aliasing epi_b, epi_p or in) must
+    // run exactly once: it is not tuned (the default shape now, the tuned one once another launch
+    // of the same key has been tuned)
+    for (int k = 0; k < a.ngroups; ++k)
+        for (int j = 0; j < a.grp[k].nrhs; ++j) {
+            const DGroup &G = a.grp[k];
+            if (G.out[j] == G.in[j] || G.out[j] == G.epi_b[j] || G.out[j] == G.epi_p[j])
+                return launch_dslash_bs(kind, a, mode, kDslashBlock, st);
+        }
     const char *env = getenv("STG_AUTOTUNE");
     int best = kDslashBlock;
     if (!(env && env[0] == '0')) {

@@ -26,6 +26,8 @@ The same JSON line carries (measured in the same run, outside the timed steps):
              solve vs the sum of separate solves, with per-instance iteration counts;
   force      48^4 fermion force (12 shifts): whole call, its double-single D_oe part and the
              per-link gather, with fractions of the measured HBM bandwidth;
+  slab       the slab decomposition's D on one of two slabs of the 32^4 lattice (local sites, and
+             its border and bulk launches), one GPU;
   cpu_baseline  the FP64 oracle on the host cores: D_eo at 16^4 and 32^4 and capped msCG
              iterations at 32^4, on one thread and on all of them.
 --impl reference times that oracle as the reference arm (the paper ships no code).
@@ -437,6 +439,50 @@ def time_batched(torch, p, peak, reps=2):
             "per_instance": per_inst}
 
 
+def time_slab(torch, p, peak, reps=32):
+    """The device part of the slab decomposition along t: one of two slabs of the 32^4 workload
+    (32^3 x 16 local slices, stored with 2 + 2 halo slices), FP32-12 links: D_oe on the local sites
+    back to back (graph replay), and its border (2 slices) and bulk (14 slices) launches of Alg. 1;
+    GB/s over the local sites' algorithmic bytes."""
+    from paper_1801_01473_gb300 import slab as sl
+    dims = (32, 32, 32, 32)
+    slab = sl.Slab(dims, 0, 2)
+    lat = slab.lattice
+    ut = torch.from_numpy(links_cached(dims, "expih", 1002)).cuda()
+    g = p.Gauge(lat, slab.stored_links(ut), "f32", 12)
+    del ut
+    ops = sl.LibraryOps(slab, g)
+    gen = torch.Generator(device="cuda").manual_seed(2002)
+    x = torch.randn((2,) + tuple(g.new_field().shape), dtype=torch.float32, device="cuda", generator=gen)
+    y = torch.zeros_like(x)
+    out = {"global": "32x32x32x32", "local": "32x32x32x16", "stored": "32x32x32x20", "links": "f32-12"}
+    local = 32 * 32 * 32 * 16 // 2
+    for name, fn, sites in (("whole", lambda j: ops.dslash(1, y[j], x[j]), local),
+                            ("borders", lambda j: ops.dslash_part(1, 1, y[j], x[j]), 2 * 32 * 32 * 32 // 2),
+                            ("bulk", lambda j: ops.dslash_part(1, 2, y[j], x[j]), 14 * 32 * 32 * 32 // 2)):
+        for j in range(2):
+            fn(j)
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for r in range(reps):
+                fn(r & 1)
+        graph.replay()
+        e0, e1 = events(torch)
+        e0.record()
+        for _ in range(3):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        t = e0.elapsed_time(e1) * 1e-3 / (3 * reps)
+        byt = bytes_per_site("f32", 12) * sites
+        out[name] = {"us": round(t * 1e6, 2), "GBs": round(byt / t / 1e9, 1), "frac": round(byt / t / 1e9 / peak, 3)}
+        del graph
+    out["note"] = ("D_oe on one slab's local sites, reading the halo slices of its input; border + bulk is the "
+                   "split Alg. 1 overlaps with the halo exchange; one GPU, so no exchange is timed")
+    return out
+
+
 # Fermion force per link (48^4, 12 shifts): the link (144 B), the output (144 B) and, with every
 # vector read once per site, 12 x 48 B of x_i or y_i per site over its 4 links = 144 B.
 FORCE_BYTES_PER_LINK = 3 * 144
@@ -706,6 +752,7 @@ def run_gpu(args):
         line["mscg"] = time_mscg(torch, p, peak)
         line["batched"] = time_batched(torch, p, peak)
         line["force"] = time_force(torch, p, peak)
+        line["slab"] = time_slab(torch, p, peak)
         line["stout"] = time_stout(torch, p)
         line["gauge"] = time_gauge(torch, p)
         line["rhmc"] = time_rhmc(torch, p)

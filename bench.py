@@ -335,14 +335,15 @@ def time_deo_sweep(torch, p, dims, peak, reps=50, b2b_batch=32):
     return out
 
 
-def mscg_alg_bytes(vh, st, inner):
-    """Algorithmic bytes of one msCG solve on one system, from its statistics.
-    Multi-shift phase, per iteration and even site (the standard count): 2 (8 links + 2 v) for
-    D_oe and D_eo, 5 v for r, p, q, and 4 v for x_i, p_i of each active shift -- summed with the
-    real number of active shifts of every iteration (sum over shifts of the iteration each stopped).
-    Refinement, per CG iteration of a shift: 2 (8 links + 2 v) + 7 v (x, r, p updates) on the FP32
-    12-real operator; per reliable update the double-single residual, 2 (8 x 144 + 2 x 48) + 4 x 48.
-    inner: (link bytes, vector bytes) of the multi-shift phase."""
+def mscg_standard_bytes(vh, st, inner):
+    """Standard per-iteration byte count of one msCG solve on one system (a figure of merit: the
+    traffic of a multi-shift CG that reads each operand once per iteration, shift and right-hand
+    side, without the solver's shared link loads and deferred shift updates).
+    Multi-shift phase, per iteration and even site: 2 (8 links + 2 v) for D_oe and D_eo, 5 v for
+    r, p, q, and 4 v for x_i, p_i of each active shift -- summed with the real number of active
+    shifts of every iteration.  Refinement, per CG iteration of a shift: 2 (8 links + 2 v) + 7 v on
+    the FP32 12-real operator; per reliable update the double-single residual,
+    2 (8 x 144 + 2 x 48) + 4 x 48.  inner: (link bytes, vector bytes) of the multi-shift phase."""
     lb, v = inner
     p1 = st["iters"] * (2 * (8 * lb + 2 * v) + 5 * v) + 4 * v * sum(st["shift_iters"])
     if lb >= 144:  # pure FP64 solve: no refinement
@@ -350,6 +351,100 @@ def mscg_alg_bytes(vh, st, inner):
     ref = sum(st["refine_shift_iters"]) * (2 * (8 * 48 + 2 * 24) + 7 * 24)
     rel = sum(st["shift_reliable_updates"]) * (2 * (8 * 144 + 2 * 48) + 4 * 48)
     return vh * (p1 + ref + rel)
+
+
+# launch grouping of the solver (solver.cu): right-hand sides per multi-shift D launch group,
+# (rhs, shift) pairs per refinement group, residuals per deferred-update window, shifts per flush block
+SOLVER_RHS_GROUP, SOLVER_REFINE_GROUP, SOLVER_HIST_MAX, SOLVER_FLUSH_SHIFTS = 8, 4, 256, 8
+
+
+def mscg_moved_bytes(insts, lb_inner, mixed, nshift):
+    """Bytes the kernels of one msCG call must move, from its per-system statistics: every field
+    a kernel touches read or written once (neighbours from cache), links once per launch group and
+    iteration in which any member of the group is live (the group's longest member: a lower bound).
+    insts: [(Vh, [stats of each right-hand side])]; lb_inner: link bytes of the multi-shift phase.
+    Mixed solves: FP32 vectors (24 B a site), double-single solutions (48 B), deferred shift
+    updates, refinement on FP32 12-real links (48 B), double-single residual operator (144 B),
+    FP64 anchor (144 B), i.e. the anchored refinement these tolerances select.  FP64 solves: FP64
+    vectors (48 B), per-iteration shift updates, one FP64 residual check per shift.
+    Returns (bytes, bytes of the FP64-arithmetic D launches, their FP64 FMAs): FP64 D is bound by
+    GB300's FP64 pipe (DFMA_PER_SITE FMAs a site and right-hand side), not by HBM."""
+    v, vh, l64, lr, lh = (24, 48, 144, 48, 144) if mixed else (48, 48, 144, 144, 144)
+    f64_b, f64_fma = 0, 0
+    W = 0
+    if mixed:
+        ring = sum(len(sts) * n * 24 for n, sts in insts)
+        fit = (4 << 30) // max(ring, 1)
+        W = min(SOLVER_HIST_MAX, fit - 1) if fit > 1 else 8
+        W = max(8, W - W % 8)
+    total = 0
+    for n, sts in insts:
+        b = 0
+        fb, ff = 0, 0  # this lattice's FP64 D bytes and FMAs (per even site)
+        for g0 in range(0, len(sts), SOLVER_RHS_GROUP):  # multi-shift D: links per rhs group
+            b += 2 * 8 * lb_inner * max(s["iters"] for s in sts[g0:g0 + SOLVER_RHS_GROUP])
+            if not mixed:
+                fb += 2 * 8 * lb_inner * max(s["iters"] for s in sts[g0:g0 + SOLVER_RHS_GROUP])
+        for s in sts:
+            it, si = s["iters"], list(s["shift_iters"])
+            if not mixed:
+                fb += it * 5 * v
+                ff += it * 2 * DFMA_PER_SITE
+            # start: canonical b; r, every p_i (and the window's base copy); x_i = 0; b in FP64/DS
+            b += 48 + v + nshift * (v + vh) + (v if W else 0) + vh
+            # per iteration: D_oe p->t (2v), D_eo t,p->q (3v), r -= alpha q (3v)
+            b += it * 8 * v
+            if W:
+                b += it * 3 * v  # base direction p = r + beta p
+                for w0 in range(0, it, W):  # window flushes
+                    w1 = min(w0 + W, it)
+                    live = [i for i in range(nshift) if si[i] > w0]
+                    pmat = [i for i in range(nshift) if si[i] > w1 and w1 < it]
+                    chunks = {i // SOLVER_FLUSH_SHIFTS for i in live + pmat}
+                    b += len(chunks) * (w1 - w0) * v        # residual ring
+                    b += len(live) * (v + 2 * vh)          # P0_i read, x_i read and written
+                    b += len(pmat) * v + (v if w1 < it else 0)  # p_i (and the base copy) written
+            else:
+                b += it * v + sum(si) * (2 * v + 2 * vh)  # r once, then p_i and x_i per live shift
+        # refinement and residuals: (rhs, shift) pairs in groups of SOLVER_REFINE_GROUP
+        pairs = [(s, i) for s in sts for i in range(nshift)]
+        for q0 in range(0, len(pairs), SOLVER_REFINE_GROUP):
+            grp = pairs[q0:q0 + SOLVER_REFINE_GROUP]
+            rit = [s["refine_shift_iters"][i] if mixed else 0 for s, i in grp]
+            rel = [s["shift_reliable_updates"][i] if mixed else 0 for s, i in grp]
+            res_d = 2 * v + 3 * v  # the D pair of one residual, vector part (precision of the pass)
+            # first true residual of every pair: FP64 anchor (mixed) or FP64 check, links once
+            b += 2 * 8 * l64 + len(grp) * 6 * vh
+            fb += 2 * 8 * l64 + len(grp) * 6 * vh
+            ff += len(grp) * 2 * DFMA_PER_SITE
+            if mixed:
+                b += len(grp) * (2 * vh + 2 * vh + 2 * vh)  # x to FP64 and back, r to DS
+                b += 2 * 8 * lr * max(rit) + sum(rit) * (res_d + 3 * v + 5 * v)
+                # reliable updates: fold (y, x, y_hi, y=0), r_hi -= A y_hi (DS), r = r_hi
+                b += 2 * 8 * lh * max(rel) + sum(rel) * ((v + 2 * vh + vh + v) + 6 * vh + (vh + v))
+            b += len(grp) * (vh + 3 * v)  # r = r_hi, p = r, y = 0 after the first residual
+            b += len(grp) * 2 * vh        # solution to the output layout
+        if mixed:
+            b += len(sts) * 3 * 2 * vh    # b between DS and FP64 around the anchor and at the end
+        total += n * b
+        f64_b += n * fb
+        f64_fma += n * ff
+    return total, f64_b, f64_fma
+
+
+# FP64 FMAs of one staggered D application per output site and right-hand side: 8 hops, each a
+# 3 x 3 complex matrix times a colour vector (36 real FMAs) and its signed accumulation (6)
+DFMA_PER_SITE = 8 * (36 + 6)
+# GB300 FP64 FMA rate: 2 per clock and SM (ncu sm__sass_thread_inst_executed_op_dfma_pred_on
+# .peak_sustained), 152 SMs, 2070 MHz: the nominal 1.25 TFLOP/s
+FP64_FMA_PER_S = 2 * 152 * 2.07e9
+
+
+def mscg_bound_s(moved, hbm_gbs):
+    """Lower bound of a solve's time from (bytes, FP64 D bytes, FP64 D FMAs): HBM time of all other
+    bytes plus, for the FP64 D launches, the larger of their HBM and FP64-pipe times."""
+    total, fb, ff = moved
+    return (total - fb) / (hbm_gbs * 1e9) + max(fb / (hbm_gbs * 1e9), ff / FP64_FMA_PER_S)
 
 
 def time_mscg(torch, p, peak, reps=3):
@@ -374,18 +469,29 @@ def time_mscg(torch, p, peak, reps=3):
             torch.cuda.synchronize()
             ts.append(time.perf_counter() - t0)
         t = float(np.median(ts))
-        alg = mscg_alg_bytes(lat.Vh, st, ib)
+        moved = mscg_moved_bytes([(lat.Vh, [st])], ib[0], inner is not None, len(shifts))
+        alg, bound = moved[0], mscg_bound_s(moved, peak)
+        std = mscg_standard_bytes(lat.Vh, st, ib)
         res[name] = {"s_per_solve": round(t, 5), "iters": st["iters"],
                      "refine_iters": st["refine_iters"], "reliable_updates": st["reliable_updates"],
                      "max_true_resid": float(max(st["true_resid"])), "converged": st["status"] == 0,
                      "alg_GB": round(alg / 1e9, 2), "eff_GBs": round(alg / t / 1e9, 1),
-                     "frac": round(alg / t / 1e9 / peak, 3)}
+                     "frac": round(alg / t / 1e9 / peak, 3),
+                     "fp64_d_GFMA": round(moved[2] / 1e9, 2), "bound_s": round(bound, 5),
+                     "frac_of_bound": round(bound / t, 3),
+                     "std_GB": round(std / 1e9, 2), "std_eff_GBs": round(std / t / 1e9, 1),
+                     "shift_iters": list(st["shift_iters"]), "refine_shift_iters": list(st["refine_shift_iters"]),
+                     "shift_reliable_updates": list(st["shift_reliable_updates"])}
         del gi
     res["mixed_speedup_vs_fp64"] = round(res["fp64"]["s_per_solve"] / min(
         res[k]["s_per_solve"] for k in ("fp32", "fp16", "bf16") if res[k]["converged"]), 3)
-    res["note"] = ("eff_GBs = algorithmic bytes (multi-shift phase with the real active-shift count per iteration, "
-                   "refinement and reliable updates) / solve time; the deferred solution update moves fewer bytes "
-                   "than the count, the FP64 verification is not counted")
+    res["note"] = ("alg_GB: bytes the solver's kernels must move (links once per launch group, deferred shift "
+                   "updates, grouped refinement, anchor and reliable updates; bench.py mscg_moved_bytes); "
+                   "eff_GBs = alg_GB / solve time, frac of measured HBM; bound_s: HBM time of those bytes with "
+                   "the FP64-arithmetic D launches (FP64 solve, FP64 anchor) at the larger of their HBM and "
+                   "FP64-pipe times (2 DFMA per clock and SM, 152 SMs, 2070 MHz), frac_of_bound = bound_s / "
+                   "solve time; std_GB: the standard per-iteration, per-shift count (mscg_standard_bytes), "
+                   "a figure of merit only")
     return res
 
 
@@ -411,7 +517,10 @@ def time_batched(torch, p, peak, reps=2):
         torch.cuda.synchronize()
         tb.append(time.perf_counter() - t0)
     worst = max(max(s["true_resid"]) for _, sts in out for s in sts)
-    alg = sum(mscg_alg_bytes(g64.lattice.Vh, s, (48, 24)) for (g64, _, _), (_, sts) in zip(insts, out) for s in sts)
+    moved = mscg_moved_bytes([(g64.lattice.Vh, sts) for (g64, _, _), (_, sts) in zip(insts, out)], 48, True,
+                             len(shifts))
+    alg = moved[0]
+    std = sum(mscg_standard_bytes(g64.lattice.Vh, s, (48, 24)) for (g64, _, _), (_, sts) in zip(insts, out) for s in sts)
     per_inst = [{"lattice": "x".join(map(str, g64.lattice.dims)), "iters": [s["iters"] for s in sts],
                  "refine_iters": [s["refine_iters"] for s in sts]} for (g64, _, _), (_, sts) in zip(insts, out)]
     ts = 0.0
@@ -435,7 +544,9 @@ def time_batched(torch, p, peak, reps=2):
     return {"s_per_batch": round(t, 5), "sum_of_separate_s": round(ts, 5),
             "speedup": round(ts / t, 3), "systems": 16, "shifts": 16,
             "max_true_resid": worst, "alg_GB": round(alg / 1e9, 2), "eff_GBs": round(alg / t / 1e9, 1),
-            "frac": round(alg / t / 1e9 / peak, 3), "separate_eff_GBs": round(alg / ts / 1e9, 1),
+            "frac": round(alg / t / 1e9 / peak, 3), "bound_s": round(mscg_bound_s(moved, peak), 5),
+            "frac_of_bound": round(mscg_bound_s(moved, peak) / t, 3), "std_GB": round(std / 1e9, 2),
+            "std_eff_GBs": round(std / t / 1e9, 1),
             "per_instance": per_inst}
 
 
@@ -767,7 +878,8 @@ def run_gpu(args):
 
 def run_case(name):
     """One small workload for a profiler to capture (no timing, no JSON line): `deo32_<storage>`
-    four D_eo launches at 32^4 on that link storage (e.g. deo32_bf16r12); `mscg` runs two mixed
+    four D_eo launches at 32^4 on that link storage (e.g. deo32_bf16r12); `deo32x<n>_<storage>` four
+    D_oe launches on n right-hand sides sharing each link load (e.g. deo32x4_f32r12); `mscg` runs two mixed
     FP32-inner solves of the 32^4 msCG workload; `force32` three double-single D_eo applications and
     one 4-shift fermion force at 32^4; `stout24` one stout step and its chain rule at 24^4;
     `gauge24` the gauge force and action at 24^4; `fp32links24` the single-precision gauge force,
@@ -775,6 +887,22 @@ def run_case(name):
     trajectory (inside the NVTX range "force_eval")."""
     import torch
     import paper_1801_01473_gb300 as p
+    if name.startswith("deo32x"):
+        # deo32x<n>_<storage>: four D_oe launches at 32^4 on n right-hand sides sharing each link load
+        nrhs, kind = name[len("deo32x"):].split("_", 1)
+        prec, recon = kind[:-3], int(kind[-2:])
+        dims = (32, 32, 32, 32)
+        lat = p.Lattice(dims)
+        g = p.Gauge(lat, torch.from_numpy(links_cached(dims, "expih", 1002)).cuda(), prec, recon)
+        gen = torch.Generator(device="cuda").manual_seed(2002)
+        f = g.new_field()
+        src = torch.randn((int(nrhs),) + tuple(f.shape), dtype=f.dtype, device="cuda", generator=gen)
+        dst = torch.empty_like(src)
+        for _ in range(4):
+            p.dslash_multi_(g, 1, dst, src)
+        torch.cuda.synchronize()
+        print(name, float(dst.abs().max()))
+        return 0
     if name.startswith("deo32_"):
         # four D_eo launches at 32^4 on one link storage (f32r12, f32r18, bf16r12, f16r12, dsr18, f64r18)
         kind = name[len("deo32_"):]
@@ -799,7 +927,9 @@ def run_case(name):
         g64, gi = p.Gauge(lat, ut, "f64", 18), p.Gauge(lat, ut, "f32", 12)
         for _ in range(2):
             x, st = p.mscg(g64, b, cfg["shifts"](), cfg["mass"], tol=1e-10, g_inner=gi)
-        print("mscg", st["iters"], st["refine_iters"], max(st["true_resid"]))
+        print("mscg", json.dumps({k: (list(v) if hasattr(v, "__len__") else v) for k, v in st.items()
+                                  if k in ("iters", "refine_iters", "reliable_updates", "shift_iters",
+                                           "refine_shift_iters", "shift_reliable_updates", "true_resid")}))
     elif name == "force32":
         dims = (32, 32, 32, 32)
         lat = p.Lattice(dims)

@@ -1005,7 +1005,8 @@ def main():
     ap.add_argument("--no-extras", action="store_true")
     ap.add_argument("--case", default=None,
                     choices=["mscg", "force32", "stout24", "gauge24", "fp32links24", "rhmc_force32", "deo32_f32r12",
-                             "deo32_f32r18", "deo32_bf16r12", "deo32_f16r12", "deo32_dsr18", "deo32_f64r18"],
+                             "deo32_f32r18", "deo32_bf16r12", "deo32_f16r12", "deo32_dsr18", "deo32_f64r18",
+                             "deo32x2_f32r12", "deo32x4_f32r12", "deo32x8_f32r12"],
                     help="run one small workload for a profiler instead of the benchmark")
     args = ap.parse_args()
     if args.case:

@@ -127,7 +127,85 @@ __device__ __forceinline__ void dslash_epilogue(const DGroup &G, const bool act[
     }
 }
 
-template <typename LinkT, int NRHS, int MODE, int BS>
+// Hop loop of the multi-rhs FP32 12-real operator with its loads one hop ahead: while hop k is
+// applied, the link of hop k + 1 and every rhs's neighbour vector of hop k + 1 are already in
+// flight in registers.  With several rhs per thread the plain loop is latency-bound (each hop's
+// multiply-adds wait for that hop's loads: 4 rhs at 32^4 reach 0.61 of HBM bandwidth with 28
+// warps per SM); one hop of lookahead costs registers (~125, 16 warps per SM) but keeps loads in
+// flight through the arithmetic (0.69).  Same operations in the same order as the plain loop, so
+// results are bitwise equal.
+template <int NRHS>
+__device__ __forceinline__ void dslash_hops_ahead_f32r12(const DGroup &G, int op, int h, const Site &s,
+                                                         const bool act[NRHS], cx<float> acc[NRHS][3])
+{
+    const int Vh = G.g.Vh;
+    Hop hq[4];
+#pragma unroll
+    for (int mu = 0; mu < 4; ++mu) hq[mu] = hop_of(G.g, s, mu);
+    // hop k = 2 mu (forward: link (mu, op) at h, input at hf) or 2 mu + 1 (backward: link (mu, 1 - op)
+    // and input at hb); a link is 3 float4 (rows 1 and 2), an FP32 vector a float4 and a float2
+    auto load = [&](int k, float4 l[3], float4 va[NRHS], float2 vb[NRHS]) {
+        const int mu = k >> 1;
+        const bool fw = (k & 1) == 0;
+        const int li = fw ? h : hq[mu].hb, vi = fw ? hq[mu].hf : hq[mu].hb;
+        const float4 *q = static_cast<const float4 *>(link_block<LinkF32R12>(G.links, Vh, mu, fw ? op : 1 - op));
+#pragma unroll
+        for (int c = 0; c < 3; ++c) l[c] = __ldg(q + (size_t)c * Vh + li);
+#pragma unroll
+        for (int j = 0; j < NRHS; ++j) {
+            if (!act[j]) continue;
+            va[j] = __ldg(static_cast<const float4 *>(G.in[j]) + vi);
+            vb[j] = __ldg(reinterpret_cast<const float2 *>(static_cast<const float4 *>(G.in[j]) + Vh) + vi);
+        }
+    };
+    float4 lc[3], ln[3], vac[NRHS], van[NRHS];
+    float2 vbc[NRHS], vbn[NRHS];
+    load(0, lc, vac, vbc);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+        if (k < 7) load(k + 1, ln, van, vbn);
+        cx<float> U[3][3];
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+            U[(2 * c) / 3][(2 * c) % 3] = cx<float>{lc[c].x, lc[c].y};
+            U[(2 * c + 1) / 3][(2 * c + 1) % 3] = cx<float>{lc[c].z, lc[c].w};
+        }
+        reconstruct_row3(U);
+        const int mu = k >> 1;
+        const float sg = (k & 1) == 0 ? hq[mu].sf : -hq[mu].sb;
+#pragma unroll
+        for (int j = 0; j < NRHS; ++j) {
+            if (!act[j]) continue;
+            const cx<float> v[3] = {cx<float>{vac[j].x, vac[j].y}, cx<float>{vac[j].z, vac[j].w},
+                                    cx<float>{vbc[j].x, vbc[j].y}};
+#pragma unroll
+            for (int r = 0; r < 3; ++r) {
+                cx<float> w = cx<float>{0.f, 0.f};
+                if ((k & 1) == 0) {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) cmac(w, U[r][c], v[c]);
+                } else {
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) cmac_conj(w, U[c][r], v[c]);
+                }
+                acc[j][r].re = fmaf(sg, w.re, acc[j][r].re);
+                acc[j][r].im = fmaf(sg, w.im, acc[j][r].im);
+            }
+        }
+        if (k < 7) {
+#pragma unroll
+            for (int c = 0; c < 3; ++c) lc[c] = ln[c];
+#pragma unroll
+            for (int j = 0; j < NRHS; ++j) {
+                vac[j] = van[j];
+                vbc[j] = vbn[j];
+            }
+        }
+    }
+}
+
+// AHEAD selects the hop loop with one hop of load lookahead (FP32 12-real links only).
+template <typename LinkT, int NRHS, int MODE, int BS, bool AHEAD = false>
 __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
 {
     using R = typename LinkT::R;
@@ -216,6 +294,9 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
                 for (int r = 0; r < 3; ++r)
                     acc[j][r] = cx<R>{ds_two_sum(ahi[j][r][0], alo[j][r][0]), ds_two_sum(ahi[j][r][1], alo[j][r][1])};
         }
+    } else if (AHEAD) {
+        if constexpr (std::is_same<LinkT, LinkF32R12>::value)
+            if (live) dslash_hops_ahead_f32r12<NRHS>(G, op, h, site_of(G.g, op, h), act, acc);
     } else if (live) {
         const Site s = site_of(G.g, op, h);
 #pragma unroll
@@ -463,9 +544,12 @@ inline void dslash_extent(const DArgs &a, int &maxv, int &maxr)
 // NRHS template the launcher uses for a largest group of `maxr` right-hand sides.
 inline int dslash_nrhs_template(int maxr) { return maxr <= 1 ? 1 : maxr <= 2 ? 2 : maxr <= 4 ? 4 : 8; }
 
-// Launch shape code: a block size (64, 128, 256) for the rhs-in-registers kernel, or
-// kSharedLinks for k_dslash_sh (64 x nrhs threads per block; FP32 arithmetic only).
+// Launch shape code: a block size (64, 128, 256) for the rhs-in-registers kernel, kSharedLinks
+// for k_dslash_sh (64 x nrhs threads per block; FP32 arithmetic only), or kLoadsAhead for the
+// rhs-in-registers kernel with one hop of load lookahead (64-thread blocks; FP32 12-real links and
+// 3 or 4 rhs, where it measured faster: 8 rhs spill).
 constexpr int kSharedLinks = 1 << 16;
+constexpr int kLoadsAhead = 1 << 17;
 template <typename LinkT>
 cudaError_t launch_dslash_t(const DArgs &a, int mode, int bs, cudaStream_t st)
 {
@@ -479,6 +563,17 @@ cudaError_t launch_dslash_t(const DArgs &a, int mode, int bs, cudaStream_t st)
             if (mode == 0) return launch_pdl_smem(k_dslash_sh<LinkT, 0>, grid, block, kShBytes, st, a);
             if (mode == 1) return launch_pdl_smem(k_dslash_sh<LinkT, 1>, grid, block, kShBytes, st, a);
             return launch_pdl_smem(k_dslash_sh<LinkT, 2>, grid, block, kShBytes, st, a);
+        } else {
+            return cudaErrorInvalidValue;
+        }
+    }
+    if (bs == kLoadsAhead) {
+        if constexpr (std::is_same<LinkT, LinkF32R12>::value) {
+            if (dslash_nrhs_template(maxr) != 4) return cudaErrorInvalidValue;
+            const dim3 grid((maxv + 63) / 64, a.ngroups);
+            if (mode == 0) return launch_pdl(k_dslash<LinkT, 4, 0, 64, true>, grid, dim3(64), st, a);
+            if (mode == 1) return launch_pdl(k_dslash<LinkT, 4, 1, 64, true>, grid, dim3(64), st, a);
+            return launch_pdl(k_dslash<LinkT, 4, 2, 64, true>, grid, dim3(64), st, a);
         } else {
             return cudaErrorInvalidValue;
         }

@@ -75,7 +75,8 @@ bool pdl_enabled()
 // Launch-shape autotuner of the D kernel.  Keyed by (device, storage kind, epilogue, rhs
 // template, largest Vh of the launch): the first launch of a key outside stream capture runs
 // the kernel with 64-, 128- and 256-thread blocks and, for several right-hand sides on FP32 /
-// 16-bit links, the shared-link operator (each launch recomputes the same outputs, so the
+// 16-bit links, the shared-link operator and (FP32 12-real, 3-4 rhs) the one-hop-lookahead loop
+// (each launch recomputes the same outputs, so the
 // repetition is harmless; launches that update an input in place are never tuned), times them
 // with CUDA events on the launch stream and keeps the fastest.  Launches during capture use the tuned size when known, else 128.  STG_AUTOTUNE=0
 // disables tuning.
@@ -130,11 +131,14 @@ static cudaError_t launch_dslash_tuned(int kind, const DArgs &a, int mode, cudaS
     int dev = 0;
     cudaGetDevice(&dev);
     const auto key = std::make_tuple(dev, kind, mode, nt, maxv);
-    // STG_DSLASH_SHAPE=64|128|256|shared fixes the launch shape (tests use it to run each variant)
+    // the lookahead kernel exists for FP32 12-real links with 3 or 4 right-hand sides
+    const bool ahead_ok = kind == kF32R12 && nt == 4;
+    // STG_DSLASH_SHAPE=64|128|256|shared|ahead fixes the launch shape (tests use it to run each variant)
     if (const char *fix = getenv("STG_DSLASH_SHAPE")) {
         const bool sh = strcmp(fix, "shared") == 0;
         if (sh && maxr >= 2 && !kind_has_u1(kind) && !kind_is_f64(kind) && !kind_is_ds(kind))
             return launch_dslash_bs(kind, a, mode, kSharedLinks, st);
+        if (strcmp(fix, "ahead") == 0 && ahead_ok) return launch_dslash_bs(kind, a, mode, kLoadsAhead, st);
         const int bs = atoi(fix);
         if (bs == 64 || bs == 128 || bs == 256) return launch_dslash_bs(kind, a, mode, bs, st);
     }
@@ -167,9 +171,10 @@ static cudaError_t launch_dslash_tuned(int kind, const DArgs &a, int mode, cudaS
         float best_t = 1e30f;
         // the shared-link operator only for several right-hand sides on FP32 / 16-bit links
         const bool shared_ok = maxr >= 2 && !kind_has_u1(kind) && !kind_is_f64(kind) && !kind_is_ds(kind);
-        const int cands[4] = {64, 128, 256, kSharedLinks};
+        const int cands[5] = {64, 128, 256, kSharedLinks, kLoadsAhead};
         for (int bs : cands) {
             if (bs == kSharedLinks && !shared_ok) continue;
+            if (bs == kLoadsAhead && !ahead_ok) continue;
             cudaError_t e = launch_dslash_bs(kind, a, mode, bs, st);  // warm-up
             if (e == cudaSuccess) e = cudaEventRecord(e0, st);
             for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_dslash_bs(kind, a, mode, bs, st);

@@ -102,11 +102,12 @@ def test_multi_rhs_matches_single(variant, nrhs):
 
 @pytest.mark.parametrize("variant", [("f32", 12), ("f32", 18), ("f16", 12), ("bf16", 12)])
 @pytest.mark.parametrize("nrhs", [2, 3, 8])
-@pytest.mark.parametrize("shape", ["shared", "64", "256"])
+@pytest.mark.parametrize("shape", ["shared", "64", "256", "ahead"])
 def test_multi_rhs_launch_shapes_bitwise(variant, nrhs, shape, monkeypatch):
     """Every launch shape of the multi-rhs operator -- including the shared-link kernel, which
-    stages each block's links in shared memory once for all rhs -- gives bitwise the single-rhs
-    results, on a lattice whose last 64-site block is ragged (Vh = 1000)."""
+    stages each block's links in shared memory once for all rhs, and the one-hop-lookahead loop
+    (FP32 12-real, 3-4 rhs; other cases fall back to the tuned shape) -- gives bitwise the
+    single-rhs results, on a lattice whose last 64-site block is ragged (Vh = 1000)."""
     p = stg()
     prec, recon = variant
     dims = (10, 10, 4, 10)
@@ -155,19 +156,21 @@ def test_pack_unpack_roundtrip():
 
 def test_full_size_32x32x32x32_sampled():
     """The benchmarked workload (32^4, exp(i 0.3 H) links, FP32 12-real and FP64 18-real):
-    D_eo over the full lattice against the oracle evaluated on every output site."""
+    D_eo and D_oe over the full lattice against the oracle evaluated on every output site."""
     p = stg()
     cfg = S.CONFIGS["bandwidth_32x32x32x32"]
     dims = cfg["dims"]
     u = S.gauge_links(dims, cfg["links"], 1000 + cfg["k"])
     psi = S.gaussian_field(dims, 2000 + cfg["k"], parity_sites=True)
-    ref = oracle.dslash(dims, u, 0, psi)
+    refs = {0: oracle.dslash(dims, u, 0, psi), 1: oracle.dslash(dims, u, 1, psi)}
     lat = p.Lattice(dims)
     ut = torch.from_numpy(u).cuda()
+    x = torch.from_numpy(psi).cuda()
     for prec, recon in [("f32", 12), ("f64", 18), ("ds", 18), ("bf16", 12)]:
         g = p.Gauge(lat, ut, prec, recon)
-        got = p.dslash_eo(g, torch.from_numpy(psi).cuda()).cpu().numpy()
-        assert rel(got, ref) <= TOL[(prec, recon)], (prec, recon, rel(got, ref))
+        for out_par, fn in ((0, p.dslash_eo), (1, p.dslash_oe)):
+            got = fn(g, x).cpu().numpy()
+            assert rel(got, refs[out_par]) <= TOL[(prec, recon)], (prec, recon, out_par, rel(got, refs[out_par]))
         del g
 
 

@@ -247,9 +247,10 @@ def test_batched_fp64_matches_single():
 
 
 def test_mixed_batch_bitwise_across_launch_shapes(monkeypatch):
-    """A mixed batch (4 sources sharing link loads, refinement in groups of 4 rhs) run with the
-    shared-link multi-rhs operator and with the 128-thread register operator: bitwise equal
-    solutions and statistics (the two operators round identically), every system <= tol."""
+    """A mixed batch (4 sources sharing link loads, refinement in groups of 4 rhs, converged
+    members skipped) run with the shared-link multi-rhs operator, the one-hop-lookahead operator
+    and the 128-thread register operator: bitwise equal solutions and statistics (the operators
+    round identically), every system <= tol."""
     p = stg()
     dims = (8, 4, 6, 6)
     u = S.gauge_links(dims, "expih", 93)
@@ -257,14 +258,15 @@ def test_mixed_batch_bitwise_across_launch_shapes(monkeypatch):
     lat, g64, gi = gauges(p, dims, u, ("f32", 12))
     bs = [torch.from_numpy(S.gaussian_field(dims, 930 + r)).cuda() for r in range(4)]
     out = {}
-    for shape in ("128", "shared"):
+    for shape in ("128", "shared", "ahead"):
         monkeypatch.setenv("STG_DSLASH_SHAPE", shape)
         (x, stats), = p.mscg_batched([(g64, gi, bs)], shifts, 0.05, tol=1e-10)
         out[shape] = (x.clone(), [(s["iters"], s["refine_iters"], s["reliable_updates"]) for s in stats])
         for r in range(4):
             assert max(stats[r]["true_resid"]) <= 1e-10
-    assert torch.equal(out["128"][0], out["shared"][0])
-    assert out["128"][1] == out["shared"][1]
+    for shape in ("shared", "ahead"):
+        assert torch.equal(out["128"][0], out[shape][0]), shape
+        assert out["128"][1] == out[shape][1], shape
 
 
 @pytest.mark.parametrize("mass,tol", [(0.3, 1e-7), (0.05, 1e-6), (0.01, 1e-7)])

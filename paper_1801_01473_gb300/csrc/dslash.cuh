@@ -75,7 +75,8 @@ __device__ __forceinline__ void neg3(cx<R> v[3])
 // doubles of shared memory; `act` is uniform over the block.
 template <typename R, int NRHS, int MODE, int BS>
 __device__ __forceinline__ void dslash_epilogue(const DGroup &G, const bool act[NRHS], bool live, int h,
-                                                const cx<R> acc[NRHS][3], double *sh)
+                                                const cx<R> acc[NRHS][3], double *sh,
+                                                const cx<R> (*pre_p)[3] = nullptr)
 {
     const int Vh = G.g.Vh;
 #pragma unroll
@@ -89,7 +90,12 @@ __device__ __forceinline__ void dslash_epilogue(const DGroup &G, const bool act[
                 for (int c = 0; c < 3; ++c) o[c] = cx<R>{R(0.5) * acc[j][c].re, R(0.5) * acc[j][c].im};
             } else {
                 cx<R> p[3];
-                Field<R>::load(G.epi_p[j], Vh, h, p);
+                if (pre_p != nullptr) {  // loaded by the caller ahead of time
+#pragma unroll
+                    for (int c = 0; c < 3; ++c) p[c] = pre_p[j][c];
+                } else {
+                    Field<R>::load(G.epi_p[j], Vh, h, p);
+                }
                 const R cj = (R)G.coef[j];
 #pragma unroll
                 for (int c = 0; c < 3; ++c)
@@ -134,9 +140,10 @@ __device__ __forceinline__ void dslash_epilogue(const DGroup &G, const bool act[
 // warps per SM); one hop of lookahead costs registers (~125, 16 warps per SM) but keeps loads in
 // flight through the arithmetic (0.69).  Same operations in the same order as the plain loop, so
 // results are bitwise equal.
-template <int NRHS>
+template <int NRHS, int MODE>
 __device__ __forceinline__ void dslash_hops_ahead_f32r12(const DGroup &G, int op, int h, const Site &s,
-                                                         const bool act[NRHS], cx<float> acc[NRHS][3])
+                                                         const bool act[NRHS], cx<float> acc[NRHS][3],
+                                                         cx<float> pre_p[NRHS][3])
 {
     const int Vh = G.g.Vh;
     Hop hq[4];
@@ -163,7 +170,17 @@ __device__ __forceinline__ void dslash_hops_ahead_f32r12(const DGroup &G, int op
     load(0, lc, vac, vbc);
 #pragma unroll
     for (int k = 0; k < 8; ++k) {
-        if (k < 7) load(k + 1, ln, van, vbn);
+        if (k < 7) {
+            load(k + 1, ln, van, vbn);
+        } else if (MODE != 0) {
+            // the last hop overlaps the epilogue's loads of p_j at the output site
+#pragma unroll
+            for (int j = 0; j < NRHS; ++j) {
+                if (!act[j]) continue;
+                van[j] = __ldg(static_cast<const float4 *>(G.epi_p[j]) + h);
+                vbn[j] = __ldg(reinterpret_cast<const float2 *>(static_cast<const float4 *>(G.epi_p[j]) + Vh) + h);
+            }
+        }
         cx<float> U[3][3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -200,6 +217,14 @@ __device__ __forceinline__ void dslash_hops_ahead_f32r12(const DGroup &G, int op
                 vac[j] = van[j];
                 vbc[j] = vbn[j];
             }
+        }
+    }
+    if (MODE != 0) {
+#pragma unroll
+        for (int j = 0; j < NRHS; ++j) {
+            pre_p[j][0] = cx<float>{van[j].x, van[j].y};
+            pre_p[j][1] = cx<float>{van[j].z, van[j].w};
+            pre_p[j][2] = cx<float>{vbn[j].x, vbn[j].y};
         }
     }
 }
@@ -295,8 +320,13 @@ __global__ void __launch_bounds__(BS) k_dslash(const __grid_constant__ DArgs a)
                     acc[j][r] = cx<R>{ds_two_sum(ahi[j][r][0], alo[j][r][0]), ds_two_sum(ahi[j][r][1], alo[j][r][1])};
         }
     } else if (AHEAD) {
-        if constexpr (std::is_same<LinkT, LinkF32R12>::value)
-            if (live) dslash_hops_ahead_f32r12<NRHS>(G, op, h, site_of(G.g, op, h), act, acc);
+        if constexpr (std::is_same<LinkT, LinkF32R12>::value) {
+            cx<float> pre_p[NRHS][3];
+            if (live) dslash_hops_ahead_f32r12<NRHS, MODE>(G, op, h, site_of(G.g, op, h), act, acc, pre_p);
+            __shared__ double sh[32];
+            dslash_epilogue<R, NRHS, MODE, BS>(G, act, live, h, acc, sh, MODE != 0 ? pre_p : nullptr);
+            return;
+        }
     } else if (live) {
         const Site s = site_of(G.g, op, h);
 #pragma unroll

@@ -856,7 +856,7 @@ def run_gpu(args):
             "roofline": {"bound": "hbm", "achieved": round(achieved, 1), "peak": peak, "unit": "GB/s",
                          "frac": round(achieved / peak, 4), "peak_kind": peak_kind,
                          "traffic": profile_traffic("deo_32x32x32x32_f32r12.md"),
-                         "kernel": "k_dslash<LinkF32R12,1,0>"},
+                         "kernel": "k_dslash<LinkF32R12,1,0,128,0>"},
             "gpu_launches": launches, "clocks": clocks, "e2e": e2e}
     if rank == 0 and not args.no_extras:
         line["sweep"] = time_deo_sweep(torch, p, (16, 16, 16, 16), peak) + time_deo_sweep(torch, p, (32, 32, 32, 32), peak)

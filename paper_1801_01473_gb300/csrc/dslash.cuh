@@ -137,9 +137,10 @@ __device__ __forceinline__ void dslash_epilogue(const DGroup &G, const bool act[
 // applied, the link of hop k + 1 and every rhs's neighbour vector of hop k + 1 are already in
 // flight in registers.  With several rhs per thread the plain loop is latency-bound (each hop's
 // multiply-adds wait for that hop's loads: 4 rhs at 32^4 reach 0.61 of HBM bandwidth with 28
-// warps per SM); one hop of lookahead costs registers (~125, 16 warps per SM) but keeps loads in
-// flight through the arithmetic (0.69).  Same operations in the same order as the plain loop, so
-// results are bitwise equal.
+// warps per SM); one hop of lookahead costs registers (127, 16 warps per SM) but keeps loads in
+// flight through the arithmetic (0.71).  With an epilogue (MODE 1, 2) the last hop loads p_j at the
+// output site instead.  Same operations in the same order as the plain loop, so results are
+// bitwise equal.
 template <int NRHS, int MODE>
 __device__ __forceinline__ void dslash_hops_ahead_f32r12(const DGroup &G, int op, int h, const Site &s,
                                                          const bool act[NRHS], cx<float> acc[NRHS][3],

@@ -22,7 +22,7 @@
 namespace stg {
 
 constexpr int kMaxRhs = 8;
-constexpr int kMaxGroups = 4;
+constexpr int kMaxGroups = 16;  // groups per launch (blockIdx.y): a DArgs of 16 groups is ~8.5 KB of kernel parameters
 constexpr int kDslashBlock = 128;   // default block; the autotuner may pick 64, 128 or 256
 constexpr int kPartialSites = 64;   // one FP64 partial per 64 output sites, whatever the block size
 

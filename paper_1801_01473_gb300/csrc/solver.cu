@@ -1464,9 +1464,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
 
     // ---------------- FP64 verification of double-single results
     if (kDS && anchored) {
-        // the residuals are FP64-anchored: x_hi to FP64 for the output, no further operator
-        st = convert_xb(true, false);
-        if (st != STG_OK) return st;
+        // the residuals are FP64-anchored: no further operator (the output unpack widens x_hi)
         stamp("anchored refinement: no FP64 verification needed");
     } else if (kDS) {
         // x_hi (per pair) and b (per system) to FP64 in place: same 48-byte site layout
@@ -1522,7 +1520,10 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
                     cp[pidx] = ConvPair{v2[pidx].xhi, inst[k].x[r * ns + i], v2[pidx].Vh};
                 }
         STG_CUDA_TRY(cudaMemcpyAsync(d_pairs, cp.data(), sizeof(ConvPair) * npair, cudaMemcpyHostToDevice, ws));
-        k_unpack_pairs<double><<<vgrid2, kVecBlock, 0, ws>>>(d_pairs);  // x_hi is FP64 here
+        if (kDS && anchored)
+            k_unpack_pairs<H><<<vgrid2, kVecBlock, 0, ws>>>(d_pairs);  // x_hi still double-single
+        else
+            k_unpack_pairs<double><<<vgrid2, kVecBlock, 0, ws>>>(d_pairs);  // x_hi is FP64 here
         STG_CUDA_TRY(cudaGetLastError());
     }
     std::vector<SysScal> f1(nsys), f2(npair);

@@ -81,9 +81,11 @@ def test_normal_op_and_fused_dot(variant):
 
 
 @pytest.mark.parametrize("variant", [("f64", 18), ("ds", 12), ("f32", 12), ("bf16", 12)])
-@pytest.mark.parametrize("nrhs", [1, 3, 8, 11])
+@pytest.mark.parametrize("nrhs", [1, 3, 8, 11, 45])
 def test_multi_rhs_matches_single(variant, nrhs):
-    """Shared link loads over nrhs right-hand sides give bitwise the single-rhs results."""
+    """Shared link loads over nrhs right-hand sides give bitwise the single-rhs results (45 rhs:
+    six groups of up to 8 in one launch; double-single splits them into 45 one-rhs groups, three
+    launches of up to 16)."""
     p = stg()
     prec, recon = variant
     dims = (8, 4, 6, 4)

@@ -879,7 +879,8 @@ def run_gpu(args):
 def run_case(name):
     """One small workload for a profiler to capture (no timing, no JSON line): `deo32_<storage>`
     four D_eo launches at 32^4 on that link storage (e.g. deo32_bf16r12); `deo32x<n>_<storage>` four
-    D_oe launches on n right-hand sides sharing each link load (e.g. deo32x4_f32r12); `mscg` runs two mixed
+    D_oe launches on n right-hand sides sharing each link load (e.g. deo32x4_f32r12); `batched` two
+    batched uneven solves (the time_batched workload); `mscg` runs two mixed
     FP32-inner solves of the 32^4 msCG workload; `force32` three double-single D_eo applications and
     one 4-shift fermion force at 32^4; `stout24` one stout step and its chain rule at 24^4;
     `gauge24` the gauge force and action at 24^4; `fp32links24` the single-precision gauge force,
@@ -930,6 +931,20 @@ def run_case(name):
         print("mscg", json.dumps({k: (list(v) if hasattr(v, "__len__") else v) for k, v in st.items()
                                   if k in ("iters", "refine_iters", "reliable_updates", "shift_iters",
                                            "refine_shift_iters", "shift_reliable_updates", "true_resid")}))
+    elif name == "batched":
+        # the batched uneven solve of time_batched (16^4, 24^3x8, 32^3x8, 24^4; 4 sources x 16 poles), twice
+        cfg = S.CONFIGS["batched_uneven"]
+        insts = []
+        for li, dims in enumerate(cfg["dims_list"]):
+            ut = torch.from_numpy(links_cached(dims, cfg["links"], 1000 + 10 * cfg["k"] + li)).cuda()
+            lat = p.Lattice(dims)
+            bs = [torch.from_numpy(S.gaussian_field(dims, 2000 + 10 * cfg["k"] + 4 * li + r)).cuda()
+                  for r in range(cfg["nrhs"])]
+            insts.append((p.Gauge(lat, ut, "f64", 18), p.Gauge(lat, ut, "f32", 12), bs))
+        for _ in range(2):
+            out = p.mscg_batched(insts, cfg["shifts"](), cfg["mass"], tol=cfg["tol"])
+        torch.cuda.synchronize()
+        print("batched", json.dumps([[(s["iters"], s["refine_iters"]) for s in sts] for _, sts in out]))
     elif name == "force32":
         dims = (32, 32, 32, 32)
         lat = p.Lattice(dims)
@@ -1006,7 +1021,7 @@ def main():
     ap.add_argument("--case", default=None,
                     choices=["mscg", "force32", "stout24", "gauge24", "fp32links24", "rhmc_force32", "deo32_f32r12",
                              "deo32_f32r18", "deo32_bf16r12", "deo32_f16r12", "deo32_dsr18", "deo32_f64r18",
-                             "deo32x2_f32r12", "deo32x4_f32r12", "deo32x8_f32r12"],
+                             "deo32x2_f32r12", "deo32x4_f32r12", "deo32x8_f32r12", "batched"],
                     help="run one small workload for a profiler instead of the benchmark")
     args = ap.parse_args()
     if args.case:

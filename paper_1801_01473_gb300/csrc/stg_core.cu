@@ -1,5 +1,6 @@
 // stg_core.cu -- C ABI: lattice and gauge handles, field packing, D_eo / D_oe and the
 // shifted normal operator (Sec. 2, Eq. shift_eo; link compression and phases, Sec. 4.1).
+#include <algorithm>
 #include <cstdio>
 #include <cstdlib>
 #include <cstring>
@@ -172,26 +173,34 @@ static cudaError_t launch_dslash_tuned(int kind, const DArgs &a, int mode, cudaS
         // the shared-link operator only for several right-hand sides on FP32 / 16-bit links
         const bool shared_ok = maxr >= 2 && !kind_has_u1(kind) && !kind_is_f64(kind) && !kind_is_ds(kind);
         const int cands[5] = {64, 128, 256, kSharedLinks, kLoadsAhead};
-        for (int bs : cands) {
-            if (bs == kSharedLinks && !shared_ok) continue;
-            if (bs == kLoadsAhead && !ahead_ok) continue;
-            cudaError_t e = launch_dslash_bs(kind, a, mode, bs, st);  // warm-up
-            if (e == cudaSuccess) e = cudaEventRecord(e0, st);
-            for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_dslash_bs(kind, a, mode, bs, st);
-            if (e == cudaSuccess) e = cudaEventRecord(e1, st);
-            if (e == cudaSuccess) e = cudaEventSynchronize(e1);
-            float ms = 0.f;
-            if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
-            if (e != cudaSuccess) {
-                cudaEventDestroy(e0);
-                cudaEventDestroy(e1);
-                return e;
+        // two passes over the candidates, each candidate keeping its faster pass: one pass of three
+        // launches picked 256-thread blocks for the solver's 4-rhs D_eo in one process and 64 in
+        // another (10 % apart per launch)
+        float t_min[5] = {1e30f, 1e30f, 1e30f, 1e30f, 1e30f};
+        for (int pass = 0; pass < 2; ++pass)
+            for (int ci = 0; ci < 5; ++ci) {
+                const int bs = cands[ci];
+                if (bs == kSharedLinks && !shared_ok) continue;
+                if (bs == kLoadsAhead && !ahead_ok) continue;
+                cudaError_t e = launch_dslash_bs(kind, a, mode, bs, st);  // warm-up
+                if (e == cudaSuccess) e = cudaEventRecord(e0, st);
+                for (int r = 0; r < 3 && e == cudaSuccess; ++r) e = launch_dslash_bs(kind, a, mode, bs, st);
+                if (e == cudaSuccess) e = cudaEventRecord(e1, st);
+                if (e == cudaSuccess) e = cudaEventSynchronize(e1);
+                float ms = 0.f;
+                if (e == cudaSuccess) e = cudaEventElapsedTime(&ms, e0, e1);
+                if (e != cudaSuccess) {
+                    cudaEventDestroy(e0);
+                    cudaEventDestroy(e1);
+                    return e;
+                }
+                t_min[ci] = std::min(t_min[ci], ms);
             }
-            if (ms < best_t) {
-                best_t = ms;
-                best = bs;
+        for (int ci = 0; ci < 5; ++ci)
+            if (t_min[ci] < best_t) {
+                best_t = t_min[ci];
+                best = cands[ci];
             }
-        }
         cudaEventDestroy(e0);
         cudaEventDestroy(e1);
     }

@@ -374,7 +374,7 @@ def mscg_moved_bytes(insts, lb_inner, mixed, nshift):
     W = 0
     if mixed:
         ring = sum(len(sts) * n * 24 for n, sts in insts)
-        fit = (4 << 30) // max(ring, 1)
+        fit = (16 << 30) // max(ring, 1)
         W = min(SOLVER_HIST_MAX, fit - 1) if fit > 1 else 8
         W = max(8, W - W % 8)
     total = 0

@@ -217,7 +217,7 @@ typedef struct {
     int32_t history;         /* mixed solves, multi-shift phase: residuals kept per window of the
                                 deferred solution update (x_i, p_i of every shift formed once per
                                 window from the stored FP32 residuals instead of every
-                                iteration); 0 -> automatic (up to 256 within 4 GiB of residual
+                                iteration); 0 -> automatic (up to 256 within 16 GiB of residual
                                 storage per solve), 1 -> per-iteration updates, >= 2 -> that many
                                 (rounded down to a multiple of 8, at least 8, at most 256);
                                 < 0 -> STG_ERR_ARG                                               */

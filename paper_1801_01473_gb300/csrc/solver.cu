@@ -1004,7 +1004,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
     memset(s1.data(), 0, sizeof(SysScal) * nsys);
     memset(s2.data(), 0, sizeof(SysScal) * npair);
     // Deferred multi-shift update (FP32 phase 1): window length W (a multiple of the chunk), ring of
-    // W + 1 residuals per system; prm->history: 0 automatic (up to kHistMax within 4 GiB of rings),
+    // W + 1 residuals per system; prm->history: 0 automatic (up to kHistMax within 16 GiB of rings),
     // 1 per-iteration updates, >= 8 that many residuals per window
     int hist_w = 0;
     if (std::is_same<R, float>::value && prm->history != 1) {
@@ -1016,7 +1016,7 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         } else {
             // slots that fit the budget, less the one holding the current residual (at least the
             // minimum window when even that does not fit)
-            const size_t budget = (size_t)4 << 30;
+            const size_t budget = (size_t)16 << 30;  // 16 GiB of the GPU's ~280 GB
             const size_t fit = budget / std::max<size_t>(ring_field, 1);
             hist_w = fit > 1 ? (int)std::min<size_t>(kHistMax, fit - 1) : 8;
         }

@@ -16,9 +16,10 @@ The same JSON line carries (measured in the same run, outside the timed steps):
              the workload computes in FP32 -- pack, D_eo, unpack, device -> host, pipelined on
              three streams; the complex128 figure beside it);
   roofline   D_eo FP32-12 against the measured HBM copy bandwidth;
-  sweep      16^4 and 32^4 D_eo for every link storage: single launches after an L2 flush that
-             leaves clean lines (median of 50), and back-to-back launches over distinct sources
-             alternating two link copies; GB/s and fraction of the measured HBM bandwidth;
+  sweep      16^4 and 32^4 D_eo for every link storage (and 32^4 D_oe for FP64-18, FP32-12 and
+             BF16-12): single launches after an L2 flush that leaves clean lines (median of 50),
+             and back-to-back launches over distinct sources alternating two link copies; GB/s
+             and fraction of the measured HBM bandwidth;
   mscg       32^4 msCG (16 poles 1e-5..10, m = 0.01, true residual 1e-10): mixed
              (FP32, FP16, BF16 inner; double-single reliable updates, FP64-verified) vs pure
              FP64, s/solve, and the effective bandwidth of the algorithmic bytes;
@@ -276,10 +277,11 @@ class L2Flush:
         self.sink.copy_(self.r.sum())
 
 
-def time_deo_sweep(torch, p, dims, peak, reps=50, b2b_batch=32):
+def time_deo_sweep(torch, p, dims, peak, reps=50, b2b_batch=32, doe=()):
     """D_eo per storage kind at `dims`: single launches after an L2 flush (median of reps), and
     back-to-back launches over distinct sources alternating two copies of the links (the
-    configuration of the headline number; replayed from a CUDA graph)."""
+    configuration of the headline number; replayed from a CUDA graph).  D_oe is timed the same way
+    for the storage kinds listed in `doe` ((prec, recon) pairs, no phase field)."""
     cfg_links = links_cached(dims, "expih", 1000 + 2)
     ut = torch.from_numpy(cfg_links).cuda()
     lat = p.Lattice(dims)
@@ -287,6 +289,39 @@ def time_deo_sweep(torch, p, dims, peak, reps=50, b2b_batch=32):
     flush = L2Flush(torch)
     out = []
     theta = torch.from_numpy(np.random.default_rng(4000 + 2).uniform(-np.pi, np.pi, (4, lat.V))).cuda()
+
+    def time_op(fn, gs, x, y, src, dst):
+        for _ in range(5):
+            fn(gs[0], y, x)
+        ts = []
+        for _ in range(reps):
+            flush()
+            e0, e1 = events(torch)
+            e0.record()
+            fn(gs[0], y, x)
+            e1.record()
+            torch.cuda.synchronize()
+            ts.append(e0.elapsed_time(e1) * 1e-3)
+        t = float(np.median(ts))
+        # back to back: the launches captured once into a CUDA graph, so that host launch overhead
+        # (~10 us per ctypes call) cannot starve the small lattices
+        for j in range(b2b_batch):
+            fn(gs[j & 1], dst[j], src[j])
+        torch.cuda.synchronize()
+        graph = torch.cuda.CUDAGraph()
+        with torch.cuda.graph(graph):
+            for j in range(b2b_batch):
+                fn(gs[j & 1], dst[j], src[j])
+        graph.replay()
+        e0, e1 = events(torch)
+        e0.record()
+        for _ in range(3):
+            graph.replay()
+        e1.record()
+        torch.cuda.synchronize()
+        del graph
+        return t, e0.elapsed_time(e1) * 1e-3 / (3 * b2b_batch)
+
     for prec, recon, u1 in [("f64", 18, False), ("f64", 12, False), ("ds", 18, False), ("ds", 12, False),
                             ("f32", 18, False), ("f32", 12, False), ("f16", 12, False), ("bf16", 12, False),
                             ("f64", 18, True), ("ds", 18, True), ("f32", 12, True), ("f16", 12, True)]:
@@ -295,42 +330,17 @@ def time_deo_sweep(torch, p, dims, peak, reps=50, b2b_batch=32):
         src = x.unsqueeze(0).repeat(b2b_batch, 1)
         dst = torch.empty_like(src)
         y = torch.empty_like(x)
-        for _ in range(5):
-            p.dslash_eo_(gs[0], y, x)
-        ts = []
-        for _ in range(reps):
-            flush()
-            e0, e1 = events(torch)
-            e0.record()
-            p.dslash_eo_(gs[0], y, x)
-            e1.record()
-            torch.cuda.synchronize()
-            ts.append(e0.elapsed_time(e1) * 1e-3)
-        t = float(np.median(ts))
-        # back to back: the launches captured once into a CUDA graph, so that host launch overhead
-        # (~10 us per ctypes call) cannot starve the small lattices
-        for j in range(b2b_batch):
-            p.dslash_eo_(gs[j & 1], dst[j], src[j])
-        torch.cuda.synchronize()
-        graph = torch.cuda.CUDAGraph()
-        with torch.cuda.graph(graph):
-            for j in range(b2b_batch):
-                p.dslash_eo_(gs[j & 1], dst[j], src[j])
-        graph.replay()
-        e0, e1 = events(torch)
-        e0.record()
-        for _ in range(3):
-            graph.replay()
-        e1.record()
-        torch.cuda.synchronize()
-        tb = e0.elapsed_time(e1) * 1e-3 / (3 * b2b_batch)
-        del graph
         # a U(1) phase field adds one stored phase per link ((cos, sin) doubles for f64/ds, a float angle otherwise)
         byt = (bytes_per_site(prec, recon) + (8 * (16 if prec in ("f64", "ds") else 4) if u1 else 0)) * lat.Vh
-        out.append({"lattice": "x".join(map(str, dims)), "links": f"{prec}-{recon}" + ("+u1" if u1 else ""),
-                    "us": round(t * 1e6, 2), "GBs": round(byt / t / 1e9, 1), "frac": round(byt / t / 1e9 / peak, 3),
-                    "b2b_us": round(tb * 1e6, 2), "b2b_GBs": round(byt / tb / 1e9, 1),
-                    "b2b_frac": round(byt / tb / 1e9 / peak, 3)})
+        ops = [("D_eo", p.dslash_eo_)] + ([("D_oe", p.dslash_oe_)] if (prec, recon) in doe and not u1 else [])
+        for name, fn in ops:
+            t, tb = time_op(fn, gs, x, y, src, dst)
+            out.append({"lattice": "x".join(map(str, dims)), "op": name,
+                        "links": f"{prec}-{recon}" + ("+u1" if u1 else ""),
+                        "us": round(t * 1e6, 2), "GBs": round(byt / t / 1e9, 1),
+                        "frac": round(byt / t / 1e9 / peak, 3),
+                        "b2b_us": round(tb * 1e6, 2), "b2b_GBs": round(byt / tb / 1e9, 1),
+                        "b2b_frac": round(byt / tb / 1e9 / peak, 3)})
         del gs, src, dst
     return out
 
@@ -866,7 +876,8 @@ def run_gpu(args):
                          "kernel": "k_dslash<LinkF32R12,1,0,128,0>"},
             "gpu_launches": launches, "clocks": clocks, "e2e": e2e}
     if rank == 0 and not args.no_extras:
-        line["sweep"] = time_deo_sweep(torch, p, (16, 16, 16, 16), peak) + time_deo_sweep(torch, p, (32, 32, 32, 32), peak)
+        line["sweep"] = time_deo_sweep(torch, p, (16, 16, 16, 16), peak) + time_deo_sweep(
+            torch, p, (32, 32, 32, 32), peak, doe=(("f64", 18), ("f32", 12), ("bf16", 12)))
         line["mscg"] = time_mscg(torch, p, peak)
         line["batched"] = time_batched(torch, p, peak)
         line["force"] = time_force(torch, p, peak)

@@ -776,9 +776,14 @@ def thermalised_start(torch, p, tab, ntraj=40, nfree=20, small=(8, 8, 8, 8), rep
             "mean_abs_dH": round(float(np.mean(np.abs(dhs))), 4) if dhs else None,
             "plaquette_start": round(plaq0, 5), "plaquette_end": round(mean_plaquette(p, lat, u), 5),
             "s": round(time.perf_counter() - t0, 2)}
-    L = small
-    big = u.reshape(4, L[3], L[2], L[1], L[0], 3, 3).repeat(1, reps, reps, reps, reps, 1, 1)
-    return big.reshape(4, -1, 3, 3).contiguous(), info
+    return tile_links(u, small, reps), info
+
+
+def tile_links(u, dims, reps):
+    """Links [4, V, 3, 3] (site x + Lx (y + Ly (z + Lz t))) of a lattice dims = (Lx, Ly, Lz, Lt)
+    repeated `reps` times along every direction: the links of the (reps Lx, ..., reps Lt) lattice."""
+    big = u.reshape(4, dims[3], dims[2], dims[1], dims[0], 3, 3).repeat(1, reps, reps, reps, reps, 1, 1)
+    return big.reshape(4, -1, 3, 3).contiguous()
 
 
 def time_rhmc(torch, p):

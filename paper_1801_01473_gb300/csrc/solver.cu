@@ -347,9 +347,8 @@ __device__ __forceinline__ void fold_acc<double>(double &acc, float v)
 // float2 number e: colours 0, 1 of site e/2 for e < 2Vh, colour 2 of site e - 2Vh above), each thread
 // block covering kFlushShifts shifts.  Sums of 8 terms are formed in FP32 and folded into an
 // accumulator of the solution precision H.
-template <typename H, bool MATP>
-__global__ void __launch_bounds__(kVecBlock) k_flush(const SysScal *__restrict__ sc, const SysVecs *__restrict__ sv,
-                                                      int nchunk)
+template <typename H, bool MATP, bool PREFETCH>
+__device__ __forceinline__ void flush_body(const SysScal *__restrict__ sc, const SysVecs *__restrict__ sv, int nchunk)
 {
     __shared__ __align__(16) float s_a[kHistMax][kFlushShifts];
     __shared__ __align__(16) float s_d[MATP ? kHistMax : 1][kFlushShifts];
@@ -388,6 +387,7 @@ __global__ void __launch_bounds__(kVecBlock) k_flush(const SysScal *__restrict__
     }
     int slot = C.first_slot;
     const int nslot = V.nslot;
+    int pslot = PREFETCH ? (slot + 8) % nslot : 0;  // slot of the residual 8 iterations on
     const char *ring = static_cast<const char *>(V.r);
     for (int t0 = 0; t0 < n; t0 += 8) {
         const int m = min(8, n - t0);
@@ -396,6 +396,15 @@ __global__ void __launch_bounds__(kVecBlock) k_flush(const SysScal *__restrict__
         for (int u = 0; u < 8; ++u) {
             if (u < m) {
                 rv[u] = reinterpret_cast<const float2 *>(ring + (size_t)slot * V.slot_bytes)[e];
+                if constexpr (PREFETCH) {
+                    // the residual 8 slots on is requested into L2 now, so that the next group's
+                    // loads find it there while this group's multiply-adds run (the same in-bounds
+                    // slot and element that the next group loads)
+                    if (t0 + 8 + u < n)
+                        asm volatile("prefetch.global.L2 [%0];" ::"l"(reinterpret_cast<const float2 *>(
+                                         ring + (size_t)pslot * V.slot_bytes) + e));
+                    pslot = pslot + 1 == nslot ? 0 : pslot + 1;
+                }
                 slot = slot + 1 == nslot ? 0 : slot + 1;
             } else {
                 rv[u] = make_float2(0.f, 0.f);
@@ -462,6 +471,22 @@ __global__ void __launch_bounds__(kVecBlock) k_flush(const SysScal *__restrict__
             }
         }
     }
+}
+
+template <typename H, bool MATP>
+__global__ void __launch_bounds__(kVecBlock) k_flush(const SysScal *__restrict__ sc, const SysVecs *__restrict__ sv,
+                                                      int nchunk)
+{
+    flush_body<H, MATP, false>(sc, sv, nchunk);
+}
+
+// The final flush of the mixed solves (solutions only, double-single): each thread keeps one group
+// of 8 residual loads in flight and requests the next group into L2 meanwhile, at three blocks of
+// 80 registers per SM.
+__global__ void __launch_bounds__(kVecBlock, 3) k_flush_final_ds(const SysScal *__restrict__ sc,
+                                                                 const SysVecs *__restrict__ sv, int nchunk)
+{
+    flush_body<dsf, false, true>(sc, sv, nchunk);
 }
 
 // ------------------------------------------------------------------ scalar kernels (one warp per system)
@@ -1282,7 +1307,9 @@ static stg_status solve_impl(int ninst, const stg_instance *inst, const stg_mscg
         if (hist_w == 0) return cudaSuccess;
         k_flush_coef<<<nsys, 32, 0, ws>>>(d_s1, d_v1, final_flush ? 1 : 0);
         const dim3 g((unsigned)(nchunk * nblke_max), nsys);
-        if (final_flush)
+        if (final_flush && std::is_same<H, dsf>::value)
+            k_flush_final_ds<<<g, kVecBlock, 0, ws>>>(d_s1, d_v1, nchunk);
+        else if (final_flush)
             k_flush<H, false><<<g, kVecBlock, 0, ws>>>(d_s1, d_v1, nchunk);
         else
             k_flush<H, true><<<g, kVecBlock, 0, ws>>>(d_s1, d_v1, nchunk);

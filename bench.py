@@ -22,7 +22,8 @@ The same JSON line carries (measured in the same run, outside the timed steps):
              and fraction of the measured HBM bandwidth;
   mscg       32^4 msCG (16 poles 1e-5..10, m = 0.01, true residual 1e-10): mixed
              (FP32, FP16, BF16 inner; double-single reliable updates, FP64-verified) vs pure
-             FP64, s/solve, and the effective bandwidth of the algorithmic bytes;
+             FP64, s/solve, and the effective bandwidth of the algorithmic bytes; the FP32-inner
+             solve also end to end through stg.mscg with a pinned host source;
   batched    the uneven batch (16^4, 24^3x8, 32^3x8, 24^4, 4 sources x 16 shifts) in one
              solve vs the sum of separate solves, with per-instance iteration counts;
   force      48^4 fermion force (12 shifts): whole call, its double-single D_oe part and the
